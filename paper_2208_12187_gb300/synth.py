@@ -1,0 +1,248 @@
+"""Seeded synthetic curve-fit problems shaped like the paper's workloads.
+
+This module only *draws inputs*: coordinates, noisy observations, per-point
+uncertainties, seed parameters and bounds.  It holds none of the fitting
+method's arithmetic (no residuals, Jacobians, reductions or trust-region
+steps).  To synthesise observations it needs the forward value of each model
+at the true parameters; those few lines are written here on their own so that
+neither the CUDA path nor the oracle is imported by the other through it.
+
+The paper's own dataset (Section 4: rotated elliptical 2D Gaussians with
+uniformly drawn parameters and fixed-sigma Gaussian noise, data lengths 1e4 to
+8e6) is itself synthetic and its parameter ranges are not given; the problems
+below stand in for it with stated, seeded recipes.
+
+Model ids (shared vocabulary of the library, the oracle and this module):
+  0  gauss1d : h = A exp(-(x-mu)^2 / (2 s^2)) + c            p = (A, mu, s, c)
+  1  dexp    : h = a1 exp(-x/t1) + a2 exp(-x/t2) + c          p = (a1, t1, a2, t2, c)
+  2  gauss2d : h = A exp(-u^2/(2 sx^2) - v^2/(2 sy^2)) + c
+               u =  (X-x0) cos(th) + (Y-y0) sin(th)
+               v = -(X-x0) sin(th) + (Y-y0) cos(th)            p = (A, x0, y0, sx, sy, th, c)
+  3  poly2   : h = p0 + p1 x + p2 x^2   (linear in p; closed-form test model)
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+MODEL_GAUSS1D = 0
+MODEL_DEXP = 1
+MODEL_GAUSS2D = 2
+MODEL_POLY2 = 3
+
+N_PARAMS = {MODEL_GAUSS1D: 4, MODEL_DEXP: 5, MODEL_GAUSS2D: 7, MODEL_POLY2: 3}
+X_DIMS = {MODEL_GAUSS1D: 1, MODEL_DEXP: 1, MODEL_GAUSS2D: 2, MODEL_POLY2: 1}
+
+# x layouts (same numbering as the C ABI)
+LAYOUT_VEC = 0    # x: [m]
+LAYOUT_SOA2 = 1   # x: [2, m]  (X row then Y row)
+LAYOUT_GRID = 2   # no x array: point i is pixel (X = i % W, Y = i // W)
+
+
+@dataclasses.dataclass
+class Problem:
+    """One fit's inputs.  Arrays are host NumPy arrays."""
+    model: int
+    x: Optional[np.ndarray]          # None for LAYOUT_GRID
+    layout: int
+    grid_wh: Optional[tuple]         # (W, H) for LAYOUT_GRID
+    y: np.ndarray
+    sigma: Optional[np.ndarray]
+    p0: np.ndarray
+    lb: Optional[np.ndarray]
+    ub: Optional[np.ndarray]
+    truth: np.ndarray
+
+    @property
+    def m(self) -> int:
+        return int(self.y.shape[0])
+
+    @property
+    def n(self) -> int:
+        return N_PARAMS[self.model]
+
+    def coords(self) -> np.ndarray:
+        """Explicit coordinates as float64 [xdims, m] (grid expanded)."""
+        if self.layout == LAYOUT_GRID:
+            W, H = self.grid_wh
+            i = np.arange(W * H, dtype=np.int64)
+            return np.stack([(i % W).astype(np.float64), (i // W).astype(np.float64)])
+        x = np.asarray(self.x, dtype=np.float64)
+        return x.reshape(1, -1) if x.ndim == 1 else x
+
+    def astype(self, dtype) -> "Problem":
+        """Same problem with data arrays cast to dtype (parameters stay float64)."""
+        cast = lambda a: None if a is None else np.ascontiguousarray(a, dtype=dtype)
+        return dataclasses.replace(self, x=cast(self.x), y=cast(self.y), sigma=cast(self.sigma))
+
+
+# ---------------------------------------------------------------- forward values
+def _forward(model: int, X: np.ndarray, p: np.ndarray) -> np.ndarray:
+    """Noise-free model value used only to synthesise observations (float64)."""
+    if model == MODEL_GAUSS1D:
+        A, mu, s, c = p
+        return A * np.exp(-((X[0] - mu) ** 2) / (2.0 * s * s)) + c
+    if model == MODEL_DEXP:
+        a1, t1, a2, t2, c = p
+        return a1 * np.exp(-X[0] / t1) + a2 * np.exp(-X[0] / t2) + c
+    if model == MODEL_GAUSS2D:
+        A, x0, y0, sx, sy, th, c = p
+        dx, dy = X[0] - x0, X[1] - y0
+        ct, st = math.cos(th), math.sin(th)
+        u = dx * ct + dy * st
+        v = -dx * st + dy * ct
+        return A * np.exp(-0.5 * (u * u / (sx * sx) + v * v / (sy * sy))) + c
+    if model == MODEL_POLY2:
+        return p[0] + p[1] * X[0] + p[2] * X[0] ** 2
+    raise ValueError(f"unknown model {model}")
+
+
+def forward_values(model: int, X: np.ndarray, p) -> np.ndarray:
+    """Public alias of the synthesis forward model (float64 [m])."""
+    return _forward(model, np.asarray(X, dtype=np.float64).reshape(-1, np.shape(X)[-1]),
+                    np.asarray(p, dtype=np.float64))
+
+
+# ---------------------------------------------------------------- generators
+def gauss1d(m: int = 10_000, seed: int = 0, noise: float = 0.1, with_sigma: bool = False,
+            truth=(5.0, 0.3, 1.2, 0.5), dtype=np.float64, noise_free: bool = False) -> Problem:
+    """1D Gaussian + offset: x ~ U[-10, 10], additive N(0, noise^2), p0 = truth*(1+U(-.2,.2))."""
+    rng = np.random.default_rng(seed)
+    truth = np.asarray(truth, dtype=np.float64)
+    x = rng.uniform(-10.0, 10.0, size=m)
+    y = _forward(MODEL_GAUSS1D, x[None, :], truth)
+    e = rng.normal(0.0, noise, size=m)
+    if not noise_free:
+        y = y + e
+    p0 = truth * (1.0 + rng.uniform(-0.2, 0.2, size=4))
+    sigma = np.ones(m) if with_sigma else None
+    return Problem(MODEL_GAUSS1D, x, LAYOUT_VEC, None, y, sigma, p0, None, None,
+                   truth).astype(dtype)
+
+
+def dexp_params(rng) -> np.ndarray:
+    """Double-exponential truth: t1,t2 log-U[0.1,100]; a1,a2 U[1,10]; c U[0,1]."""
+    t1, t2 = np.exp(rng.uniform(math.log(0.1), math.log(100.0), size=2))
+    a1, a2 = rng.uniform(1.0, 10.0, size=2)
+    c = rng.uniform(0.0, 1.0)
+    return np.array([a1, t1, a2, t2, c])
+
+
+def dexp(m: int, seed: int = 0, truth=None, dtype=np.float64, noise_free: bool = False,
+         bounded: bool = True) -> Problem:
+    """Double exponential: x ~ U[0, 5 max(t)], noise N(0, (0.01 (a1+a2+c))^2), t > 0 bounds."""
+    rng = np.random.default_rng(seed)
+    truth = dexp_params(rng) if truth is None else np.asarray(truth, dtype=np.float64)
+    x = rng.uniform(0.0, 5.0 * max(truth[1], truth[3]), size=m)
+    y = _forward(MODEL_DEXP, x[None, :], truth)
+    e = rng.normal(0.0, 0.01 * (truth[0] + truth[2] + truth[4]), size=m)
+    if not noise_free:
+        y = y + e
+    p0 = truth * (1.0 + rng.uniform(-0.2, 0.2, size=5))
+    lb = ub = None
+    if bounded:
+        lb = np.array([-np.inf, 0.0, -np.inf, 0.0, -np.inf])
+        ub = np.full(5, np.inf)
+    return Problem(MODEL_DEXP, x, LAYOUT_VEC, None, y, None, p0, lb, ub, truth).astype(dtype)
+
+
+def gauss2d_grid(W: int = 1024, H: Optional[int] = None, seed: int = 0, truth=None,
+                 dtype=np.float32, layout: int = LAYOUT_GRID, poisson: bool = True,
+                 bounded: bool = True) -> Problem:
+    """Rotated 2D Gaussian on a W x H pixel grid with Poisson counts.
+
+    Default truth for 1024 x 1024: A=980, c=20 (peak 1000 on background 20),
+    x0=512.3, y0=498.7, sx=60, sy=35, theta=0.4.  Other sizes scale centre and
+    widths with W.  sigma = sqrt(max(y, 1)).  Bounds: sx, sy in [0.5, 500],
+    theta in [-pi/2, pi/2].  p0: A, c, sx, sy x (1+U(-.2,.2)); x0, y0 + U(-5,5);
+    theta + U(-0.1, 0.1).
+    """
+    H = W if H is None else H
+    rng = np.random.default_rng(seed)
+    if truth is None:
+        k = W / 1024.0
+        truth = np.array([980.0, 512.3 * k, 498.7 * H / 1024.0, 60.0 * k, 35.0 * k, 0.4, 20.0])
+    truth = np.asarray(truth, dtype=np.float64)
+    i = np.arange(W * H, dtype=np.int64)
+    X = np.stack([(i % W).astype(np.float64), (i // W).astype(np.float64)])
+    mu = _forward(MODEL_GAUSS2D, X, truth)
+    y = rng.poisson(mu).astype(np.float64) if poisson else mu
+    sigma = np.sqrt(np.maximum(y, 1.0))
+    p0 = truth.copy()
+    for j in (0, 6, 3, 4):
+        p0[j] *= 1.0 + rng.uniform(-0.2, 0.2)
+    p0[1] += rng.uniform(-5.0, 5.0)
+    p0[2] += rng.uniform(-5.0, 5.0)
+    p0[5] += rng.uniform(-0.1, 0.1)
+    lb = ub = None
+    if bounded:
+        lb = np.array([-np.inf, -np.inf, -np.inf, 0.5, 0.5, -math.pi / 2, -np.inf])
+        ub = np.array([np.inf, np.inf, np.inf, 500.0, 500.0, math.pi / 2, np.inf])
+        p0 = np.clip(p0, lb + 1e-6, ub - 1e-6)
+    x = None if layout == LAYOUT_GRID else X
+    return Problem(MODEL_GAUSS2D, x, layout, (W, H) if layout == LAYOUT_GRID else None,
+                   y, sigma, p0, lb, ub, truth).astype(dtype)
+
+
+def poly2(m: int = 1000, seed: int = 0, truth=(1.5, -0.7, 0.25), noise: float = 0.05,
+          with_sigma: bool = True, dtype=np.float64) -> Problem:
+    """Quadratic polynomial (linear least squares): x ~ U[-3, 3], sigma ~ U[0.5, 2]."""
+    rng = np.random.default_rng(seed)
+    truth = np.asarray(truth, dtype=np.float64)
+    x = rng.uniform(-3.0, 3.0, size=m)
+    sigma = rng.uniform(0.5, 2.0, size=m) if with_sigma else None
+    y = _forward(MODEL_POLY2, x[None, :], truth)
+    y = y + rng.normal(0.0, noise, size=m) * (sigma if sigma is not None else 1.0)
+    p0 = truth + rng.uniform(-1.0, 1.0, size=3)
+    return Problem(MODEL_POLY2, x, LAYOUT_VEC, None, y, sigma, p0, None, None, truth).astype(dtype)
+
+
+# ---------------------------------------------------------------- batched fits
+@dataclasses.dataclass
+class Batch:
+    """Many independent fits of one model, concatenated (segment offsets)."""
+    model: int
+    x: np.ndarray            # [total]  (1D models)
+    y: np.ndarray            # [total]
+    sigma: Optional[np.ndarray]
+    offsets: np.ndarray      # int64 [nfits + 1]
+    p0: np.ndarray           # [nfits, n]
+    lb: Optional[np.ndarray] # [nfits, n]
+    ub: Optional[np.ndarray]
+    truth: np.ndarray        # [nfits, n]
+
+    @property
+    def nfits(self) -> int:
+        return int(self.offsets.shape[0] - 1)
+
+    def fit(self, k: int) -> Problem:
+        a, b = int(self.offsets[k]), int(self.offsets[k + 1])
+        sig = None if self.sigma is None else self.sigma[a:b]
+        lb = None if self.lb is None else self.lb[k]
+        ub = None if self.ub is None else self.ub[k]
+        return Problem(self.model, self.x[a:b], LAYOUT_VEC, None, self.y[a:b], sig,
+                       self.p0[k].copy(), lb, ub, self.truth[k])
+
+
+def log_uniform_int(rng, lo: float, hi: float, size) -> np.ndarray:
+    return np.floor(np.exp(rng.uniform(math.log(lo), math.log(hi), size=size))).astype(np.int64)
+
+
+def dexp_batch(nfits: int = 4096, seed: int = 0, m_lo: int = 200, m_hi: int = 200_000,
+               dtype=np.float32) -> Batch:
+    """Ragged batch of double-exponential fits (m log-uniform in [m_lo, m_hi])."""
+    rng = np.random.default_rng(seed)
+    ms = log_uniform_int(rng, m_lo, m_hi, nfits)
+    offsets = np.zeros(nfits + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(ms)
+    xs, ys, p0s, truths = [], [], [], []
+    for k in range(nfits):
+        pr = dexp(int(ms[k]), seed=int(rng.integers(1 << 62)), dtype=np.float64)
+        xs.append(pr.x); ys.append(pr.y); p0s.append(pr.p0); truths.append(pr.truth)
+    lb = np.tile(np.array([-np.inf, 0.0, -np.inf, 0.0, -np.inf]), (nfits, 1))
+    ub = np.full((nfits, 5), np.inf)
+    return Batch(MODEL_DEXP, np.concatenate(xs).astype(dtype), np.concatenate(ys).astype(dtype),
+                 None, offsets, np.array(p0s), lb, ub, np.array(truths))
