@@ -1,0 +1,185 @@
+/*
+ * gbfit.h -- C ABI of the GB300 trust-region-reflective curve-fit library.
+ *
+ * The library fits h(x; p) to observations (x_i, y_i) with per-point
+ * uncertainties sigma_i by minimising f(p) = 1/2 sum_i ((h(x_i;p) - y_i)/sigma_i)^2
+ * (paper Section 2, Eqs. residual and msqe; Appendix C, Eq. explicit) with the
+ * trust-region method of Algorithms 1-3, Coleman-Li reflective bounds, and the
+ * scaled subproblem solved through the n x n factorisation of J^T J
+ * (Appendix B).  Everything after argument checking runs on one GPU: model,
+ * residual and Jacobian rows are formed in registers and reduced to J^T J,
+ * J^T r and the cost without writing J to memory; the n x n step, ratio,
+ * radius update and termination run on the device; the iteration loop is a
+ * CUDA graph with a device-set WHILE condition, so a fit makes no host round
+ * trip per iteration.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: GBFIT_OK (0) or a negative GBFIT_E_* code; the message of
+ *     the last error on the calling thread is gbfit_last_error().
+ *   - Data arrays (xdata, ydata, sigma, offsets' data) may be device pointers
+ *     (preferred; read in place, never written or freed) or host pointers
+ *     (detected with cudaPointerGetAttributes; copied to the device inside the
+ *     call, pinned host memory copies fastest).
+ *   - Parameter-sized arrays (p0, lb, ub, x_scale) and all outputs are HOST
+ *     pointers owned by the caller.
+ *   - cuda_stream is a cudaStream_t (NULL = legacy default stream).  The call
+ *     enqueues its work on that stream and returns after the results have
+ *     been copied back (one stream synchronisation per call).
+ *   - Calls on one device are serialised by an internal lock (the device
+ *     workspace and cached graphs are shared).
+ *   - Fit non-convergence is not an error: it is reported in fit_status.
+ */
+#ifndef GBFIT_H
+#define GBFIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBFIT_VERSION 1
+
+/* ---- return codes ---- */
+#define GBFIT_OK                 0
+#define GBFIT_E_INVALID_ARG     -1  /* bad id/layout/dtype, m < n, lb >= ub, non-finite p0, sigma <= 0 or non-finite data */
+#define GBFIT_E_INFEASIBLE_X0   -2  /* p0 not strictly inside (lb, ub) */
+#define GBFIT_E_OOM             -3  /* device or pinned allocation failed */
+#define GBFIT_E_BUDGET          -4  /* serving: request larger than the HBM budget */
+#define GBFIT_E_CUDA            -5  /* a CUDA runtime call failed (message has the CUDA error) */
+#define GBFIT_E_TIMEOUT         -6  /* a bounded device wait gave up */
+#define GBFIT_E_UNSUPPORTED     -7  /* valid request this build does not implement */
+
+/* ---- fit_status (per fit; mirrors the termination tests) ---- */
+#define GBFIT_FIT_NUMERICAL     -1  /* non-finite cost or Jacobian at p0 */
+#define GBFIT_FIT_MAX_NFEV       0  /* nfev reached max_nfev */
+#define GBFIT_FIT_GTOL           1  /* ||v * g||_inf < gtol */
+#define GBFIT_FIT_FTOL           2  /* accepted step with f - f_new < ftol * f */
+#define GBFIT_FIT_XTOL           3  /* step with ||w|| < xtol * (xtol + ||x||) */
+#define GBFIT_FIT_FTOL_XTOL      4  /* both on the same step */
+#define GBFIT_FIT_INVALID_DATA  -2  /* sigma <= 0 or non-finite x/y/sigma found on the device */
+
+/* ---- built-in models (model_id) ---- */
+#define GBFIT_MODEL_GAUSS1D  0  /* A exp(-(x-mu)^2/(2 s^2)) + c;          p = (A, mu, s, c)           */
+#define GBFIT_MODEL_DEXP     1  /* a1 exp(-x/t1) + a2 exp(-x/t2) + c;     p = (a1, t1, a2, t2, c)     */
+#define GBFIT_MODEL_GAUSS2D  2  /* rotated elliptical 2D Gaussian + c;     p = (A, x0, y0, sx, sy, theta, c);
+                                   u = (X-x0)cos th + (Y-y0)sin th, v = -(X-x0)sin th + (Y-y0)cos th,
+                                   h = A exp(-u^2/(2 sx^2) - v^2/(2 sy^2)) + c                          */
+#define GBFIT_MODEL_POLY2    3  /* p0 + p1 x + p2 x^2 (linear test model); p = (p0, p1, p2)           */
+#define GBFIT_NUM_MODELS     4
+#define GBFIT_MAX_PARAMS     8
+
+/* ---- x layouts ---- */
+#define GBFIT_X_VEC   0  /* xdata: [m] (1D models)                                            */
+#define GBFIT_X_SOA2  1  /* xdata: [2][m], X row then Y row (2D models)                       */
+#define GBFIT_X_GRID  2  /* xdata unused: point i is pixel X = i % W, Y = i / W, W*H == m      */
+
+/* ---- data dtypes ---- */
+#define GBFIT_F32 0
+#define GBFIT_F64 1
+
+/* ---- precision modes ---- */
+#define GBFIT_PREC_FP64   0  /* plain: model, Jacobian, reductions and solve in FP64           */
+#define GBFIT_PREC_MIXED  1  /* model and Jacobian rows in FP32 (actual reduction in the
+                                cancellation-free difference form), tile sums promoted to
+                                FP64; combine, n x n solve, ratio and tests in FP64            */
+
+typedef struct gbfit_options {
+    double ftol, xtol, gtol;   /* termination tolerances (defaults 1e-8)                         */
+    int max_nfev;              /* <= 0: 100 * n                                                  */
+    int x_scale_jac;           /* 1: D from running Jacobian column norms; 0: D = 1/x_scale      */
+    const double* x_scale;     /* host [n] or NULL (all ones); ignored when x_scale_jac          */
+    int absolute_sigma;        /* 1: pcov not rescaled by 2 cost / (m - n)                       */
+    int precision;             /* GBFIT_PREC_*                                                   */
+    int tile_points;           /* points per reduction tile; 0 = library choice                  */
+    int reserved[4];
+} gbfit_options;
+
+/* Library version (GBFIT_VERSION). */
+int gbfit_version(void);
+
+/* Message of the last failing call on this thread ("" if none).  Owned by the library. */
+const char* gbfit_last_error(void);
+
+/* Fill *opt with defaults (tolerances 1e-8, mixed precision, D = I). */
+int gbfit_default_options(gbfit_options* opt);
+
+/* Registry query: number of parameters and coordinate dimensions of model_id. */
+int gbfit_model_info(int model_id, int* n_params, int* x_dims);
+
+/*
+ * One fit (paper Section 2, Algorithm 1; the SciPy-style problem statement the
+ * paper's drop-in claim refers to).
+ *   model_id   GBFIT_MODEL_*
+ *   xdata      coordinates in x_layout (NULL for GBFIT_X_GRID), dtype
+ *   m          number of points (>= n)
+ *   x_layout   GBFIT_X_*; grid_wh = host int64[2] {W, H} for GBFIT_X_GRID, else NULL
+ *   ydata      [m] observations, dtype
+ *   sigma      [m] per-point standard deviations (> 0, Appendix C Eq. svector) or NULL (= 1)
+ *   dtype      GBFIT_F32 | GBFIT_F64 (applies to xdata, ydata, sigma)
+ *   p0         host [n] start, strictly inside (lb, ub)
+ *   lb, ub     host [n] bounds (+-INFINITY for none) or NULL (unbounded)
+ *   opt        options or NULL (defaults)
+ * Outputs (host): popt [n]; pcov [n*n] row-major or NULL; cost = f(popt);
+ *   nfev (function evaluations, including the one at p0); fit_status GBFIT_FIT_*.
+ * Errors: GBFIT_E_INVALID_ARG, GBFIT_E_INFEASIBLE_X0, GBFIT_E_OOM, GBFIT_E_CUDA.
+ */
+int gbfit_curve_fit(int model_id,
+                    const void* xdata, int64_t m, int x_layout, const int64_t* grid_wh,
+                    const void* ydata, const void* sigma, int dtype,
+                    const double* p0, const double* lb, const double* ub,
+                    const gbfit_options* opt,
+                    double* popt, double* pcov, double* cost, int* nfev, int* fit_status,
+                    void* cuda_stream);
+
+/*
+ * Many independent fits of one model over concatenated data (paper Appendix A's
+ * fixed-size padding replaced by segment offsets: no point of one fit touches
+ * another).  All fits iterate together: each graph round evaluates every
+ * running fit once, in shared launches, and a fit that has finished takes no
+ * further work.  A fit's reduction tiling depends only on its own m, so its
+ * result is bit-identical alone and in any batch.
+ *   nfits      number of fits (>= 1)
+ *   offsets    host int64 [nfits + 1], offsets[0] = 0, strictly increasing by >= n
+ *   xdata      [total] (GBFIT_X_VEC) or [2][total] (GBFIT_X_SOA2)
+ *   ydata, sigma  [total] (sigma may be NULL)
+ *   p0         host [nfits * n];  lb, ub host [nfits * n] or NULL
+ * Outputs (host, per fit): popt [nfits*n], pcov [nfits*n*n] or NULL, cost [nfits],
+ *   nfev [nfits], fit_status [nfits].
+ */
+int gbfit_curve_fit_batch(int model_id, int nfits, const int64_t* offsets,
+                          const void* xdata, int x_layout,
+                          const void* ydata, const void* sigma, int dtype,
+                          const double* p0, const double* lb, const double* ub,
+                          const gbfit_options* opt,
+                          double* popt, double* pcov, double* cost, int* nfev, int* fit_status,
+                          void* cuda_stream);
+
+/*
+ * Evaluate the fused reduction once at parameters p (no iteration): the
+ * packed upper triangle of B = J^T J (n(n+1)/2), g = J^T r (n) and cost
+ * f = r^T r / 2, all FP64, for the given precision mode (paper Eqs. msqe,
+ * gradient, hessian).  Output is a host array out[n(n+1)/2 + n + 1].
+ */
+int gbfit_evaluate(int model_id,
+                   const void* xdata, int64_t m, int x_layout, const int64_t* grid_wh,
+                   const void* ydata, const void* sigma, int dtype,
+                   const double* p, int precision, int tile_points,
+                   double* out, void* cuda_stream);
+
+/*
+ * Solve one scaled trust-region subproblem on the device (paper Algorithm 1's
+ * step with Algorithm 2; Appendix B): given the symmetric n x n B (host,
+ * row-major), g [n], radius Delta and the previous LM parameter alpha0,
+ * returns p [n] minimising g.p + p^T B p / 2 within ||p|| <= Delta (to
+ * Algorithm 2's accuracy), the LM parameter alpha and the eigenvalues lam [n]
+ * (ascending order not guaranteed).  Runs the same device code as the fit.
+ */
+int gbfit_tr_subproblem(int n, const double* B, const double* g, double Delta, double alpha0,
+                        double* p, double* alpha, double* lam, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBFIT_H */

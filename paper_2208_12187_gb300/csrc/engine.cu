@@ -1,0 +1,594 @@
+// Host side of libgbfit: argument checking, device workspace, the cached
+// iteration graph and the extern "C" entry points declared in gbfit.h.
+//
+// One fit or a batch of fits runs as ONE graph launch:
+//   init_fits_kernel (pass constants at p0)
+//   WHILE (any fit running && rounds < cap) {
+//       eval_round_kernel x UNROLL      (one TRF iteration of every running fit each)
+//       round_end_kernel                (sets the WHILE condition)
+//   }
+// followed by one device-to-host copy of the per-fit results.  Several
+// iterations per WHILE trip amortise the conditional node (~5 us per trip on
+// GB300 against ~0.6 us per chained kernel node); an iteration launched after
+// a fit has finished costs that fit nothing but an early exit.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gbfit.h"
+#include "kernels.cuh"
+#include "models.cuh"
+
+using namespace gbfit;
+
+namespace {
+
+constexpr int UNROLL = 4;
+constexpr int TILE_MIN = 2048, TILE_MAX = 16384, TILE_SPLIT = 304;
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(x)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (x);                                                                \
+        if (e_ != cudaSuccess) return fail(GBFIT_E_CUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+int grow_dev(T*& p, size_t& cap, size_t need, bool& changed) {
+    if (need <= cap && p) return GBFIT_OK;
+    size_t n = need > 16 ? need + need / 2 : 16;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc((void**)&p, n * sizeof(T));
+    if (e != cudaSuccess) { p = nullptr; return fail(GBFIT_E_OOM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e)); }
+    cap = n;
+    changed = true;
+    return GBFIT_OK;
+}
+
+struct Ctx {
+    int device = -1, sms = 0, grid = 0;
+    std::mutex mu;
+    FitDesc* desc = nullptr; size_t cap_fits = 0;
+    FitState* state = nullptr; size_t cap_state = 0;
+    FitResult* results = nullptr; size_t cap_res = 0;
+    int* fit_cnt = nullptr; size_t cap_fcnt = 0;
+    WorkItem* items = nullptr; size_t cap_items = 0;
+    float* tile_part = nullptr; size_t cap_tp = 0;
+    double* tile_part_d = nullptr; size_t cap_tpd = 0;
+    double* group_part = nullptr; size_t cap_gp = 0;
+    int* group_cnt = nullptr; size_t cap_gc = 0;
+    int* scalars = nullptr;       // n_items, running, rounds, max_rounds, nfits
+    double* wbuf = nullptr; size_t cap_w = 0;
+    char* databuf = nullptr; size_t cap_data = 0;
+    double* small = nullptr;      // subproblem scratch
+    // pinned host staging
+    char* hbuf = nullptr; size_t hcap = 0;
+    // graphs per precision
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+
+    Engine engine() const {
+        Engine E;
+        E.desc = desc; E.state = state; E.items = items; E.n_items = scalars + 0;
+        E.tile_part = tile_part; E.tile_part_d = tile_part_d; E.group_part = group_part;
+        E.group_cnt = group_cnt; E.fit_cnt = fit_cnt; E.running = scalars + 1; E.rounds = scalars + 2;
+        E.max_rounds = scalars + 3; E.nfits_dev = scalars + 4;
+        return E;
+    }
+    void drop_graphs() {
+        for (int p = 0; p < 2; ++p) {
+            if (exec[p]) cudaGraphExecDestroy(exec[p]);
+            if (graph[p]) cudaGraphDestroy(graph[p]);
+            exec[p] = nullptr; graph[p] = nullptr;
+        }
+    }
+    int pinned(size_t need) {
+        if (need <= hcap) return GBFIT_OK;
+        if (hbuf) cudaFreeHost(hbuf);
+        hbuf = nullptr; hcap = 0;
+        size_t n = need + need / 2 + 4096;
+        cudaError_t e = cudaMallocHost((void**)&hbuf, n);
+        if (e != cudaSuccess) return fail(GBFIT_E_OOM, "cudaMallocHost(%zu): %s", n, cudaGetErrorString(e));
+        hcap = n;
+        return GBFIT_OK;
+    }
+};
+
+std::mutex g_ctx_mu;
+Ctx* g_ctx[64] = {};
+
+int get_ctx(Ctx** out) {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(GBFIT_E_CUDA, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> g(g_ctx_mu);
+    if (!g_ctx[dev]) {
+        Ctx* c = new Ctx();
+        c->device = dev;
+        cudaDeviceProp prop;
+        cudaError_t e = cudaGetDeviceProperties(&prop, dev);
+        if (e != cudaSuccess) { delete c; return fail(GBFIT_E_CUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e)); }
+        c->sms = prop.multiProcessorCount;
+        int b0 = eval_blocks_per_sm(PREC_FP64), b1 = eval_blocks_per_sm(PREC_MIXED);
+        int b = b0 < b1 ? b0 : b1;
+        if (b < 1) b = 1;
+        c->grid = c->sms * b;
+        e = cudaMalloc((void**)&c->scalars, 16 * sizeof(int));
+        if (e != cudaSuccess) { delete c; return fail(GBFIT_E_OOM, "cudaMalloc: %s", cudaGetErrorString(e)); }
+        e = cudaMalloc((void**)&c->small, 256 * sizeof(double));
+        if (e != cudaSuccess) { delete c; return fail(GBFIT_E_OOM, "cudaMalloc: %s", cudaGetErrorString(e)); }
+        g_ctx[dev] = c;
+    }
+    *out = g_ctx[dev];
+    return GBFIT_OK;
+}
+
+int ensure(Ctx* c, size_t nfits, size_t ntiles, size_t ngroups, size_t nitems) {
+    bool changed = false;
+    int rc;
+    if ((rc = grow_dev(c->desc, c->cap_fits, nfits, changed))) return rc;
+    if ((rc = grow_dev(c->state, c->cap_state, nfits, changed))) return rc;
+    if ((rc = grow_dev(c->results, c->cap_res, nfits, changed))) return rc;
+    if ((rc = grow_dev(c->fit_cnt, c->cap_fcnt, nfits, changed))) return rc;
+    if ((rc = grow_dev(c->items, c->cap_items, nitems, changed))) return rc;
+    if ((rc = grow_dev(c->tile_part, c->cap_tp, ntiles * KMAX, changed))) return rc;
+    if ((rc = grow_dev(c->tile_part_d, c->cap_tpd, ntiles * KMAX, changed))) return rc;
+    if ((rc = grow_dev(c->group_part, c->cap_gp, ngroups * KMAX, changed))) return rc;
+    if ((rc = grow_dev(c->group_cnt, c->cap_gc, ngroups, changed))) return rc;
+    if (changed) c->drop_graphs();
+    return GBFIT_OK;
+}
+
+template <int P>
+int build_graph(Ctx* c) {
+    if (c->exec[P]) return GBFIT_OK;
+    cudaGraph_t g;
+    CUDA_TRY(cudaGraphCreate(&g, 0));
+    Engine E = c->engine();
+    FitResult* res = c->results;
+    cudaGraphNode_t n_init;
+    {
+        void* args[] = {&E};
+        cudaKernelNodeParams kp = {};
+        kp.func = kernel_init_fits(P);
+        kp.gridDim = dim3(256);
+        kp.blockDim = dim3(32);
+        kp.kernelParams = args;
+        CUDA_TRY(cudaGraphAddKernelNode(&n_init, g, nullptr, 0, &kp));
+    }
+    cudaGraphConditionalHandle h;
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t n_cond;
+    CUDA_TRY(cudaGraphAddNode(&n_cond, g, &n_init, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaGraphNode_t prev = nullptr;
+    for (int u = 0; u < UNROLL; ++u) {
+        void* args[] = {&E, &res};
+        cudaKernelNodeParams kp = {};
+        kp.func = kernel_eval_round(P);
+        kp.gridDim = dim3(c->grid);
+        kp.blockDim = dim3(EVAL_THREADS);
+        kp.kernelParams = args;
+        cudaGraphNode_t nn;
+        CUDA_TRY(cudaGraphAddKernelNode(&nn, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+        prev = nn;
+    }
+    {
+        void* args[] = {&E, &h};
+        cudaKernelNodeParams kp = {};
+        kp.func = kernel_round_end();
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(1);
+        kp.kernelParams = args;
+        cudaGraphNode_t nn;
+        CUDA_TRY(cudaGraphAddKernelNode(&nn, body, &prev, 1, &kp));
+    }
+    cudaGraphExec_t ex;
+    CUDA_TRY(cudaGraphInstantiate(&ex, g, 0));
+    c->graph[P] = g;
+    c->exec[P] = ex;
+    return GBFIT_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int choose_tile(int64_t m, int user) {
+    if (user > 0) return ((user + EVAL_THREADS - 1) / EVAL_THREADS) * EVAL_THREADS;
+    int64_t t = (m + TILE_SPLIT - 1) / TILE_SPLIT;
+    t = ((t + EVAL_THREADS - 1) / EVAL_THREADS) * EVAL_THREADS;
+    if (t < TILE_MIN) t = TILE_MIN;
+    if (t > TILE_MAX) t = TILE_MAX;
+    return (int)t;
+}
+
+struct FitArgs {
+    int model, n, layout, dtype;
+    int64_t m, grid_w;
+    const void *x, *x2, *y, *sigma;
+    const double *p0, *lb, *ub;
+};
+
+int check_params(const FitArgs& a, bool* bounded) {
+    *bounded = false;
+    for (int i = 0; i < a.n; ++i) {
+        if (!std::isfinite(a.p0[i])) return fail(GBFIT_E_INVALID_ARG, "p0[%d] is not finite", i);
+        double lo = a.lb ? a.lb[i] : -INFINITY, hi = a.ub ? a.ub[i] : INFINITY;
+        if (std::isnan(lo) || std::isnan(hi)) return fail(GBFIT_E_INVALID_ARG, "bound %d is NaN", i);
+        if (!(lo < hi)) return fail(GBFIT_E_INVALID_ARG, "lb[%d] >= ub[%d]", i, i);
+        if (std::isfinite(lo) || std::isfinite(hi)) *bounded = true;
+        if (!(a.p0[i] > lo && a.p0[i] < hi))
+            return fail(GBFIT_E_INFEASIBLE_X0, "p0[%d] = %g is not strictly inside (%g, %g)", i, a.p0[i], lo, hi);
+    }
+    return GBFIT_OK;
+}
+
+int check_opts(const gbfit_options* o, int n) {
+    if (!(o->ftol >= 0) || !(o->xtol >= 0) || !(o->gtol >= 0)) return fail(GBFIT_E_INVALID_ARG, "tolerances must be >= 0");
+    if (o->precision != GBFIT_PREC_FP64 && o->precision != GBFIT_PREC_MIXED) return fail(GBFIT_E_INVALID_ARG, "unknown precision %d", o->precision);
+    if (o->x_scale && !o->x_scale_jac)
+        for (int i = 0; i < n; ++i)
+            if (!(o->x_scale[i] > 0) || !std::isfinite(o->x_scale[i])) return fail(GBFIT_E_INVALID_ARG, "x_scale[%d] must be > 0", i);
+    if (o->tile_points < 0 || o->tile_points > (1 << 24)) return fail(GBFIT_E_INVALID_ARG, "tile_points out of range");
+    return GBFIT_OK;
+}
+
+gbfit_options defaults() {
+    gbfit_options o;
+    memset(&o, 0, sizeof o);
+    o.ftol = o.xtol = o.gtol = 1e-8;
+    o.precision = GBFIT_PREC_MIXED;
+    return o;
+}
+
+// Run nfits fits whose descriptors (data pointers already on the device) are
+// in hd[]; writes per-fit results into hr[].
+int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::vector<double>>& p0s,
+             std::vector<FitResult>& hr, cudaStream_t s, int* rounds_out) {
+    size_t nf = hd.size();
+    size_t ntiles = 0, ngroups = 0;
+    int max_nfev = 1;
+    for (auto& d : hd) {
+        d.tile_base = (int64_t)ntiles;
+        d.group_base = (int64_t)ngroups;
+        ntiles += d.n_tiles;
+        ngroups += d.n_groups;
+        if (d.max_nfev > max_nfev) max_nfev = d.max_nfev;
+    }
+    int rc;
+    if ((rc = ensure(c, nf, ntiles, ngroups, ntiles))) return rc;
+    if (prec == PREC_MIXED) { if ((rc = build_graph<PREC_MIXED>(c))) return rc; }
+    else { if ((rc = build_graph<PREC_FP64>(c))) return rc; }
+    size_t off_desc = 0, off_state = off_desc + nf * sizeof(FitDesc);
+    size_t off_items = off_state + nf * sizeof(FitState);
+    size_t off_sc = off_items + ntiles * sizeof(WorkItem);
+    size_t off_res = off_sc + 16 * sizeof(int);
+    size_t total = off_res + nf * sizeof(FitResult);
+    if ((rc = c->pinned(total))) return rc;
+    char* hb = c->hbuf;
+    memcpy(hb + off_desc, hd.data(), nf * sizeof(FitDesc));
+    FitState* hs = (FitState*)(hb + off_state);
+    memset(hs, 0, nf * sizeof(FitState));
+    WorkItem* hi = (WorkItem*)(hb + off_items);
+    size_t k = 0;
+    for (size_t f = 0; f < nf; ++f) {
+        FitState& st = hs[f];
+        st.run = RS_RUNNING;
+        st.phase = PH_INIT;
+        for (int i = 0; i < hd[f].n; ++i) { st.x[i] = p0s[f][i]; st.xt[i] = p0s[f][i]; st.scale_inv[i] = 1.0; }
+        for (int t = 0; t < hd[f].n_tiles; ++t) hi[k++] = WorkItem{(int)f, t};
+    }
+    int* sc = (int*)(hb + off_sc);
+    memset(sc, 0, 16 * sizeof(int));
+    sc[0] = (int)ntiles;
+    sc[1] = (int)nf;
+    sc[2] = 0;
+    sc[3] = (max_nfev + 2) / UNROLL + 3;
+    sc[4] = (int)nf;
+    CUDA_TRY(cudaMemcpyAsync(c->desc, hb + off_desc, nf * sizeof(FitDesc), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->state, hb + off_state, nf * sizeof(FitState), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->items, hb + off_items, ntiles * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->scalars, sc, 16 * sizeof(int), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(c->group_cnt, 0, ngroups * sizeof(int), s));
+    CUDA_TRY(cudaMemsetAsync(c->fit_cnt, 0, nf * sizeof(int), s));
+    CUDA_TRY(cudaGraphLaunch(c->exec[prec], s));
+    CUDA_TRY(cudaMemcpyAsync(hb + off_res, c->results, nf * sizeof(FitResult), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(sc, c->scalars, 16 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    hr.resize(nf);
+    memcpy(hr.data(), hb + off_res, nf * sizeof(FitResult));
+    if (rounds_out) *rounds_out = sc[2];
+    if (sc[1] != 0) return fail(GBFIT_E_TIMEOUT, "%d fit(s) still running after the round cap", sc[1]);
+    return GBFIT_OK;
+}
+
+// Stage data arrays that live in host memory into the device buffer.
+struct Staged {
+    const void *x = nullptr, *x2 = nullptr, *y = nullptr, *sigma = nullptr;
+};
+
+int stage_data(Ctx* c, const void* x, size_t xbytes, const void* y, size_t ybytes, const void* sg, size_t sbytes,
+               cudaStream_t s, Staged* out) {
+    bool hx = x && !is_device_ptr(x), hy = !is_device_ptr(y), hsg = sg && !is_device_ptr(sg);
+    out->x = x; out->y = y; out->sigma = sg;
+    size_t need = (hx ? xbytes + 256 : 0) + (hy ? ybytes + 256 : 0) + (hsg ? sbytes + 256 : 0);
+    if (need == 0) return GBFIT_OK;
+    bool changed = false;
+    int rc = grow_dev(c->databuf, c->cap_data, need, changed);
+    if (rc) return rc;
+    size_t off = 0;
+    auto put = [&](const void* src, size_t nb, const void** dst) -> int {
+        char* d = c->databuf + off;
+        CUDA_TRY(cudaMemcpyAsync(d, src, nb, cudaMemcpyHostToDevice, s));
+        *dst = d;
+        off += (nb + 255) / 256 * 256;
+        return GBFIT_OK;
+    };
+    if (hx && (rc = put(x, xbytes, &out->x))) return rc;
+    if (hy && (rc = put(y, ybytes, &out->y))) return rc;
+    if (hsg && (rc = put(sg, sbytes, &out->sigma))) return rc;
+    return GBFIT_OK;
+}
+
+int fill_desc(FitDesc& d, const FitArgs& a, const gbfit_options& o, bool bounded, int64_t m, int tile_user) {
+    memset(&d, 0, sizeof d);
+    d.model = a.model; d.n = a.n; d.layout = a.layout; d.dtype = a.dtype;
+    d.prec = o.precision; d.bounded = bounded ? 1 : 0; d.jac_scale = o.x_scale_jac ? 1 : 0;
+    d.m = m; d.grid_w = a.grid_w;
+    d.tile_points = choose_tile(m, tile_user);
+    d.n_tiles = (int)((m + d.tile_points - 1) / d.tile_points);
+    d.n_groups = (d.n_tiles + GROUP_TILES - 1) / GROUP_TILES;
+    d.max_nfev = o.max_nfev > 0 ? o.max_nfev : 100 * a.n;
+    for (int i = 0; i < NMAX; ++i) {
+        d.lb[i] = (a.lb && i < a.n) ? a.lb[i] : -INFINITY;
+        d.ub[i] = (a.ub && i < a.n) ? a.ub[i] : INFINITY;
+        d.xscale[i] = (o.x_scale && i < a.n && !o.x_scale_jac) ? o.x_scale[i] : 1.0;
+    }
+    d.ftol = o.ftol; d.xtol = o.xtol; d.gtol = o.gtol;
+    d.absolute_sigma = o.absolute_sigma;
+    return GBFIT_OK;
+}
+
+// Set data pointers and weights of d (after staging); plain path stages w = 1/sigma.
+int set_data(Ctx* c, FitDesc& d, const void* x, const void* x2, const void* y, const void* sigma,
+             int64_t w_offset, cudaStream_t s) {
+    d.x = x; d.x2 = x2; d.y = y;
+    if (!sigma) { d.wkind = W_NONE; d.w = nullptr; return GBFIT_OK; }
+    if (d.prec == PREC_MIXED) { d.wkind = W_SIGMA; d.w = sigma; return GBFIT_OK; }
+    d.wkind = W_ARRAY;              // staged FP64 w = 1/sigma
+    d.w = c->wbuf + w_offset;
+    return GBFIT_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+int gbfit_version(void) { return GBFIT_VERSION; }
+
+const char* gbfit_last_error(void) { return g_err.c_str(); }
+
+int gbfit_default_options(gbfit_options* opt) {
+    if (!opt) return fail(GBFIT_E_INVALID_ARG, "opt is NULL");
+    *opt = defaults();
+    return GBFIT_OK;
+}
+
+int gbfit_model_info(int model_id, int* n_params, int* x_dims) {
+    if (model_id < 0 || model_id >= GBFIT_NUM_MODELS) return fail(GBFIT_E_INVALID_ARG, "unknown model %d", model_id);
+    if (n_params) *n_params = model_nparams(model_id);
+    if (x_dims) *x_dims = model_xdims(model_id);
+    return GBFIT_OK;
+}
+
+static int check_common(int model_id, int x_layout, int dtype, const void* ydata, int* n) {
+    if (model_id < 0 || model_id >= GBFIT_NUM_MODELS) return fail(GBFIT_E_INVALID_ARG, "unknown model %d", model_id);
+    *n = model_nparams(model_id);
+    int xd = model_xdims(model_id);
+    if (dtype != GBFIT_F32 && dtype != GBFIT_F64) return fail(GBFIT_E_INVALID_ARG, "unknown dtype %d", dtype);
+    if (xd == 1 && x_layout != GBFIT_X_VEC) return fail(GBFIT_E_INVALID_ARG, "1D model needs GBFIT_X_VEC");
+    if (xd == 2 && x_layout != GBFIT_X_SOA2 && x_layout != GBFIT_X_GRID)
+        return fail(GBFIT_E_INVALID_ARG, "2D model needs GBFIT_X_SOA2 or GBFIT_X_GRID");
+    if (!ydata) return fail(GBFIT_E_INVALID_ARG, "ydata is NULL");
+    return GBFIT_OK;
+}
+
+// Shared body of gbfit_curve_fit and gbfit_evaluate (single fit).
+static int single_fit(int model_id, const void* xdata, int64_t m, int x_layout, const int64_t* grid_wh,
+                      const void* ydata, const void* sigma, int dtype, const double* p0, const double* lb,
+                      const double* ub, const gbfit_options* opt_in, FitResult* out, void* cuda_stream,
+                      bool eval_only) {
+    int n, rc;
+    if ((rc = check_common(model_id, x_layout, dtype, ydata, &n))) return rc;
+    gbfit_options o = opt_in ? *opt_in : defaults();
+    if ((rc = check_opts(&o, n))) return rc;
+    if (m < n) return fail(GBFIT_E_INVALID_ARG, "m = %lld < n = %d", (long long)m, n);
+    if (m > ((int64_t)1 << 40)) return fail(GBFIT_E_INVALID_ARG, "m too large");
+    int64_t gw = 0;
+    if (x_layout == GBFIT_X_GRID) {
+        if (!grid_wh || grid_wh[0] <= 0 || grid_wh[1] <= 0 || grid_wh[0] * grid_wh[1] != m)
+            return fail(GBFIT_E_INVALID_ARG, "grid_wh must give W*H == m");
+        gw = grid_wh[0];
+    } else if (!xdata) {
+        return fail(GBFIT_E_INVALID_ARG, "xdata is NULL");
+    }
+    if (!p0) return fail(GBFIT_E_INVALID_ARG, "p0 is NULL");
+    FitArgs a{model_id, n, x_layout, dtype, m, gw, xdata, nullptr, ydata, sigma, p0, lb, ub};
+    bool bounded;
+    if ((rc = check_params(a, &bounded))) return rc;
+    if (eval_only) { bounded = false; o.max_nfev = 1; }
+    Ctx* c;
+    if ((rc = get_ctx(&c))) return rc;
+    std::lock_guard<std::mutex> lock(c->mu);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    size_t es = dtype == GBFIT_F64 ? 8 : 4;
+    size_t xbytes = x_layout == GBFIT_X_GRID ? 0 : (size_t)m * es * (x_layout == GBFIT_X_SOA2 ? 2 : 1);
+    Staged sd;
+    if ((rc = stage_data(c, x_layout == GBFIT_X_GRID ? nullptr : xdata, xbytes, ydata, (size_t)m * es, sigma,
+                         (size_t)m * es, s, &sd))) return rc;
+    std::vector<FitDesc> hd(1);
+    fill_desc(hd[0], a, o, bounded, m, o.tile_points);
+    const void* x2 = (x_layout == GBFIT_X_SOA2) ? (const char*)sd.x + (size_t)m * es : nullptr;
+    if (sigma && o.precision == GBFIT_PREC_FP64) {
+        bool changed = false;
+        if ((rc = grow_dev(c->wbuf, c->cap_w, (size_t)m, changed))) return rc;
+        CUDA_TRY(launch_stage_weights(dtype == GBFIT_F64, sd.sigma, c->wbuf, m, c->sms * 8, s));
+    }
+    set_data(c, hd[0], sd.x, x2, sd.y, sd.sigma, 0, s);
+    std::vector<std::vector<double>> p0s(1, std::vector<double>(p0, p0 + n));
+    std::vector<FitResult> hr;
+    int rounds = 0;
+    rc = run_fits(c, o.precision, hd, p0s, hr, s, &rounds);
+    if (rc) return rc;
+    *out = hr[0];
+    out->rounds = rounds;
+    if (out->fit_status == -2) return fail(GBFIT_E_INVALID_ARG, "sigma <= 0 or non-finite x/y/sigma in the data");
+    return GBFIT_OK;
+}
+
+int gbfit_curve_fit(int model_id, const void* xdata, int64_t m, int x_layout, const int64_t* grid_wh,
+                    const void* ydata, const void* sigma, int dtype, const double* p0, const double* lb,
+                    const double* ub, const gbfit_options* opt, double* popt, double* pcov, double* cost,
+                    int* nfev, int* fit_status, void* cuda_stream) {
+    FitResult r;
+    int rc = single_fit(model_id, xdata, m, x_layout, grid_wh, ydata, sigma, dtype, p0, lb, ub, opt, &r,
+                        cuda_stream, false);
+    if (rc) return rc;
+    int n = model_nparams(model_id);
+    if (popt) for (int i = 0; i < n; ++i) popt[i] = r.popt[i];
+    if (pcov) for (int i = 0; i < n * n; ++i) pcov[i] = r.pcov[i];
+    if (cost) *cost = r.cost;
+    if (nfev) *nfev = r.nfev;
+    if (fit_status) *fit_status = r.fit_status;
+    return GBFIT_OK;
+}
+
+int gbfit_evaluate(int model_id, const void* xdata, int64_t m, int x_layout, const int64_t* grid_wh,
+                   const void* ydata, const void* sigma, int dtype, const double* p, int precision,
+                   int tile_points, double* out, void* cuda_stream) {
+    gbfit_options o = defaults();
+    o.precision = precision;
+    o.tile_points = tile_points;
+    FitResult r;
+    int rc = single_fit(model_id, xdata, m, x_layout, grid_wh, ydata, sigma, dtype, p, nullptr, nullptr, &o, &r,
+                        cuda_stream, true);
+    if (rc) return rc;
+    int n = model_nparams(model_id);
+    int K = n_tri(n) + n + 1;
+    for (int k = 0; k < K; ++k) out[k] = r.tot[k];
+    out[K - 1] = 0.5 * r.tot[K - 1];
+    return GBFIT_OK;
+}
+
+int gbfit_curve_fit_batch(int model_id, int nfits, const int64_t* offsets, const void* xdata, int x_layout,
+                          const void* ydata, const void* sigma, int dtype, const double* p0, const double* lb,
+                          const double* ub, const gbfit_options* opt_in, double* popt, double* pcov, double* cost,
+                          int* nfev, int* fit_status, void* cuda_stream) {
+    int n, rc;
+    if ((rc = check_common(model_id, x_layout, dtype, ydata, &n))) return rc;
+    if (x_layout == GBFIT_X_GRID) return fail(GBFIT_E_UNSUPPORTED, "batched fits take explicit coordinates");
+    if (nfits < 1 || !offsets || !xdata || !p0) return fail(GBFIT_E_INVALID_ARG, "bad batch arguments");
+    gbfit_options o = opt_in ? *opt_in : defaults();
+    if ((rc = check_opts(&o, n))) return rc;
+    if (offsets[0] != 0) return fail(GBFIT_E_INVALID_ARG, "offsets[0] must be 0");
+    for (int f = 0; f < nfits; ++f)
+        if (offsets[f + 1] - offsets[f] < n) return fail(GBFIT_E_INVALID_ARG, "fit %d has fewer than n points", f);
+    int64_t total = offsets[nfits];
+    std::vector<bool> bnd(nfits);
+    for (int f = 0; f < nfits; ++f) {
+        FitArgs a{model_id, n, x_layout, dtype, offsets[f + 1] - offsets[f], 0, nullptr, nullptr, ydata, sigma,
+                  p0 + (size_t)f * n, lb ? lb + (size_t)f * n : nullptr, ub ? ub + (size_t)f * n : nullptr};
+        bool b;
+        if ((rc = check_params(a, &b))) return fail(rc, "fit %d: %s", f, g_err.c_str());
+        bnd[f] = b;
+    }
+    Ctx* c;
+    if ((rc = get_ctx(&c))) return rc;
+    std::lock_guard<std::mutex> lock(c->mu);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    size_t es = dtype == GBFIT_F64 ? 8 : 4;
+    size_t xbytes = (size_t)total * es * (x_layout == GBFIT_X_SOA2 ? 2 : 1);
+    Staged sd;
+    if ((rc = stage_data(c, xdata, xbytes, ydata, (size_t)total * es, sigma, (size_t)total * es, s, &sd))) return rc;
+    if (sigma && o.precision == GBFIT_PREC_FP64) {
+        bool changed = false;
+        if ((rc = grow_dev(c->wbuf, c->cap_w, (size_t)total, changed))) return rc;
+        CUDA_TRY(launch_stage_weights(dtype == GBFIT_F64, sd.sigma, c->wbuf, total, c->sms * 8, s));
+    }
+    std::vector<FitDesc> hd(nfits);
+    std::vector<std::vector<double>> p0s(nfits);
+    for (int f = 0; f < nfits; ++f) {
+        int64_t a0 = offsets[f], mf = offsets[f + 1] - offsets[f];
+        FitArgs a{model_id, n, x_layout, dtype, mf, 0, nullptr, nullptr, ydata, sigma,
+                  p0 + (size_t)f * n, lb ? lb + (size_t)f * n : nullptr, ub ? ub + (size_t)f * n : nullptr};
+        fill_desc(hd[f], a, o, bnd[f], mf, o.tile_points);
+        const char* xb = (const char*)sd.x + a0 * es;
+        const void* x2 = x_layout == GBFIT_X_SOA2 ? (const char*)sd.x + (total + a0) * es : nullptr;
+        set_data(c, hd[f], xb, x2, (const char*)sd.y + a0 * es, sigma ? (const char*)sd.sigma + a0 * es : nullptr, a0, s);
+        p0s[f].assign(p0 + (size_t)f * n, p0 + (size_t)(f + 1) * n);
+    }
+    std::vector<FitResult> hr;
+    rc = run_fits(c, o.precision, hd, p0s, hr, s, nullptr);
+    if (rc) return rc;
+    for (int f = 0; f < nfits; ++f) {
+        const FitResult& r = hr[f];
+        if (popt) for (int i = 0; i < n; ++i) popt[(size_t)f * n + i] = r.popt[i];
+        if (pcov) for (int i = 0; i < n * n; ++i) pcov[(size_t)f * n * n + i] = r.pcov[i];
+        if (cost) cost[f] = r.cost;
+        if (nfev) nfev[f] = r.nfev;
+        if (fit_status) fit_status[f] = r.fit_status;
+    }
+    return GBFIT_OK;
+}
+
+int gbfit_tr_subproblem(int n, const double* B, const double* g, double Delta, double alpha0, double* p,
+                        double* alpha, double* lam, void* cuda_stream) {
+    if (n < 1 || n > NMAX || !B || !g || !p || !alpha || !lam) return fail(GBFIT_E_INVALID_ARG, "bad subproblem arguments");
+    if (!(Delta > 0)) return fail(GBFIT_E_INVALID_ARG, "Delta must be > 0");
+    Ctx* c;
+    int rc;
+    if ((rc = get_ctx(&c))) return rc;
+    std::lock_guard<std::mutex> lock(c->mu);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    double* d = c->small;
+    if ((rc = c->pinned(256 * sizeof(double)))) return rc;
+    double* h = (double*)c->hbuf;
+    memcpy(h, B, n * n * sizeof(double));
+    memcpy(h + 64, g, n * sizeof(double));
+    CUDA_TRY(cudaMemcpyAsync(d, h, 72 * sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(launch_tr_subproblem(n, d, d + 64, Delta, alpha0, d + 80, d + 88, d + 96, s));
+    CUDA_TRY(cudaMemcpyAsync(h + 80, d + 80, 24 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < n; ++i) { p[i] = h[80 + i]; lam[i] = h[96 + i]; }
+    *alpha = h[88];
+    return GBFIT_OK;
+}
+
+}  // extern "C"

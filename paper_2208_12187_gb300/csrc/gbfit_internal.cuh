@@ -1,0 +1,92 @@
+// Internal device/host data structures of libgbfit (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gbfit {
+
+constexpr int NMAX = 8;                          // max parameters (rotated 2D Gaussian has 7)
+constexpr int NTMAX = NMAX * (NMAX + 1) / 2;     // packed upper triangle size
+constexpr int KMAX = NTMAX + NMAX + 3;           // accumulator slots per evaluation
+constexpr int EVAL_THREADS = 256;                // threads per reduction CTA
+constexpr int GROUP_TILES = 32;                  // tiles per first-level combine group
+constexpr int PF = 32;                           // float pass constants (mixed)
+constexpr int PD = 16;                           // double pass constants (plain)
+
+enum Prec { PREC_FP64 = 0, PREC_MIXED = 1 };
+enum Layout { X_VEC = 0, X_SOA2 = 1, X_GRID = 2 };
+enum DType { F32 = 0, F64 = 1 };
+enum WKind { W_NONE = 0, W_ARRAY = 1, W_SIGMA = 2 };
+enum RunState { RS_RUNNING = 0, RS_DONE = 1 };
+enum Phase { PH_INIT = 0, PH_TRIAL = 1 };
+
+// Accumulator slot layout for a model with n parameters (NT = n(n+1)/2):
+//   [0, NT)        packed upper triangle of J'^T J' at the evaluated point
+//   [NT, NT+n)     J'^T r'
+//   NT+n           sum r'^2                        (= 2 f at the evaluated point)
+//   NT+n+1         sum dr (2 r + dr)   mixed only  (= 2 (f' - f), cancellation-free)
+//   NT+n+2         sum r^2             mixed only  (= 2 f at the base point)
+__host__ __device__ constexpr int n_tri(int n) { return n * (n + 1) / 2; }
+__host__ __device__ constexpr int n_acc(int n, int prec) { return n_tri(n) + n + (prec == PREC_MIXED ? 3 : 1); }
+
+// Immutable description of one fit (uploaded once).
+struct FitDesc {
+    int model, n, layout, dtype;
+    int prec, wkind, bounded, jac_scale;
+    int64_t m;
+    int64_t grid_w;
+    const void* x;         // VEC: [m]; SOA2: X row at x, Y row at x2
+    const void* x2;
+    const void* y;
+    const void* w;         // staged weights (plain) or sigma (mixed) or null
+    int tile_points, n_tiles, n_groups, max_nfev;
+    int64_t tile_base;     // first row of this fit in the tile-partial buffer
+    int64_t group_base;    // first row in the group-partial buffer / group counters
+    double lb[NMAX], ub[NMAX], xscale[NMAX];
+    double ftol, xtol, gtol;
+    int absolute_sigma, pad_;
+};
+
+// Mutable per-fit state, kept on the device across iterations.
+struct FitState {
+    // --- read by the evaluation pass ---
+    int run;               // RunState
+    int phase;             // Phase of the pending evaluation
+    int bad_data;          // set by the INIT pass when sigma <= 0 or non-finite data
+    int pad0;
+    float pf[PF];          // mixed-precision pass constants (base x -> trial xt)
+    double pd[PD];         // plain pass constants (trial xt)
+    // --- TRF state ---
+    int fit_status, nfev, njev, factor_valid;
+    int last_kind, alg2_iters, jacobi_sweeps, has_basis;
+    double f, Delta, alpha;
+    double x[NMAX], xt[NMAX], g[NMAX];
+    double B[NTMAX];       // packed Gram at x
+    double scale_inv[NMAX];
+    double V[NMAX * NMAX]; // eigenvectors (columns) of the scaled model matrix at x
+    double lam[NMAX];
+    double predicted, step_norm;
+    double s_h[NMAX];      // scaled step of the pending trial
+    double pcov[NMAX * NMAX];
+};
+
+struct WorkItem { int fit; int tile; };
+
+// Pointers shared by every kernel of one engine instance.
+struct Engine {
+    FitDesc* desc;
+    FitState* state;
+    WorkItem* items;
+    int* n_items;
+    float* tile_part;      // [tiles][KMAX] mixed tile sums (FP32)
+    double* tile_part_d;   // [tiles][KMAX] plain tile sums (FP64)
+    double* group_part;    // [groups][KMAX]
+    int* group_cnt;        // [groups]
+    int* fit_cnt;          // [fits]
+    int* running;          // number of running fits
+    int* rounds;           // graph bodies executed since launch
+    int* max_rounds;       // cap on graph bodies (guarantees the WHILE loop ends)
+    int* nfits_dev;        // number of fits of the current launch
+};
+
+}  // namespace gbfit

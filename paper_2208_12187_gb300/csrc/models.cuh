@@ -1,0 +1,251 @@
+// Model registry: h(x; p) and analytic partials dh/dp for each built-in model.
+//
+// The paper forms the Jacobian (Section 2, Eq. jacobian) by automatic
+// differentiation; this library ships a fixed registry of models with their
+// partials written out, the explicit-Jacobian alternative Appendix C allows.
+//
+// Two evaluation forms per model:
+//   plain  (FP64): value and partials at the trial point p'.
+//   mixed  (FP32): value at the base point p, the difference
+//                  dh = h(p') - h(p) in a cancellation-free form (no
+//                  subtraction of two O(h) numbers), and the partials at p'.
+//                  The actual reduction of Eq. accuracy is then accumulated as
+//                  sum dr (2 r + dr), which keeps full relative accuracy when
+//                  f(p) - f(p') is many orders below f (near convergence).
+// Pass constants are prepared once per pass from FP64 parameters:
+//   plain: pd[] (doubles) from p'.
+//   mixed: pf[] (floats) from float images of p, p' and of the FP64
+//          differences p' - p; location parameters also carry a lo word
+//          (p = hi + lo) so that x - x0 keeps ~46 bits of x0.
+#pragma once
+#include "gbfit_internal.cuh"
+
+namespace gbfit {
+
+// expm1(z) for FP32: Taylor series through z^9 for |z| <= 0.5 (truncation
+// error below 3e-9 relative), exp(z) - 1 otherwise (no cancellation there).
+__device__ __forceinline__ float expm1_series(float z) {
+    float p = fmaf(z, 1.0f / 362880.0f, 1.0f / 40320.0f);
+    p = fmaf(z, p, 1.0f / 5040.0f);
+    p = fmaf(z, p, 1.0f / 720.0f);
+    p = fmaf(z, p, 1.0f / 120.0f);
+    p = fmaf(z, p, 1.0f / 24.0f);
+    p = fmaf(z, p, 1.0f / 6.0f);
+    p = fmaf(z, p, 0.5f);
+    p = fmaf(z, p, 1.0f);
+    p = p * z;
+    return fabsf(z) <= 0.5f ? p : __expf(z) - 1.0f;
+}
+
+// E' = E exp(-dq) and dE = E' - E without cancellation.  For large -dq the
+// base value E is already tiny (E <= exp(-15)) and E' is taken directly.
+__device__ __forceinline__ void exp_shift(float E, float q_new, float dq, float& En, float& dE) {
+    float z = -dq;
+    if (z > 15.0f) {
+        En = __expf(-q_new);
+        dE = En - E;
+    } else {
+        dE = E * expm1_series(z);
+        En = E + dE;
+    }
+}
+
+// Float images of the FP64 parameters handed to the mixed prep.
+struct MixedParams {
+    float x[NMAX];    // base p (rounded)
+    float xlo[NMAX];  // p - double(x) (rounded)
+    float xt[NMAX];   // trial p' (rounded)
+    float dx[NMAX];   // p' - p (FP64 difference, rounded)
+};
+
+// ------------------------------------------------------------------ gauss1d
+// h = A exp(-(x-mu)^2/(2 s^2)) + c,  p = (A, mu, s, c)
+struct MGauss1D {
+    static constexpr int N = 4;
+    __device__ static void prep_plain(const double* p, double* pd) {
+        double s = p[2];
+        double is2 = 1.0 / (s * s);
+        pd[0] = p[0]; pd[1] = p[1]; pd[2] = 0.5 * is2; pd[3] = p[3];
+        pd[4] = p[0] * is2; pd[5] = p[0] * is2 / s;
+    }
+    __device__ static void eval_plain(const double* pd, double X, double, double& h, double* J) {
+        double d = X - pd[1];
+        double E = exp(-pd[2] * d * d);
+        h = fma(pd[0], E, pd[3]);
+        J[0] = E; J[1] = pd[4] * E * d; J[2] = pd[5] * E * d * d; J[3] = 1.0;
+    }
+    __device__ static void prep_mixed(const MixedParams& P, float* pf) {
+        float s = P.x[2], st = P.xt[2], ds = P.dx[2];
+        float k = 0.5f / (s * s), kt = 0.5f / (st * st);
+        pf[0] = P.x[0]; pf[1] = P.x[1]; pf[2] = P.xlo[1]; pf[3] = k; pf[4] = P.x[3];
+        pf[5] = P.dx[1];                                   // dmu
+        pf[6] = -ds * (st + s) * k * kt * 2.0f;            // k' - k = -(s'-s)(s'+s)/(2 s^2 s'^2)
+        pf[7] = kt; pf[8] = P.xt[0]; pf[9] = P.dx[0]; pf[10] = P.dx[3];
+        pf[11] = P.xt[0] * 2.0f * kt;                      // A'/s'^2
+        pf[12] = P.xt[0] * 2.0f * kt / st;                 // A'/s'^3
+    }
+    __device__ static void eval_mixed(const float* pf, float X, float, float& hb, float& dh, float* J) {
+        float d = (X - pf[1]) - pf[2];
+        float q = pf[3] * d * d;
+        float E = __expf(-q);
+        hb = fmaf(pf[0], E, pf[4]);
+        float dn = d - pf[5];
+        float dq = fmaf(pf[7] * (-pf[5]), dn + d, pf[6] * d * d);
+        float En, dE;
+        exp_shift(E, pf[7] * dn * dn, dq, En, dE);
+        dh = fmaf(pf[0], dE, fmaf(pf[9], En, pf[10]));
+        J[0] = En; J[1] = pf[11] * En * dn; J[2] = pf[12] * En * dn * dn; J[3] = 1.0f;
+    }
+};
+
+// ------------------------------------------------------------------ dexp
+// h = a1 exp(-x/t1) + a2 exp(-x/t2) + c,  p = (a1, t1, a2, t2, c)
+struct MDexp {
+    static constexpr int N = 5;
+    __device__ static void prep_plain(const double* p, double* pd) {
+        double k1 = 1.0 / p[1], k2 = 1.0 / p[3];
+        pd[0] = p[0]; pd[1] = k1; pd[2] = p[2]; pd[3] = k2; pd[4] = p[4];
+        pd[5] = p[0] * k1 * k1; pd[6] = p[2] * k2 * k2;
+    }
+    __device__ static void eval_plain(const double* pd, double X, double, double& h, double* J) {
+        double e1 = exp(-X * pd[1]), e2 = exp(-X * pd[3]);
+        h = pd[0] * e1 + pd[2] * e2 + pd[4];
+        J[0] = e1; J[1] = pd[5] * X * e1; J[2] = e2; J[3] = pd[6] * X * e2; J[4] = 1.0;
+    }
+    __device__ static void prep_mixed(const MixedParams& P, float* pf) {
+        float t1 = P.x[1], t2 = P.x[3], t1n = P.xt[1], t2n = P.xt[3];
+        float k1 = 1.0f / t1, k2 = 1.0f / t2, k1n = 1.0f / t1n, k2n = 1.0f / t2n;
+        pf[0] = P.x[0]; pf[1] = k1; pf[2] = P.x[2]; pf[3] = k2; pf[4] = P.x[4];
+        pf[5] = -P.dx[1] * k1 * k1n;                        // 1/t1' - 1/t1
+        pf[6] = -P.dx[3] * k2 * k2n;
+        pf[7] = P.xt[0]; pf[8] = P.xt[2];
+        pf[9] = P.dx[0]; pf[10] = P.dx[2]; pf[11] = P.dx[4];
+        pf[12] = P.xt[0] * k1n * k1n; pf[13] = P.xt[2] * k2n * k2n;
+        pf[14] = k1n; pf[15] = k2n;
+    }
+    __device__ static void eval_mixed(const float* pf, float X, float, float& hb, float& dh, float* J) {
+        float q1 = X * pf[1], q2 = X * pf[3];
+        float e1 = __expf(-q1), e2 = __expf(-q2);
+        hb = fmaf(pf[0], e1, fmaf(pf[2], e2, pf[4]));
+        float e1n, de1, e2n, de2;
+        exp_shift(e1, X * pf[14], X * pf[5], e1n, de1);
+        exp_shift(e2, X * pf[15], X * pf[6], e2n, de2);
+        dh = fmaf(pf[0], de1, fmaf(pf[9], e1n, fmaf(pf[2], de2, fmaf(pf[10], e2n, pf[11]))));
+        J[0] = e1n; J[1] = pf[12] * X * e1n; J[2] = e2n; J[3] = pf[13] * X * e2n; J[4] = 1.0f;
+    }
+};
+
+// ------------------------------------------------------------------ gauss2d
+// u =  (X-x0) cos th + (Y-y0) sin th,  v = -(X-x0) sin th + (Y-y0) cos th
+// h = A exp(-u^2/(2 sx^2) - v^2/(2 sy^2)) + c,  p = (A, x0, y0, sx, sy, th, c)
+struct MGauss2D {
+    static constexpr int N = 7;
+    __device__ static void prep_plain(const double* p, double* pd) {
+        double s, c;
+        sincos(p[5], &s, &c);
+        double ka = 0.5 / (p[3] * p[3]), kb = 0.5 / (p[4] * p[4]);
+        pd[0] = p[0]; pd[1] = p[1]; pd[2] = p[2]; pd[3] = c; pd[4] = s;
+        pd[5] = ka; pd[6] = kb; pd[7] = p[6];
+        pd[8] = 2.0 * ka / p[3]; pd[9] = 2.0 * kb / p[4];
+    }
+    __device__ static void eval_plain(const double* pd, double X, double Y, double& h, double* J) {
+        double dx = X - pd[1], dy = Y - pd[2];
+        double u = dx * pd[3] + dy * pd[4];
+        double v = -dx * pd[4] + dy * pd[3];
+        double E = exp(-(pd[5] * u * u + pd[6] * v * v));
+        double Q = pd[0] * E;
+        h = Q + pd[7];
+        double au = 2.0 * pd[5] * u, bv = 2.0 * pd[6] * v;
+        J[0] = E;
+        J[1] = Q * (au * pd[3] - bv * pd[4]);
+        J[2] = Q * (au * pd[4] + bv * pd[3]);
+        J[3] = Q * pd[8] * u * u;
+        J[4] = Q * pd[9] * v * v;
+        J[5] = Q * 2.0 * u * v * (pd[6] - pd[5]);
+        J[6] = 1.0;
+    }
+    __device__ static void prep_mixed(const MixedParams& P, float* pf) {
+        float th = P.x[5], tht = P.xt[5], dth = P.dx[5];
+        float s, c, st, ct;
+        sincosf(th, &s, &c);
+        sincosf(tht, &st, &ct);
+        float mid = th + 0.5f * dth;
+        float sh = sinf(0.5f * dth);
+        float dc = -2.0f * sinf(mid) * sh;                  // cos th' - cos th
+        float ds = 2.0f * cosf(mid) * sh;                   // sin th' - sin th
+        float sx = P.x[3], sy = P.x[4], sxt = P.xt[3], syt = P.xt[4];
+        float ka = 0.5f / (sx * sx), kb = 0.5f / (sy * sy);
+        float kat = 0.5f / (sxt * sxt), kbt = 0.5f / (syt * syt);
+        float dx0 = P.dx[1], dy0 = P.dx[2];
+        pf[0] = P.x[0]; pf[1] = P.x[1]; pf[2] = P.xlo[1]; pf[3] = P.x[2]; pf[4] = P.xlo[2];
+        pf[5] = c; pf[6] = s; pf[7] = ka; pf[8] = kb; pf[9] = P.x[6];
+        pf[10] = dc; pf[11] = ds;
+        pf[12] = -dx0 * ct - dy0 * st;                      // ku
+        pf[13] = dx0 * st - dy0 * ct;                       // kv
+        pf[14] = kat; pf[15] = kbt;
+        pf[16] = -P.dx[3] * (sxt + sx) * 2.0f * ka * kat;   // ka' - ka
+        pf[17] = -P.dx[4] * (syt + sy) * 2.0f * kb * kbt;   // kb' - kb
+        pf[18] = P.xt[0]; pf[19] = P.dx[0]; pf[20] = P.dx[6];
+        pf[21] = ct; pf[22] = st;
+        pf[23] = 2.0f * kat / sxt; pf[24] = 2.0f * kbt / syt;
+    }
+    __device__ static void eval_mixed(const float* pf, float X, float Y, float& hb, float& dh, float* J) {
+        float dx = (X - pf[1]) - pf[2];
+        float dy = (Y - pf[3]) - pf[4];
+        float u = fmaf(dx, pf[5], dy * pf[6]);
+        float v = fmaf(dy, pf[5], -dx * pf[6]);
+        float q = fmaf(pf[7] * u, u, pf[8] * v * v);
+        float E = __expf(-q);
+        hb = fmaf(pf[0], E, pf[9]);
+        float du = fmaf(dx, pf[10], fmaf(dy, pf[11], pf[12]));
+        float dv = fmaf(dy, pf[10], fmaf(-dx, pf[11], pf[13]));
+        float un = u + du, vn = v + dv;
+        float dq = fmaf(pf[14] * du, un + u, fmaf(pf[16] * u, u, fmaf(pf[15] * dv, vn + v, pf[17] * v * v)));
+        float qn = fmaf(pf[14] * un, un, pf[15] * vn * vn);
+        float En, dE;
+        exp_shift(E, qn, dq, En, dE);
+        dh = fmaf(pf[0], dE, fmaf(pf[19], En, pf[20]));
+        float Q = pf[18] * En;
+        float au = 2.0f * pf[14] * un, bv = 2.0f * pf[15] * vn;
+        J[0] = En;
+        J[1] = Q * fmaf(au, pf[21], -bv * pf[22]);
+        J[2] = Q * fmaf(au, pf[22], bv * pf[21]);
+        J[3] = Q * pf[23] * un * un;
+        J[4] = Q * pf[24] * vn * vn;
+        J[5] = Q * 2.0f * un * vn * (pf[15] - pf[14]);
+        J[6] = 1.0f;
+    }
+};
+
+// ------------------------------------------------------------------ poly2
+// h = p0 + p1 x + p2 x^2  (linear in p)
+struct MPoly2 {
+    static constexpr int N = 3;
+    __device__ static void prep_plain(const double* p, double* pd) { pd[0] = p[0]; pd[1] = p[1]; pd[2] = p[2]; }
+    __device__ static void eval_plain(const double* pd, double X, double, double& h, double* J) {
+        h = fma(fma(pd[2], X, pd[1]), X, pd[0]);
+        J[0] = 1.0; J[1] = X; J[2] = X * X;
+    }
+    __device__ static void prep_mixed(const MixedParams& P, float* pf) {
+        pf[0] = P.x[0]; pf[1] = P.x[1]; pf[2] = P.x[2];
+        pf[3] = P.dx[0]; pf[4] = P.dx[1]; pf[5] = P.dx[2];
+    }
+    __device__ static void eval_mixed(const float* pf, float X, float, float& hb, float& dh, float* J) {
+        hb = fmaf(fmaf(pf[2], X, pf[1]), X, pf[0]);
+        dh = fmaf(fmaf(pf[5], X, pf[4]), X, pf[3]);
+        J[0] = 1.0f; J[1] = X; J[2] = X * X;
+    }
+};
+
+__host__ __device__ inline int model_nparams(int model) {
+    switch (model) {
+        case 0: return MGauss1D::N;
+        case 1: return MDexp::N;
+        case 2: return MGauss2D::N;
+        case 3: return MPoly2::N;
+    }
+    return 0;
+}
+__host__ __device__ inline int model_xdims(int model) { return model == 2 ? 2 : 1; }
+
+}  // namespace gbfit

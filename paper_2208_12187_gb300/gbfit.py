@@ -1,0 +1,265 @@
+"""Python binding of libgbfit's C ABI (argument marshalling only).
+
+Every step of a fit runs in the CUDA library; this module converts Python
+arguments to the C call and the outputs back.  It never falls back to a CPU
+path: if libgbfit.so is missing or no GPU is present the call raises.
+
+Data arrays may be torch tensors (CUDA or CPU) or NumPy arrays; CUDA tensors
+are read in place, host arrays are copied to the device inside the call.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from .build import LIB
+
+# ---- constants mirrored from include/gbfit.h
+OK = 0
+E_INVALID_ARG, E_INFEASIBLE_X0, E_OOM, E_BUDGET, E_CUDA, E_TIMEOUT, E_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
+MODEL_GAUSS1D, MODEL_DEXP, MODEL_GAUSS2D, MODEL_POLY2 = 0, 1, 2, 3
+X_VEC, X_SOA2, X_GRID = 0, 1, 2
+F32, F64 = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+FIT_INVALID_DATA, FIT_NUMERICAL, FIT_MAX_NFEV, FIT_GTOL, FIT_FTOL, FIT_XTOL, FIT_FTOL_XTOL = -2, -1, 0, 1, 2, 3, 4
+N_PARAMS = {0: 4, 1: 5, 2: 7, 3: 3}
+
+EXPORTS = ["gbfit_version", "gbfit_last_error", "gbfit_default_options", "gbfit_model_info",
+           "gbfit_curve_fit", "gbfit_curve_fit_batch", "gbfit_evaluate", "gbfit_tr_subproblem"]
+
+
+class GbfitError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"gbfit error {code}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("ftol", ctypes.c_double), ("xtol", ctypes.c_double), ("gtol", ctypes.c_double),
+                ("max_nfev", ctypes.c_int), ("x_scale_jac", ctypes.c_int),
+                ("x_scale", ctypes.POINTER(ctypes.c_double)), ("absolute_sigma", ctypes.c_int),
+                ("precision", ctypes.c_int), ("tile_points", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
+
+
+_LIB = None
+
+
+def load(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load libgbfit.so (built by paper_2208_12187_gb300.build.build())."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgbfit.so not found at {path}; run paper_2208_12187_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    DP = ctypes.POINTER(ctypes.c_double)
+    IP = ctypes.POINTER(ctypes.c_int)
+    lib.gbfit_version.restype = I
+    lib.gbfit_last_error.restype = ctypes.c_char_p
+    lib.gbfit_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.gbfit_model_info.argtypes = [I, IP, IP]
+    lib.gbfit_curve_fit.argtypes = [I, P, I64, I, ctypes.POINTER(ctypes.c_int64), P, P, I, DP, DP, DP,
+                                    ctypes.POINTER(Options), DP, DP, DP, IP, IP, P]
+    lib.gbfit_curve_fit_batch.argtypes = [I, I, ctypes.POINTER(ctypes.c_int64), P, I, P, P, I, DP, DP, DP,
+                                          ctypes.POINTER(Options), DP, DP, DP, IP, IP, P]
+    lib.gbfit_evaluate.argtypes = [I, P, I64, I, ctypes.POINTER(ctypes.c_int64), P, P, I, DP, I, I, DP, P]
+    lib.gbfit_tr_subproblem.argtypes = [I, DP, DP, D, D, DP, DP, DP, P]
+    for name in EXPORTS:
+        getattr(lib, name)
+    _LIB = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise GbfitError(rc, load().gbfit_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _array_info(a):
+    """(pointer, dtype code, keepalive) for a torch tensor or NumPy array."""
+    if a is None:
+        return None, None, None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if not a.is_contiguous():
+                a = a.contiguous()
+            code = {torch.float32: F32, torch.float64: F64}.get(a.dtype)
+            if code is None:
+                raise TypeError("data tensors must be float32 or float64")
+            return ctypes.c_void_p(a.data_ptr()), code, a
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(a)
+    code = {np.dtype(np.float32): F32, np.dtype(np.float64): F64}.get(a.dtype)
+    if code is None:
+        raise TypeError("data arrays must be float32 or float64")
+    return ctypes.c_void_p(a.ctypes.data), code, a
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+def _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points):
+    o = Options()
+    load().gbfit_default_options(ctypes.byref(o))
+    o.ftol, o.xtol, o.gtol = ftol, xtol, gtol
+    o.max_nfev = int(max_nfev or 0)
+    keep = None
+    if isinstance(x_scale, str):
+        if x_scale != "jac":
+            raise ValueError("x_scale must be 'jac' or positive numbers")
+        o.x_scale_jac = 1
+    elif x_scale is not None and not (np.isscalar(x_scale) and float(x_scale) == 1.0):
+        keep = np.ascontiguousarray(np.broadcast_to(np.asarray(x_scale, dtype=np.float64), (n,)))
+        o.x_scale = _dptr(keep)
+    o.absolute_sigma = int(bool(absolute_sigma))
+    o.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision] if isinstance(precision, str) else int(precision)
+    o.tile_points = int(tile_points)
+    return o, keep
+
+
+def _bounds(n, lb, ub):
+    lbv = None if lb is None else np.ascontiguousarray(np.broadcast_to(np.asarray(lb, np.float64), (n,)))
+    ubv = None if ub is None else np.ascontiguousarray(np.broadcast_to(np.asarray(ub, np.float64), (n,)))
+    return lbv, ubv
+
+
+def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None, ub=None,
+              grid_wh=None, ftol=1e-8, xtol=1e-8, gtol=1e-8, max_nfev=None, x_scale=1.0,
+              absolute_sigma=False, precision="mixed", tile_points=0, stream=None) -> dict:
+    """Fit `model` by the GPU trust-region-reflective method (gbfit_curve_fit).
+
+    xdata: [m] (1D models), [2, m] (2D explicit coordinates) or None with
+    grid_wh=(W, H) for the implicit pixel grid.  Returns dict(popt, pcov, cost,
+    nfev, status).
+    """
+    lib = load()
+    n = N_PARAMS[model]
+    yp, dt, ykeep = _array_info(ydata)
+    xp, xdt, xkeep = _array_info(xdata)
+    sp, sdt, skeep = _array_info(sigma)
+    m = int(ykeep.shape[0])
+    if xp is not None and xdt != dt or sp is not None and sdt != dt:
+        raise TypeError("xdata, ydata and sigma must share one dtype")
+    if grid_wh is not None:
+        layout = X_GRID
+        gw = (ctypes.c_int64 * 2)(int(grid_wh[0]), int(grid_wh[1]))
+        xp = None
+    else:
+        layout = X_SOA2 if (xkeep is not None and len(xkeep.shape) == 2) else X_VEC
+        gw = None
+    p0a = np.ascontiguousarray(np.asarray(p0, dtype=np.float64))
+    lbv, ubv = _bounds(n, lb, ub)
+    opt, okeep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points)
+    popt = np.zeros(n)
+    pcov = np.zeros(n * n)
+    cost = ctypes.c_double()
+    nfev = ctypes.c_int()
+    status = ctypes.c_int()
+    rc = lib.gbfit_curve_fit(model, xp, m, layout, gw, yp, sp, dt, _dptr(p0a),
+                             None if lbv is None else _dptr(lbv), None if ubv is None else _dptr(ubv),
+                             ctypes.byref(opt), _dptr(popt), _dptr(pcov), ctypes.byref(cost),
+                             ctypes.byref(nfev), ctypes.byref(status), _stream_ptr(stream))
+    _check(rc)
+    return dict(popt=popt, pcov=pcov.reshape(n, n), cost=cost.value, nfev=nfev.value, status=status.value)
+
+
+def curve_fit_batch(model: int, offsets, xdata, ydata, p0, sigma=None, lb=None, ub=None,
+                    ftol=1e-8, xtol=1e-8, gtol=1e-8, max_nfev=None, x_scale=1.0,
+                    absolute_sigma=False, precision="mixed", tile_points=0, stream=None) -> dict:
+    """Many independent fits over concatenated data (gbfit_curve_fit_batch)."""
+    lib = load()
+    n = N_PARAMS[model]
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    nf = off.shape[0] - 1
+    yp, dt, ykeep = _array_info(ydata)
+    xp, xdt, xkeep = _array_info(xdata)
+    sp, sdt, skeep = _array_info(sigma)
+    layout = X_SOA2 if len(xkeep.shape) == 2 else X_VEC
+    p0a = np.ascontiguousarray(np.asarray(p0, dtype=np.float64).reshape(nf, n))
+    lba = None if lb is None else np.ascontiguousarray(np.broadcast_to(np.asarray(lb, np.float64), (nf, n)))
+    uba = None if ub is None else np.ascontiguousarray(np.broadcast_to(np.asarray(ub, np.float64), (nf, n)))
+    opt, okeep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points)
+    popt = np.zeros((nf, n))
+    pcov = np.zeros((nf, n, n))
+    cost = np.zeros(nf)
+    nfev = np.zeros(nf, dtype=np.int32)
+    status = np.zeros(nf, dtype=np.int32)
+    IP = ctypes.POINTER(ctypes.c_int)
+    rc = lib.gbfit_curve_fit_batch(model, nf, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), xp, layout,
+                                   yp, sp, dt, _dptr(p0a), None if lba is None else _dptr(lba),
+                                   None if uba is None else _dptr(uba), ctypes.byref(opt), _dptr(popt),
+                                   _dptr(pcov), _dptr(cost), nfev.ctypes.data_as(IP),
+                                   status.ctypes.data_as(IP), _stream_ptr(stream))
+    _check(rc)
+    return dict(popt=popt, pcov=pcov, cost=cost, nfev=nfev, status=status)
+
+
+def evaluate(model: int, xdata, ydata, p, sigma=None, grid_wh=None, precision="fp64", tile_points=0,
+             stream=None):
+    """One fused reduction at p: (B packed upper, g, cost) as FP64 arrays (gbfit_evaluate)."""
+    lib = load()
+    n = N_PARAMS[model]
+    yp, dt, ykeep = _array_info(ydata)
+    xp, _, xkeep = _array_info(xdata)
+    sp, _, skeep = _array_info(sigma)
+    m = int(ykeep.shape[0])
+    if grid_wh is not None:
+        layout, gw, xp = X_GRID, (ctypes.c_int64 * 2)(int(grid_wh[0]), int(grid_wh[1])), None
+    else:
+        layout, gw = (X_SOA2 if len(xkeep.shape) == 2 else X_VEC), None
+    pa = np.ascontiguousarray(np.asarray(p, dtype=np.float64))
+    nt = n * (n + 1) // 2
+    out = np.zeros(nt + n + 1)
+    prec = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision] if isinstance(precision, str) else int(precision)
+    rc = lib.gbfit_evaluate(model, xp, m, layout, gw, yp, sp, dt, _dptr(pa), prec, int(tile_points),
+                            _dptr(out), _stream_ptr(stream))
+    _check(rc)
+    return out[:nt], out[nt:nt + n], float(out[nt + n])
+
+
+def tr_subproblem(B, g, Delta: float, alpha0: float = 0.0, stream=None):
+    """Device solve of one scaled trust-region subproblem: (p, alpha, eigenvalues)."""
+    lib = load()
+    B = np.ascontiguousarray(np.asarray(B, dtype=np.float64))
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.float64))
+    n = g.shape[0]
+    p = np.zeros(n)
+    lam = np.zeros(n)
+    alpha = ctypes.c_double()
+    rc = lib.gbfit_tr_subproblem(n, _dptr(B), _dptr(g), float(Delta), float(alpha0), _dptr(p),
+                                 ctypes.byref(alpha), _dptr(lam), _stream_ptr(stream))
+    _check(rc)
+    return p, alpha.value, lam
+
+
+def unpack_upper(packed, n):
+    """Symmetric n x n matrix from its packed row-major upper triangle."""
+    B = np.zeros((n, n))
+    k = 0
+    for i in range(n):
+        for j in range(i, n):
+            B[i, j] = B[j, i] = packed[k]
+            k += 1
+    return B

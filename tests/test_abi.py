@@ -1,0 +1,76 @@
+"""The C-ABI library builds, loads and exports every symbol include/gbfit.h declares.
+
+No compute calls here (no GPU): only symbol checks, the registry query and the
+host-side argument checks that fail before any device work.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2208_12187_gb300 import build, gbfit
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return gbfit.load()
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "gbfit.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gbfit_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_exports():
+    assert _declared_functions() == sorted(gbfit.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_version_and_model_registry(lib):
+    assert lib.gbfit_version() == 1
+    n, xd = ctypes.c_int(), ctypes.c_int()
+    expect = {0: (4, 1), 1: (5, 1), 2: (7, 2), 3: (3, 1)}
+    for mid, (np_, xdim) in expect.items():
+        assert lib.gbfit_model_info(mid, ctypes.byref(n), ctypes.byref(xd)) == 0
+        assert (n.value, xd.value) == (np_, xdim)
+    assert lib.gbfit_model_info(9, ctypes.byref(n), ctypes.byref(xd)) == gbfit.E_INVALID_ARG
+    assert b"unknown model" in lib.gbfit_last_error()
+
+
+def test_default_options(lib):
+    o = gbfit.Options()
+    assert lib.gbfit_default_options(ctypes.byref(o)) == 0
+    assert o.ftol == o.xtol == o.gtol == 1e-8
+    assert o.precision == gbfit.PREC_MIXED
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(p0=[1.0, 0.0, 1.0, 0.0], lb=[0, -1, 0, -1], ub=[2, 1, 2, 1]), gbfit.E_INVALID_ARG),  # 1D model, 2D x
+    (dict(p0=[1.0, np.nan, 1.0, 0.0]), gbfit.E_INVALID_ARG),
+    (dict(p0=[1.0, 0.0, 1.0, 0.0], lb=[2, -1, 0, -1], ub=[3, 1, 2, 1]), gbfit.E_INFEASIBLE_X0),
+    (dict(p0=[1.0, 0.0, 1.0, 0.0], lb=[1, -1, 0, -1], ub=[1, 1, 2, 1]), gbfit.E_INVALID_ARG),
+])
+def test_host_argument_checks(lib, kw, code):
+    x = np.zeros((2, 10)) if "lb" in kw and kw["lb"][0] == 0 else np.zeros(10)
+    with pytest.raises(gbfit.GbfitError) as e:
+        gbfit.curve_fit(gbfit.MODEL_GAUSS1D, x, np.zeros(10), **kw)
+    assert e.value.code == code
+
+
+def test_too_few_points_rejected(lib):
+    with pytest.raises(gbfit.GbfitError) as e:
+        gbfit.curve_fit(gbfit.MODEL_GAUSS2D, None, np.zeros(6), [1, 0, 0, 1, 1, 0, 0], grid_wh=(2, 3))
+    assert e.value.code == gbfit.E_INVALID_ARG
+    with pytest.raises(gbfit.GbfitError) as e:
+        gbfit.curve_fit(gbfit.MODEL_GAUSS1D, np.zeros(0), np.zeros(0), [1, 0, 1, 0])
+    assert e.value.code == gbfit.E_INVALID_ARG
