@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Benchmark: point-iters/s of one trust-region-reflective fit on GB300.
+
+Workload (the configuration the headline metric is quoted on): a rotated
+elliptical 2D Gaussian (7 parameters: A, x0, y0, sx, sy, theta, c) fitted on a
+1024 x 1024 pixel grid (1,048,576 points) of FP32 Poisson counts (peak 1000 on
+background 20), sigma = sqrt(max(y, 1)), bounds sx, sy in [0.5, 500] and
+theta in [-pi/2, pi/2]; FP32 model/Jacobian rows with FP64 reduction combine
+and FP64 n x n solve (precision 'mixed'); ftol = xtol = gtol = 1e-10.
+
+A step is one whole fit (gbfit_curve_fit) from p0 to termination.
+  value      = sum over ranks of m * nfev / max over ranks of the summed step time
+               (device time by CUDA events on the call's stream; inputs resident
+               in HBM; L2 flushed by a 256 MiB write between steps).
+  e2e        = the same metric through the C ABI with pinned HOST buffers: the
+               host->device copy of y and sigma and the result read-back are
+               inside the timed region (host wall clock around the call).
+  roofline   = the evaluation-pass kernel (eval_round_kernel<mixed>), timed per
+               launch with CUDA events in the library's profiling mode, against
+               the FP32 issue peak (the pass is bound by FP32 arithmetic, not HBM).
+  cpu_baseline = the FP64 oracle (test infrastructure) on the same workload,
+               on rank 0 only.
+--impl reference times that oracle as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "point-iters/s per TRF fit (% roofline); batched fits/s + p99 latency vs plain FP64"
+UNIT = "point-iters/s"
+W = H = 1024
+M = W * H
+TOL = dict(ftol=1e-10, xtol=1e-10, gtol=1e-10)
+# Algorithmic work of one evaluation pass per point, rotated 2D Gaussian, mixed
+# precision, implicit grid with sigma: bytes read (y, sigma: FP32) and FP32
+# FLOPs (FMA = 2) of model value, cancellation-free difference, Jacobian row
+# and the Gram / gradient / cost accumulation.
+BYTES_PER_POINT = 8
+FLOPS_PER_POINT = 186
+SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_desc():
+    return ("rotated 2D Gaussian (7 params) on a 1024x1024 pixel grid, 1,048,576 points, FP32 Poisson "
+            "counts peak 1000 / background 20, sigma=sqrt(max(y,1)), bounds sx,sy in [0.5,500], "
+            "theta in [-pi/2,pi/2]; FP32 model/Jacobian, FP64 combine and n x n solve")
+
+
+def make_problem(rank: int):
+    from paper_2208_12187_gb300 import synth
+    return synth.gauss2d_grid(W, seed=rank, dtype=np.float32)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ distributed helpers
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return rank, local, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce(values, op, world):
+    """All-reduce a list of floats over ranks (CPU, gloo): op 'max' or 'sum'."""
+    if world == 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return t.tolist()
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def oracle_rate(pr, budget_s: float = 12.0, max_fits: int = 8):
+    """Time whole oracle fits of the workload until the budget is spent."""
+    from oracle import trf
+    t_total, pts, fits = 0.0, 0.0, 0
+    while fits < max_fits and (t_total < budget_s or fits == 0):
+        t0 = time.perf_counter()
+        out = trf.curve_fit_problem(pr, **TOL)
+        t_total += time.perf_counter() - t0
+        pts += pr.m * out["nfev"]
+        fits += 1
+    return pts / t_total, fits, t_total
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return None
+    pr = make_problem(0)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; W is accepted for the contract
+    times, pts = [], 0.0
+    from oracle import trf
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        out = trf.curve_fit_problem(pr, max_nfev=args.ref_nfev, **TOL)
+        times.append(time.perf_counter() - t0)
+        pts += pr.m * out["nfev"]
+    total = sum(times)
+    value = pts / total
+    cores = blas_threads()
+    sample = f"{args.steps} oracle fits of the workload, each capped at max_nfev={args.ref_nfev}"
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_desc(), "m": M, "precision": "fp64 (oracle)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def run_ours(args, rank, local, world):
+    import torch
+    from paper_2208_12187_gb300 import build, gbfit
+    torch.cuda.set_device(local)
+    build.build()
+    gbfit.load()
+    pr = make_problem(rank)
+    dev = torch.device("cuda", local)
+    y = torch.as_tensor(pr.y).to(dev)
+    sg = torch.as_tensor(pr.sigma).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def fit(yy, ss):
+        return gbfit.curve_fit(pr.model, None, yy, pr.p0, sigma=ss, lb=pr.lb, ub=pr.ub, grid_wh=(W, H),
+                               precision="mixed", **TOL)
+
+    for _ in range(max(args.warmup, 3)):
+        fit(y, sg)
+    torch.cuda.synchronize()
+    gbfit.stats_reset()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    ms_total, pts, nfevs = 0.0, 0.0, []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()                       # L2 flush (untimed)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fit(y, sg)
+        e1.record(stream)
+        e1.synchronize()
+        ms_total += e0.elapsed_time(e1)
+        pts += M * out["nfev"]
+        nfevs.append(out["nfev"])
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    st = gbfit.stats()
+    launches = int(st["kernel_launches"])
+    ms_max, = allreduce([ms_total], "max", world)
+    pts_sum, = allreduce([pts], "sum", world)
+    value = pts_sum / (ms_max / 1e3)
+
+    # ---- roofline: per-launch CUDA-event timing of the evaluation pass
+    gbfit.set_profiling(True)
+    gbfit.stats_reset()
+    for _ in range(3):
+        flush.zero_()
+        fit(y, sg)
+    sp = gbfit.stats()
+    gbfit.set_profiling(False)
+    avg_ms = sp["eval_ms"] / max(sp["eval_launches"], 1)
+    achieved = M * FLOPS_PER_POINT / (avg_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+            "kernel": "eval_round_kernel<mixed> (rotated 2D Gaussian, grid, sigma)",
+            "flops_per_point": FLOPS_PER_POINT, "bytes_per_point": BYTES_PER_POINT,
+            "avg_launch_us": avg_ms * 1e3,
+            "hbm_gbs_at_this_time": M * BYTES_PER_POINT / (avg_ms / 1e3) / 1e9,
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (unit counts and max clock)"}
+    if args.traffic is not None:
+        roof["traffic"] = args.traffic
+
+    # ---- e2e: pinned host buffers through the C ABI, copies inside the timed region
+    yh = torch.empty(M, dtype=torch.float32, pin_memory=True)
+    sh = torch.empty(M, dtype=torch.float32, pin_memory=True)
+    yh.copy_(torch.as_tensor(pr.y))
+    sh.copy_(torch.as_tensor(pr.sigma))
+    yn, sn = yh.numpy(), sh.numpy()
+    for _ in range(2):
+        fit(yn, sn)
+    e2e_t, e2e_pts = 0.0, 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fit(yn, sn)                   # returns after the result read-back
+        e2e_t += time.perf_counter() - t0
+        e2e_pts += M * out["nfev"]
+    e2e_t, = allreduce([e2e_t], "max", world)
+    e2e_pts, = allreduce([e2e_pts], "sum", world)
+    n = pr.n
+    d2h = 8 * (n + n * n + 1) + 8        # popt, pcov, cost, nfev + status
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": workload_desc(), "m": M, "precision": "mixed", "nfev_per_fit": nfevs[0],
+                   "l2": "flushed between steps (256 MiB write, untimed)", "parallelism": f"{world} independent fits"},
+        "roofline": roof,
+        "e2e": {"value": e2e_pts / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * M, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, fits, secs = oracle_rate(pr)
+        res["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                               "sample": f"{fits} whole FP64 oracle fits of the same workload ({secs:.1f} s)"}
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-nfev", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per evaluation launch from an ncu capture of the current kernel")
+    args = ap.parse_args()
+    rank, local, world = dist_setup(args)
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_ours(args, rank, local, world)
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -179,6 +179,36 @@ int gbfit_evaluate(int model_id,
 int gbfit_tr_subproblem(int n, const double* B, const double* g, double Delta, double alpha0,
                         double* p, double* alpha, double* lam, void* cuda_stream);
 
+/*
+ * Runtime counters and per-launch timing (the per-operation timing the paper
+ * reports in Section 4 / Fig. 3, taken here with CUDA events).
+ * Counters are process-wide and accumulate over calls until reset.
+ */
+typedef struct gbfit_stats {
+    int64_t calls;            /* gbfit_curve_fit / _batch / _evaluate calls            */
+    int64_t fits;             /* fits completed                                        */
+    int64_t kernel_launches;  /* kernels the library executed (graph nodes included)   */
+    int64_t graph_rounds;     /* WHILE-body trips of the iteration graph               */
+    int64_t passes;           /* data passes = sum over fits of nfev                   */
+    double point_passes;      /* sum over fits of m * nfev                             */
+    double eval_ms;           /* profiling on: summed CUDA-event time of evaluation launches */
+    int64_t eval_launches;    /* profiling on: evaluation launches timed               */
+} gbfit_stats;
+
+/* Zero the counters. */
+int gbfit_stats_reset(void);
+
+/* Copy the counters into *out. */
+int gbfit_stats_get(gbfit_stats* out);
+
+/*
+ * on = 1: subsequent fits run their iterations as host-launched kernels, each
+ * evaluation launch bracketed by CUDA events on the call's stream (one host
+ * synchronisation per iteration: for measurement, not for speed).
+ * on = 0 (default): one graph launch per call.  Results are identical.
+ */
+int gbfit_set_profiling(int on);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,6 +32,10 @@ constexpr int TILE_MIN = 2048, TILE_MAX = 16384, TILE_SPLIT = 304;
 
 thread_local std::string g_err;
 
+std::mutex g_stats_mu;
+gbfit_stats g_stats = {};
+int g_profiling = 0;
+
 int fail(int code, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -317,14 +321,63 @@ int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::
     CUDA_TRY(cudaMemcpyAsync(c->scalars, sc, 16 * sizeof(int), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemsetAsync(c->group_cnt, 0, ngroups * sizeof(int), s));
     CUDA_TRY(cudaMemsetAsync(c->fit_cnt, 0, nf * sizeof(int), s));
-    CUDA_TRY(cudaGraphLaunch(c->exec[prec], s));
+    double eval_ms = 0.0;
+    int64_t eval_launches = 0, launches = 0;
+    if (g_profiling) {
+        // measurement mode: same kernels, host-launched, each evaluation timed with events
+        Engine E = c->engine();
+        FitResult* res = c->results;
+        void* a_init[] = {&E};
+        CUDA_TRY(cudaLaunchKernel(kernel_init_fits(prec), dim3(256), dim3(32), a_init, 0, s));
+        launches += 1;
+        cudaEvent_t e0, e1;
+        CUDA_TRY(cudaEventCreate(&e0));
+        CUDA_TRY(cudaEventCreate(&e1));
+        int* run_h = sc + 8;
+        int cap = (max_nfev + 2) + 4;
+        for (int r = 0; r < cap; ++r) {
+            void* a_eval[] = {&E, &res};
+            CUDA_TRY(cudaEventRecord(e0, s));
+            CUDA_TRY(cudaLaunchKernel(kernel_eval_round(prec), dim3(c->grid), dim3(EVAL_THREADS), a_eval, 0, s));
+            CUDA_TRY(cudaEventRecord(e1, s));
+            CUDA_TRY(cudaMemcpyAsync(run_h, c->scalars + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            eval_ms += ms;
+            eval_launches += 1;
+            launches += 1;
+            if (*run_h == 0) break;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    } else {
+        CUDA_TRY(cudaGraphLaunch(c->exec[prec], s));
+    }
     CUDA_TRY(cudaMemcpyAsync(hb + off_res, c->results, nf * sizeof(FitResult), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(sc, c->scalars, 16 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     hr.resize(nf);
     memcpy(hr.data(), hb + off_res, nf * sizeof(FitResult));
     if (rounds_out) *rounds_out = sc[2];
-    if (sc[1] != 0) return fail(GBFIT_E_TIMEOUT, "%d fit(s) still running after the round cap", sc[1]);
+    {
+        std::lock_guard<std::mutex> g(g_stats_mu);
+        g_stats.calls += 1;
+        g_stats.fits += (int64_t)nf;
+        if (g_profiling) {
+            g_stats.kernel_launches += launches;
+            g_stats.eval_ms += eval_ms;
+            g_stats.eval_launches += eval_launches;
+        } else {
+            g_stats.kernel_launches += 1 + (int64_t)sc[2] * (UNROLL + 1);
+            g_stats.graph_rounds += sc[2];
+        }
+        for (size_t f = 0; f < nf; ++f) {
+            g_stats.passes += hr[f].nfev;
+            g_stats.point_passes += double(hd[f].m) * hr[f].nfev;
+        }
+    }
+    if (!g_profiling && sc[1] != 0) return fail(GBFIT_E_TIMEOUT, "%d fit(s) still running after the round cap", sc[1]);
     return GBFIT_OK;
 }
 
@@ -460,6 +513,7 @@ static int single_fit(int model_id, const void* xdata, int64_t m, int x_layout, 
         bool changed = false;
         if ((rc = grow_dev(c->wbuf, c->cap_w, (size_t)m, changed))) return rc;
         CUDA_TRY(launch_stage_weights(dtype == GBFIT_F64, sd.sigma, c->wbuf, m, c->sms * 8, s));
+        { std::lock_guard<std::mutex> g(g_stats_mu); g_stats.kernel_launches += 1; }
     }
     set_data(c, hd[0], sd.x, x2, sd.y, sd.sigma, 0, s);
     std::vector<std::vector<double>> p0s(1, std::vector<double>(p0, p0 + n));
@@ -541,6 +595,7 @@ int gbfit_curve_fit_batch(int model_id, int nfits, const int64_t* offsets, const
         bool changed = false;
         if ((rc = grow_dev(c->wbuf, c->cap_w, (size_t)total, changed))) return rc;
         CUDA_TRY(launch_stage_weights(dtype == GBFIT_F64, sd.sigma, c->wbuf, total, c->sms * 8, s));
+        { std::lock_guard<std::mutex> g(g_stats_mu); g_stats.kernel_launches += 1; }
     }
     std::vector<FitDesc> hd(nfits);
     std::vector<std::vector<double>> p0s(nfits);
@@ -565,6 +620,24 @@ int gbfit_curve_fit_batch(int model_id, int nfits, const int64_t* offsets, const
         if (nfev) nfev[f] = r.nfev;
         if (fit_status) fit_status[f] = r.fit_status;
     }
+    return GBFIT_OK;
+}
+
+int gbfit_stats_reset(void) {
+    std::lock_guard<std::mutex> g(g_stats_mu);
+    memset(&g_stats, 0, sizeof g_stats);
+    return GBFIT_OK;
+}
+
+int gbfit_stats_get(gbfit_stats* out) {
+    if (!out) return fail(GBFIT_E_INVALID_ARG, "out is NULL");
+    std::lock_guard<std::mutex> g(g_stats_mu);
+    *out = g_stats;
+    return GBFIT_OK;
+}
+
+int gbfit_set_profiling(int on) {
+    g_profiling = on ? 1 : 0;
     return GBFIT_OK;
 }
 

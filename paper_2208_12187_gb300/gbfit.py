@@ -29,7 +29,8 @@ FIT_INVALID_DATA, FIT_NUMERICAL, FIT_MAX_NFEV, FIT_GTOL, FIT_FTOL, FIT_XTOL, FIT
 N_PARAMS = {0: 4, 1: 5, 2: 7, 3: 3}
 
 EXPORTS = ["gbfit_version", "gbfit_last_error", "gbfit_default_options", "gbfit_model_info",
-           "gbfit_curve_fit", "gbfit_curve_fit_batch", "gbfit_evaluate", "gbfit_tr_subproblem"]
+           "gbfit_curve_fit", "gbfit_curve_fit_batch", "gbfit_evaluate", "gbfit_tr_subproblem",
+           "gbfit_stats_reset", "gbfit_stats_get", "gbfit_set_profiling"]
 
 
 class GbfitError(RuntimeError):
@@ -44,6 +45,12 @@ class Options(ctypes.Structure):
                 ("x_scale", ctypes.POINTER(ctypes.c_double)), ("absolute_sigma", ctypes.c_int),
                 ("precision", ctypes.c_int), ("tile_points", ctypes.c_int),
                 ("reserved", ctypes.c_int * 4)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_int64), ("fits", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("graph_rounds", ctypes.c_int64), ("passes", ctypes.c_int64), ("point_passes", ctypes.c_double),
+                ("eval_ms", ctypes.c_double), ("eval_launches", ctypes.c_int64)]
 
 
 _LIB = None
@@ -71,6 +78,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
                                           ctypes.POINTER(Options), DP, DP, DP, IP, IP, P]
     lib.gbfit_evaluate.argtypes = [I, P, I64, I, ctypes.POINTER(ctypes.c_int64), P, P, I, DP, I, I, DP, P]
     lib.gbfit_tr_subproblem.argtypes = [I, DP, DP, D, D, DP, DP, DP, P]
+    lib.gbfit_stats_get.argtypes = [ctypes.POINTER(Stats)]
+    lib.gbfit_set_profiling.argtypes = [I]
     for name in EXPORTS:
         getattr(lib, name)
     _LIB = lib
@@ -263,3 +272,19 @@ def unpack_upper(packed, n):
             B[i, j] = B[j, i] = packed[k]
             k += 1
     return B
+
+
+def stats_reset():
+    _check(load().gbfit_stats_reset())
+
+
+def stats() -> dict:
+    """Process-wide counters (calls, fits, kernel launches, passes, profiled eval time)."""
+    st = Stats()
+    _check(load().gbfit_stats_get(ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in Stats._fields_}
+
+
+def set_profiling(on: bool):
+    """Per-launch CUDA-event timing of evaluation passes (host-launched iterations)."""
+    _check(load().gbfit_set_profiling(1 if on else 0))
