@@ -193,6 +193,17 @@ typedef struct gbfit_stats {
     double point_passes;      /* sum over fits of m * nfev                             */
     double eval_ms;           /* profiling on: summed CUDA-event time of evaluation launches */
     int64_t eval_launches;    /* profiling on: evaluation launches timed               */
+    double phase_cycles[24];  /* summed over fits and iterations (SM cycles unless noted):
+                                 0 own tile, 1 combine, 2 accept/terminate logic,
+                                 3 n x n eigen-decomposition, 4 combine: store, fence and
+                                 arrival, 5 step (solve, Algorithm 2, bounded selection),
+                                 6 pass constants, 7 final pcov, 8-9 combine: group,
+                                 final, 10-13 eigen: warm start, FP32 Jacobi,
+                                 re-orthonormalisation, refinement, 14 FP32 Jacobi sweeps
+                                 (count), 15 refinement passes (count), 16 Gauss-Newton
+                                 fast path, 17 fast-path steps (count), 18 eigen
+                                 decompositions (count), 19 Algorithm 2 iterations
+                                 (count), 20 bounded non-full steps (count), 21-23 spare */
 } gbfit_stats;
 
 /* Zero the counters. */

@@ -66,19 +66,33 @@ int grow_dev(T*& p, size_t& cap, size_t need, bool& changed) {
     return GBFIT_OK;
 }
 
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Byte layout of one call's job buffer: what the host uploads ([0, res_hdr))
+// and what it reads back ([res_hdr, end)) are each one contiguous copy.
+struct Layout {
+    size_t eng, desc, state, items, gcnt, fcnt, res_hdr, res, end;
+    Layout(size_t nf, size_t ntiles, size_t ngroups) {
+        size_t o = 0;
+        eng = o;     o += align256(sizeof(Engine));
+        desc = o;    o += align256(nf * sizeof(FitDesc));
+        state = o;   o += align256(nf * sizeof(FitState));
+        items = o;   o += align256(ntiles * sizeof(WorkItem));
+        gcnt = o;    o += align256(ngroups * sizeof(int));
+        fcnt = o;    o += align256(nf * sizeof(int));
+        res_hdr = o; o += 256;
+        res = o;     o += align256(nf * sizeof(FitResult));
+        end = o;
+    }
+};
+
 struct Ctx {
-    int device = -1, sms = 0, grid = 0;
+    int device = -1, sms = 0, grid_p[2] = {0, 0};
     std::mutex mu;
-    FitDesc* desc = nullptr; size_t cap_fits = 0;
-    FitState* state = nullptr; size_t cap_state = 0;
-    FitResult* results = nullptr; size_t cap_res = 0;
-    int* fit_cnt = nullptr; size_t cap_fcnt = 0;
-    WorkItem* items = nullptr; size_t cap_items = 0;
+    char* job = nullptr; size_t cap_job = 0;   // Engine header + per-fit records
     float* tile_part = nullptr; size_t cap_tp = 0;
     double* tile_part_d = nullptr; size_t cap_tpd = 0;
     double* group_part = nullptr; size_t cap_gp = 0;
-    int* group_cnt = nullptr; size_t cap_gc = 0;
-    int* scalars = nullptr;       // n_items, running, rounds, max_rounds, nfits
     double* wbuf = nullptr; size_t cap_w = 0;
     char* databuf = nullptr; size_t cap_data = 0;
     double* small = nullptr;      // subproblem scratch
@@ -88,12 +102,21 @@ struct Ctx {
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
 
-    Engine engine() const {
+    Engine* eng_dev() const { return (Engine*)job; }
+    Engine engine(const Layout& L) const {
         Engine E;
-        E.desc = desc; E.state = state; E.items = items; E.n_items = scalars + 0;
+        memset(&E, 0, sizeof E);
+        Engine* ed = eng_dev();
+        E.results = (FitResult*)(job + L.res);
+        E.out = (int*)(job + L.res_hdr);
+        E.desc = (FitDesc*)(job + L.desc);
+        E.state = (FitState*)(job + L.state);
+        E.items = (WorkItem*)(job + L.items);
+        E.group_cnt = (int*)(job + L.gcnt);
+        E.fit_cnt = (int*)(job + L.fcnt);
         E.tile_part = tile_part; E.tile_part_d = tile_part_d; E.group_part = group_part;
-        E.group_cnt = group_cnt; E.fit_cnt = fit_cnt; E.running = scalars + 1; E.rounds = scalars + 2;
-        E.max_rounds = scalars + 3; E.nfits_dev = scalars + 4;
+        E.n_items = &ed->sc[0]; E.running = &ed->sc[1]; E.rounds = &ed->sc[2];
+        E.max_rounds = &ed->sc[3]; E.nfits_dev = &ed->sc[4];
         return E;
     }
     void drop_graphs() {
@@ -131,11 +154,8 @@ int get_ctx(Ctx** out) {
         if (e != cudaSuccess) { delete c; return fail(GBFIT_E_CUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e)); }
         c->sms = prop.multiProcessorCount;
         int b0 = eval_blocks_per_sm(PREC_FP64), b1 = eval_blocks_per_sm(PREC_MIXED);
-        int b = b0 < b1 ? b0 : b1;
-        if (b < 1) b = 1;
-        c->grid = c->sms * b;
-        e = cudaMalloc((void**)&c->scalars, 16 * sizeof(int));
-        if (e != cudaSuccess) { delete c; return fail(GBFIT_E_OOM, "cudaMalloc: %s", cudaGetErrorString(e)); }
+        c->grid_p[PREC_FP64] = c->sms * (b0 < 1 ? 1 : b0);
+        c->grid_p[PREC_MIXED] = c->sms * (b1 < 1 ? 1 : b1);
         e = cudaMalloc((void**)&c->small, 256 * sizeof(double));
         if (e != cudaSuccess) { delete c; return fail(GBFIT_E_OOM, "cudaMalloc: %s", cudaGetErrorString(e)); }
         g_ctx[dev] = c;
@@ -144,19 +164,14 @@ int get_ctx(Ctx** out) {
     return GBFIT_OK;
 }
 
-int ensure(Ctx* c, size_t nfits, size_t ntiles, size_t ngroups, size_t nitems) {
-    bool changed = false;
+int ensure(Ctx* c, const Layout& L, size_t ntiles, size_t ngroups) {
+    bool job_changed = false, scratch_changed = false;
     int rc;
-    if ((rc = grow_dev(c->desc, c->cap_fits, nfits, changed))) return rc;
-    if ((rc = grow_dev(c->state, c->cap_state, nfits, changed))) return rc;
-    if ((rc = grow_dev(c->results, c->cap_res, nfits, changed))) return rc;
-    if ((rc = grow_dev(c->fit_cnt, c->cap_fcnt, nfits, changed))) return rc;
-    if ((rc = grow_dev(c->items, c->cap_items, nitems, changed))) return rc;
-    if ((rc = grow_dev(c->tile_part, c->cap_tp, ntiles * KMAX, changed))) return rc;
-    if ((rc = grow_dev(c->tile_part_d, c->cap_tpd, ntiles * KMAX, changed))) return rc;
-    if ((rc = grow_dev(c->group_part, c->cap_gp, ngroups * KMAX, changed))) return rc;
-    if ((rc = grow_dev(c->group_cnt, c->cap_gc, ngroups, changed))) return rc;
-    if (changed) c->drop_graphs();
+    if ((rc = grow_dev(c->job, c->cap_job, L.end, job_changed))) return rc;
+    if ((rc = grow_dev(c->tile_part, c->cap_tp, ntiles * KMAX, scratch_changed))) return rc;
+    if ((rc = grow_dev(c->tile_part_d, c->cap_tpd, ntiles * KMAX, scratch_changed))) return rc;
+    if ((rc = grow_dev(c->group_part, c->cap_gp, ngroups * KMAX, scratch_changed))) return rc;
+    if (job_changed) c->drop_graphs();   // kernels are bound to the job buffer's address
     return GBFIT_OK;
 }
 
@@ -165,8 +180,7 @@ int build_graph(Ctx* c) {
     if (c->exec[P]) return GBFIT_OK;
     cudaGraph_t g;
     CUDA_TRY(cudaGraphCreate(&g, 0));
-    Engine E = c->engine();
-    FitResult* res = c->results;
+    Engine* E = c->eng_dev();
     cudaGraphNode_t n_init;
     {
         void* args[] = {&E};
@@ -189,10 +203,10 @@ int build_graph(Ctx* c) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     cudaGraphNode_t prev = nullptr;
     for (int u = 0; u < UNROLL; ++u) {
-        void* args[] = {&E, &res};
+        void* args[] = {&E};
         cudaKernelNodeParams kp = {};
         kp.func = kernel_eval_round(P);
-        kp.gridDim = dim3(c->grid);
+        kp.gridDim = dim3(c->grid_p[P]);
         kp.blockDim = dim3(EVAL_THREADS);
         kp.kernelParams = args;
         cudaGraphNode_t nn;
@@ -272,7 +286,8 @@ gbfit_options defaults() {
 }
 
 // Run nfits fits whose descriptors (data pointers already on the device) are
-// in hd[]; writes per-fit results into hr[].
+// in hd[]; writes per-fit results into hr[].  One host-to-device copy of the
+// job buffer, one graph launch, one device-to-host copy of the results.
 int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::vector<double>>& p0s,
              std::vector<FitResult>& hr, cudaStream_t s, int* rounds_out) {
     size_t nf = hd.size();
@@ -285,21 +300,24 @@ int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::
         ngroups += d.n_groups;
         if (d.max_nfev > max_nfev) max_nfev = d.max_nfev;
     }
+    Layout L(nf, ntiles, ngroups);
     int rc;
-    if ((rc = ensure(c, nf, ntiles, ngroups, ntiles))) return rc;
+    if ((rc = ensure(c, L, ntiles, ngroups))) return rc;
     if (prec == PREC_MIXED) { if ((rc = build_graph<PREC_MIXED>(c))) return rc; }
     else { if ((rc = build_graph<PREC_FP64>(c))) return rc; }
-    size_t off_desc = 0, off_state = off_desc + nf * sizeof(FitDesc);
-    size_t off_items = off_state + nf * sizeof(FitState);
-    size_t off_sc = off_items + ntiles * sizeof(WorkItem);
-    size_t off_res = off_sc + 16 * sizeof(int);
-    size_t total = off_res + nf * sizeof(FitResult);
-    if ((rc = c->pinned(total))) return rc;
+    if ((rc = c->pinned(L.end))) return rc;
     char* hb = c->hbuf;
-    memcpy(hb + off_desc, hd.data(), nf * sizeof(FitDesc));
-    FitState* hs = (FitState*)(hb + off_state);
-    memset(hs, 0, nf * sizeof(FitState));
-    WorkItem* hi = (WorkItem*)(hb + off_items);
+    memset(hb, 0, L.res_hdr);
+    Engine E = c->engine(L);
+    E.sc[0] = (int)ntiles;
+    E.sc[1] = (int)nf;
+    E.sc[2] = 0;
+    E.sc[3] = (max_nfev + 2) / UNROLL + 3;
+    E.sc[4] = (int)nf;
+    memcpy(hb + L.eng, &E, sizeof E);
+    memcpy(hb + L.desc, hd.data(), nf * sizeof(FitDesc));
+    FitState* hs = (FitState*)(hb + L.state);
+    WorkItem* hi = (WorkItem*)(hb + L.items);
     size_t k = 0;
     for (size_t f = 0; f < nf; ++f) {
         FitState& st = hs[f];
@@ -308,39 +326,25 @@ int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::
         for (int i = 0; i < hd[f].n; ++i) { st.x[i] = p0s[f][i]; st.xt[i] = p0s[f][i]; st.scale_inv[i] = 1.0; }
         for (int t = 0; t < hd[f].n_tiles; ++t) hi[k++] = WorkItem{(int)f, t};
     }
-    int* sc = (int*)(hb + off_sc);
-    memset(sc, 0, 16 * sizeof(int));
-    sc[0] = (int)ntiles;
-    sc[1] = (int)nf;
-    sc[2] = 0;
-    sc[3] = (max_nfev + 2) / UNROLL + 3;
-    sc[4] = (int)nf;
-    CUDA_TRY(cudaMemcpyAsync(c->desc, hb + off_desc, nf * sizeof(FitDesc), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(c->state, hb + off_state, nf * sizeof(FitState), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(c->items, hb + off_items, ntiles * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(c->scalars, sc, 16 * sizeof(int), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemsetAsync(c->group_cnt, 0, ngroups * sizeof(int), s));
-    CUDA_TRY(cudaMemsetAsync(c->fit_cnt, 0, nf * sizeof(int), s));
+    CUDA_TRY(cudaMemcpyAsync(c->job, hb, L.res_hdr, cudaMemcpyHostToDevice, s));
     double eval_ms = 0.0;
     int64_t eval_launches = 0, launches = 0;
     if (g_profiling) {
         // measurement mode: same kernels, host-launched, each evaluation timed with events
-        Engine E = c->engine();
-        FitResult* res = c->results;
-        void* a_init[] = {&E};
-        CUDA_TRY(cudaLaunchKernel(kernel_init_fits(prec), dim3(256), dim3(32), a_init, 0, s));
+        Engine* Ed = c->eng_dev();
+        void* a_eng[] = {&Ed};
+        CUDA_TRY(cudaLaunchKernel(kernel_init_fits(prec), dim3(256), dim3(32), a_eng, 0, s));
         launches += 1;
         cudaEvent_t e0, e1;
         CUDA_TRY(cudaEventCreate(&e0));
         CUDA_TRY(cudaEventCreate(&e1));
-        int* run_h = sc + 8;
+        int* run_h = (int*)(hb + L.res_hdr);
         int cap = (max_nfev + 2) + 4;
         for (int r = 0; r < cap; ++r) {
-            void* a_eval[] = {&E, &res};
             CUDA_TRY(cudaEventRecord(e0, s));
-            CUDA_TRY(cudaLaunchKernel(kernel_eval_round(prec), dim3(c->grid), dim3(EVAL_THREADS), a_eval, 0, s));
+            CUDA_TRY(cudaLaunchKernel(kernel_eval_round(prec), dim3(c->grid_p[prec]), dim3(EVAL_THREADS), a_eng, 0, s));
             CUDA_TRY(cudaEventRecord(e1, s));
-            CUDA_TRY(cudaMemcpyAsync(run_h, c->scalars + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaMemcpyAsync(run_h, &Ed->sc[1], sizeof(int), cudaMemcpyDeviceToHost, s));
             CUDA_TRY(cudaStreamSynchronize(s));
             float ms = 0.f;
             CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
@@ -351,15 +355,17 @@ int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        CUDA_TRY(cudaMemcpyAsync(c->job + L.res_hdr, &Ed->sc[1], 2 * sizeof(int), cudaMemcpyDeviceToDevice, s));
     } else {
         CUDA_TRY(cudaGraphLaunch(c->exec[prec], s));
     }
-    CUDA_TRY(cudaMemcpyAsync(hb + off_res, c->results, nf * sizeof(FitResult), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(sc, c->scalars, 16 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(hb + L.res_hdr, c->job + L.res_hdr, L.end - L.res_hdr, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    const int* outsc = (const int*)(hb + L.res_hdr);
+    int running = outsc[0], rounds = outsc[1];
     hr.resize(nf);
-    memcpy(hr.data(), hb + off_res, nf * sizeof(FitResult));
-    if (rounds_out) *rounds_out = sc[2];
+    memcpy(hr.data(), hb + L.res, nf * sizeof(FitResult));
+    if (rounds_out) *rounds_out = rounds;
     {
         std::lock_guard<std::mutex> g(g_stats_mu);
         g_stats.calls += 1;
@@ -369,15 +375,16 @@ int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::
             g_stats.eval_ms += eval_ms;
             g_stats.eval_launches += eval_launches;
         } else {
-            g_stats.kernel_launches += 1 + (int64_t)sc[2] * (UNROLL + 1);
-            g_stats.graph_rounds += sc[2];
+            g_stats.kernel_launches += 1 + (int64_t)rounds * (UNROLL + 1);
+            g_stats.graph_rounds += rounds;
         }
         for (size_t f = 0; f < nf; ++f) {
+            for (int k = 0; k < 24; ++k) g_stats.phase_cycles[k] += hr[f].trace[k];
             g_stats.passes += hr[f].nfev;
             g_stats.point_passes += double(hd[f].m) * hr[f].nfev;
         }
     }
-    if (!g_profiling && sc[1] != 0) return fail(GBFIT_E_TIMEOUT, "%d fit(s) still running after the round cap", sc[1]);
+    if (!g_profiling && running != 0) return fail(GBFIT_E_TIMEOUT, "%d fit(s) still running after the round cap", running);
     return GBFIT_OK;
 }
 

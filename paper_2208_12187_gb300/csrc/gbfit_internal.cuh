@@ -65,15 +65,21 @@ struct FitState {
     double scale_inv[NMAX];
     double V[NMAX * NMAX]; // eigenvectors (columns) of the scaled model matrix at x
     double lam[NMAX];
-    double predicted, step_norm;
+    double predicted, step_norm, s_norm, xtol_thr;
     double s_h[NMAX];      // scaled step of the pending trial
-    double pcov[NMAX * NMAX];
+    unsigned long long trace[24];  // SM cycles / counts per phase of the step, summed over iterations
 };
 
 struct WorkItem { int fit; int tile; };
 
-// Pointers shared by every kernel of one engine instance.
+struct FitResult;
+
+// Everything one launch of the iteration graph works on.  It lives at the
+// start of the job buffer in device memory (kernels receive its address), so
+// the cached graph stays valid while per-call sizes and scratch change.
 struct Engine {
+    FitResult* results;    // [fits]
+    int* out;              // in the result region: [0] running, [1] rounds (copied back)
     FitDesc* desc;
     FitState* state;
     WorkItem* items;
@@ -87,6 +93,7 @@ struct Engine {
     int* rounds;           // graph bodies executed since launch
     int* max_rounds;       // cap on graph bodies (guarantees the WHILE loop ends)
     int* nfits_dev;        // number of fits of the current launch
+    int sc[8];             // the scalars the pointers above refer to
 };
 
 }  // namespace gbfit

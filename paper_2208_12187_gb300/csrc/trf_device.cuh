@@ -45,9 +45,15 @@ struct FitResult {
     double popt[NMAX];
     double pcov[NMAX * NMAX];
     double tot[KMAX];      // sums of the last evaluation (Gram, gradient, cost)
+    double trace[24];      // SM cycles per phase (see TracePhase), summed over iterations
     double cost;
     int nfev, njev, fit_status, rounds;
 };
+
+// Phases timed (clock64, SM cycles) inside the step, summed per fit.
+enum TracePhase { TR_TILE = 0, TR_COMBINE, TR_LOGIC, TR_EIGEN, TR_C_FENCE, TR_STEP, TR_PREP, TR_FINISH,
+                  TR_C_GROUP, TR_C_FINAL, TR_E_WARM, TR_E_J32, TR_E_NS, TR_E_RR, TR_E_SWEEPS, TR_E_REFINES,
+                  TR_GN, TR_N_GN, TR_N_EIG, TR_N_ALG2IT, TR_N_BOUNDED, TR_RES1, TR_RES2, TR_RES3 };
 
 // Shared-memory workspace of the warp that runs one fit's step.
 struct TrfSmem {
@@ -57,14 +63,39 @@ struct TrfSmem {
     double Ah[64];    // scaled model matrix D B D + diag(C)
     double V[64];
     double W[64];     // scratch matrix
+    double V0[64];    // scratch matrix (starting basis)
+    double H[64];     // partial products of mm8
     double vec[16][8];
-    double cs[8];
+    double sd[8];
+    double pds[PD];
+    float Af[64];     // FP32 Jacobi work matrix
+    float Af2[64];
+    float Rf[64];     // FP32 accumulated rotations
+    float Rf2[64];
+    float Lf[64];     // FP32 Cholesky factor (fast path)
+    float csf[8];
+    float pfs[PF];
+    MixedParams mp;
+    int si[8];
     int pairs[8];
 };
 // named rows of TrfSmem::vec
 enum { VX = 0, VXT, VG, VLB, VUB, VSX, VV, VDV, VD, VGH, VC, VLAM, VGV, VSTR, VSH, VTMP };
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// 1/x to about one ulp: FP32 reciprocal seed, two FP64 Newton steps (an FP64
+// division costs ~10 FP64 instructions on GB300, this ~6).
+__device__ __forceinline__ double rcp64(double x) {
+    float xf = float(x);
+    float ax = fabsf(xf);
+    if (!(ax > 1e-36f && ax < 1e36f)) return 1.0 / x;
+    double y = double(__frcp_rn(xf));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
 
 // sum over lanes 0..7 (lanes 8..31 form their own groups); result in every lane of the group
 __device__ __forceinline__ double gsum8(double v) {
@@ -218,24 +249,24 @@ __device__ inline void congruence(int n, const double* M, const double* V0, doub
 __device__ __forceinline__ void phi_dphi(double lam, double gv, double alpha, double Delta, double& phi, double& dphi) {
     double qa = 0.0, qb = 0.0;
     if (gv != 0.0) {
-        double r = 1.0 / (lam + alpha);
+        double r = rcp64(lam + alpha);
         qa = gv * r;
         qb = qa * qa * r;
     }
     double pn = sqrt(gsum8(qa * qa));
     phi = pn - Delta;
-    dphi = -gsum8(qb) / pn;
+    dphi = -gsum8(qb) * rcp64(pn);
 }
 
 // Algorithm 2 (readings R1, R3, R4). lam, gv: lane values.
 __device__ inline double lm_parameter(double lam, double gv, double gh_norm, double Delta, double alpha0,
                                bool full_rank, int* iters) {
-    double u = gh_norm / Delta;
+    double u = gh_norm * rcp64(Delta);
     double lo = 0.0;
     if (full_rank) {
         double phi0, dphi0;
         phi_dphi(lam, gv, 0.0, Delta, phi0, dphi0);
-        lo = -phi0 / dphi0;
+        lo = -phi0 * rcp64(dphi0);
     }
     double alpha = alpha0;
     if (!(lo <= alpha && alpha <= u)) alpha = fmax(0.001 * u, sqrt(lo * u));
@@ -244,8 +275,8 @@ __device__ inline double lm_parameter(double lam, double gv, double gh_norm, dou
         double phi, dphi;
         phi_dphi(lam, gv, alpha, Delta, phi, dphi);
         if (fabs(phi) <= 0.1 * Delta) break;
-        double ratio = phi / dphi;
-        double at = alpha - ((phi + Delta) / Delta) * ratio;
+        double ratio = phi * rcp64(dphi);
+        double at = alpha - ((phi + Delta) * rcp64(Delta)) * ratio;
         lo = fmax(lo, alpha - ratio);
         if (phi < 0.0) u = alpha;
         alpha = (lo <= at && at <= u) ? at : fmax(0.001 * u, sqrt(lo * u));
@@ -266,8 +297,8 @@ __device__ __forceinline__ double quad_value(const double* Ah, const double* gh,
 // Largest t >= 0 with lb <= x + t s <= ub (lane values); hits = lanes that bind.
 __device__ __forceinline__ double step_to_bound(double x, double s, double lb, double ub, bool& hit) {
     double t = INFINITY;
-    if (s > 0.0) t = (ub - x) / s;
-    else if (s < 0.0) t = (lb - x) / s;
+    if (s > 0.0) t = (ub - x) * rcp64(s);
+    else if (s < 0.0) t = (lb - x) * rcp64(s);
     double tmin = gmin8(lane_id() < 8 ? t : INFINITY);
     hit = (t == tmin) && isfinite(t);
     return fmax(tmin, 0.0);
@@ -277,7 +308,7 @@ __device__ __forceinline__ double step_to_bound(double x, double s, double lb, d
 __device__ __forceinline__ double tr_intersect(double s0, double r, double Delta) {
     double a = gsum8(r * r), b = 2.0 * gsum8(s0 * r), c = gsum8(s0 * s0) - Delta * Delta;
     double disc = sqrt(fmax(b * b - 4.0 * a * c, 0.0));
-    return b <= 0.0 ? (-b + disc) / (2.0 * a) : (2.0 * c) / (-b - disc);
+    return b <= 0.0 ? (-b + disc) * rcp64(2.0 * a) : (2.0 * c) * rcp64(-b - disc);
 }
 
 // min over [t_lo, t_hi] of t -> q(s0 + t r); s0, r smem vectors, tmp scratch vector.
@@ -293,7 +324,7 @@ __device__ inline double minimize_on_segment(const double* Ah, const double* gh,
     double cand[3] = {t_lo, t_hi, t_lo};
     int nc = 2;
     if (curv > 0.0) {
-        double ts = -slope / curv;
+        double ts = -slope * rcp64(curv);
         if (t_lo < ts && ts < t_hi) { cand[2] = ts; nc = 3; }
     }
     // q(s0 + t r) = q0 + t slope + t^2 curv / 2 (exact for the quadratic model)

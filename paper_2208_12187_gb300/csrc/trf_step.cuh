@@ -1,0 +1,713 @@
+// The trust-region step of one fit, run by the CTA that completed the fit's
+// evaluation (all EVAL_THREADS threads call it; warp 0 carries the scalar and
+// n-vector logic, warps 0-3 share the FP64 8x8 matrix products).
+//
+// GB300 FP64 issues at ~1/64 of FP32 and one FP64 warp instruction occupies
+// its SM sub-partition for ~64 cycles whatever the active lanes, so:
+//   * n x n products are spread over 4 warps (one per sub-partition);
+//   * the eigen-decomposition runs its many sequential Jacobi rotations in
+//     FP32, then an FP64 refinement made of matrix products only restores
+//     FP64 accuracy (Newton-Schulz re-orthonormalisation, Rayleigh-Ritz
+//     V^T A V, and a first/second-order perturbation update); every
+//     quantity the algorithm decides on is FP64;
+//   * divisions use an FP32 reciprocal refined by two FP64 Newton steps;
+//   * norms needed by the next iteration are formed once, at step time.
+#pragma once
+#include "gbfit_internal.cuh"
+#include "models.cuh"
+#include "trf_device.cuh"
+
+namespace gbfit {
+
+__device__ __forceinline__ void trace_add(FitState* st, int phase, long long& t) {
+    long long now = clock64();
+    if (threadIdx.x == 0) st->trace[phase] += (unsigned long long)(now - t);
+    t = now;
+}
+
+__device__ __forceinline__ void trace_add_arr(unsigned long long* trace, int phase, long long& t) {
+    long long now = clock64();
+    if (threadIdx.x == 0) trace[phase] += (unsigned long long)(now - t);
+    t = now;
+}
+
+// C = op(A) B on n x n blocks of 8x8 row-major smem matrices (C must not
+// alias A or B).  Warps 0-3 (one per SM sub-partition) each take half of
+// the k range of 32 outputs; the halves meet through shared memory.  Every
+// thread of the CTA must call (two __syncthreads).
+__device__ __forceinline__ void mm8(int n, const double* A, bool tA, const double* B, double* C,
+                                    double* half) {
+    int t = threadIdx.x;
+    if (t < 128) {
+        int e = t & 63, h = t >> 6;
+        int i = e >> 3, j = e & 7;
+        double acc = 0.0;
+        int k0 = h * 4, k1 = min(n, k0 + 4);
+        if (i < n && j < n)
+            for (int k = k0; k < k1; ++k) acc = fma(tA ? A[k * 8 + i] : A[i * 8 + k], B[k * 8 + j], acc);
+        if (h) half[e] = acc;
+        __syncthreads();
+        if (!h) C[e] = acc + half[e];
+    } else {
+        __syncthreads();
+    }
+    __syncthreads();
+}
+
+// Partner of each index in round r of the parallel round-robin ordering on
+// np = 2, 4, 6, 8 indices (an index paired with itself rests that round);
+// 3 bits per index so that every lane reads the same word.
+__constant__ unsigned c_partner_packed[4][7] = {
+    {0xfac681u, 0xfac688u, 0xfac688u, 0xfac688u, 0xfac688u, 0xfac688u, 0xfac688u},
+    {0xfac053u, 0xfac4c1u, 0xfac21au, 0xfac688u, 0xfac688u, 0xfac688u, 0xfac688u},
+    {0xf814e5u, 0xf93941u, 0xfa521au, 0xf8a12bu, 0xf98a54u, 0xfac688u, 0xfac688u},
+    {0x053977u, 0x4e5dc1u, 0x97721au, 0xdca12bu, 0x298bbcu, 0x706e55u, 0xa394e6u},
+};
+
+// FP32 cyclic Jacobi, one fused pass per round (warp 0 only).  The lane
+// numbered like the smaller index of each pair forms that pair's rotation
+// (branch-free); every lane then takes the rotations its elements need by
+// shuffle and updates two elements of A' = J^T A J and of R' = R J into the
+// second buffer (one __syncwarp per round).  Relative stopping test
+// |a_pq| <= 2.5e-7 sqrt(a_pp a_qq).  A, A2, R, R2: float 8x8 smem; on return
+// *Ares / *Rres point at the results.
+__device__ int jacobi32(int n, float* A, float* A2, float* R, float* R2, int max_sweeps,
+                        float** Ares, float** Rres) {
+    const int l = threadIdx.x & 31;
+    const int np = n + (n & 1);
+    const float tol2 = 2.5e-7f * 2.5e-7f;
+    const int i0 = l >> 3, i1 = i0 + 4, j = l & 7;
+    int sweeps = 0;
+    for (; sweeps < max_sweeps; ++sweeps) {
+        bool any = false;
+        for (int r = 0; r < np - 1; ++r) {
+            const unsigned word = c_partner_packed[np / 2 - 1][r];
+            // owner lane l (< 8) rotates the pair (l, partner) when l < partner < n
+            float c = 1.0f, s = 0.0f;
+            {
+                int x = l & 7, y = (word >> (3 * x)) & 7;
+                bool own = l < 8 && x < y && y < n;
+                float app = A[x * 8 + x], aqq = A[y * 8 + y], apq = A[x * 8 + y];
+                bool act = own && (apq * apq > tol2 * fabsf(app * aqq)) && apq != 0.0f;
+                float th = __fdividef(aqq - app, 2.0f * (act ? apq : 1.0f));
+                float h = fmaf(th, th, 1.0f);
+                float t = copysignf(__fdividef(1.0f, fabsf(th) + h * rsqrtf(h)), th);
+                t = (h < 1e36f) ? t : __fdividef(0.5f, th);
+                float cc = rsqrtf(fmaf(t, t, 1.0f));
+                float ss = t * cc;
+                float nf = fmaf(-0.5f, fmaf(cc, cc, ss * ss), 1.5f);   // c^2 + s^2 -> 1
+                c = act ? cc * nf : 1.0f;
+                s = act ? ss * nf : 0.0f;
+                any |= act;
+            }
+            int pj = (word >> (3 * j)) & 7, p0 = (word >> (3 * i0)) & 7, p1 = (word >> (3 * i1)) & 7;
+            // rotation of index x: owner lane min(x, partner); coefficient on the partner is -s for the smaller index
+            float cj = __shfl_sync(FULL, c, min(j, pj)), sj = __shfl_sync(FULL, s, min(j, pj));
+            float c0 = __shfl_sync(FULL, c, min(i0, p0)), s0 = __shfl_sync(FULL, s, min(i0, p0));
+            float c1 = __shfl_sync(FULL, c, min(i1, p1)), s1 = __shfl_sync(FULL, s, min(i1, p1));
+            bool aj = sj != 0.0f;
+            sj = (j < pj) ? -sj : sj;
+            s0 = (i0 < p0) ? -s0 : s0;
+            s1 = (i1 < p1) ? -s1 : s1;
+            float x0 = c0 * (cj * A[i0 * 8 + j] + sj * A[i0 * 8 + pj]) + s0 * (cj * A[p0 * 8 + j] + sj * A[p0 * 8 + pj]);
+            float x1 = c1 * (cj * A[i1 * 8 + j] + sj * A[i1 * 8 + pj]) + s1 * (cj * A[p1 * 8 + j] + sj * A[p1 * 8 + pj]);
+            if (aj && p0 == j) x0 = 0.0f;      // the rotated pair's off-diagonal
+            if (aj && p1 == j) x1 = 0.0f;
+            A2[i0 * 8 + j] = x0;
+            A2[i1 * 8 + j] = x1;
+            R2[i0 * 8 + j] = cj * R[i0 * 8 + j] + sj * R[i0 * 8 + pj];
+            R2[i1 * 8 + j] = cj * R[i1 * 8 + j] + sj * R[i1 * 8 + pj];
+            __syncwarp();
+            float* tA = A; A = A2; A2 = tA;
+            float* tR = R; R = R2; R2 = tR;
+        }
+        if (!__any_sync(FULL, any)) break;
+    }
+    *Ares = A;
+    *Rres = R;
+    return sweeps;
+}
+
+// ---- Gauss-Newton fast path: FP32 Cholesky, FP64 iterative refinement.
+// Lower Cholesky factor of M = sc * Ah (sc = 1 / max diagonal) in FP32 into
+// L (float 8x8 smem, lower triangle; the diagonal holds 1/L_kk).  Warp 0.
+// Returns false when a pivot is not positive.  min_diag: smallest diagonal
+// entry of M.
+__device__ bool chol32(int n, const double* Ah, float* L, float& sc, float& min_diag) {
+    const int l = threadIdx.x & 31;
+    double dmax = gmax8((l < n) ? Ah[l * 8 + l] : 0.0);
+    if (!(dmax > 0.0)) return false;
+    sc = float(rcp64(dmax));
+    for (int e = l; e < 64; e += 32) {
+        int i = e >> 3, j = e & 7;
+        L[e] = (i < n && j <= i) ? float(Ah[e]) * sc : 0.0f;
+    }
+    __syncwarp();
+    bool ok = true;
+    min_diag = 1.0f;
+    for (int k = 0; k < n; ++k) min_diag = fminf(min_diag, L[k * 8 + k]);
+    for (int k = 0; k < n; ++k) {
+        float akk = L[k * 8 + k];
+        ok = ok && akk > 0.0f;
+        float rd = rsqrtf(akk > 0.0f ? akk : 1.0f);         // 1 / L_kk
+        __syncwarp();
+        if (l > k && l < n) L[l * 8 + k] *= rd;               // column k
+        if (l == k) L[k * 8 + k] = rd;
+        __syncwarp();
+        for (int e = l; e < 64; e += 32) {                    // trailing update
+            int i = e >> 3, j = e & 7;
+            if (j > k && i >= j && i < n) L[e] = fmaf(-L[i * 8 + k], L[j * 8 + k], L[e]);
+        }
+        __syncwarp();
+    }
+    return ok;
+}
+
+// z = (L L^T)^-1 b in FP32 (lane values; L from chol32 with inverse diagonal).
+__device__ __forceinline__ float cholsolve32(int n, const float* L, float b) {
+    const int l = threadIdx.x & 31;
+    for (int k = 0; k < n; ++k) {                             // L y = b
+        float yk = __shfl_sync(FULL, b, k) * L[k * 8 + k];
+        if (l == k) b = yk;
+        else if (l > k && l < n) b = fmaf(-L[l * 8 + k], yk, b);
+    }
+    for (int k = n - 1; k >= 0; --k) {                        // L^T z = y
+        float zk = __shfl_sync(FULL, b, k) * L[k * 8 + k];
+        if (l == k) b = zk;
+        else if (l < k) b = fmaf(-L[k * 8 + l], zk, b);
+    }
+    return (l < n) ? b : 0.0f;
+}
+
+// Ah p = rhs to FP64 accuracy: FP32 Cholesky solve (M = sc Ah, so
+// p = M^-1 (sc rhs)), then two rounds of FP64 residual + FP32 correction.
+// d1, d2: norms of the two corrections (FP32); their ratio estimates
+// eps32 * cond of the equilibrated matrix.  tmp: an 8-double smem vector.
+__device__ double solve_refined(int n, const double* Ah, const float* L, float sc, double rhs, double* tmp,
+                                float& d1, float& d2) {
+    const int l = threadIdx.x & 31;
+    double p = double(cholsolve32(n, L, float(rhs) * sc));
+    float dn[2];
+    for (int it = 0; it < 2; ++it) {
+        if (l < 8) tmp[l] = (l < n) ? p : 0.0;
+        __syncwarp();
+        double r = rhs - matvec8(Ah, tmp, n);
+        float dz = cholsolve32(n, L, float(r) * sc);
+        p += double(dz);
+        float q = dz * dz;
+        for (int o = 4; o; o >>= 1) q += __shfl_xor_sync(FULL, q, o);
+        dn[it] = sqrtf(__shfl_sync(FULL, q, 0));
+    }
+    d1 = dn[0];
+    d2 = dn[1];
+    return (l < n) ? p : 0.0;
+}
+
+// FP64-accurate eigen-decomposition Ah = V diag(lam) V^T (Appendix B: Ah =
+// B_hat, lam = Sigma^2).  Vwarm (global, may be null): a previous basis to
+// start from.  All CTA threads call; results in S.V and S.vec[VLAM].
+// Returns the FP32 Jacobi sweeps.
+__device__ int eig_fast(int n, const double* Ah, const double* Vwarm, TrfSmem& S,
+                        unsigned long long* trace = nullptr) {
+    const int t = threadIdx.x, warp = t >> 5, l = t & 31;
+    const bool warm = Vwarm != nullptr;
+    long long tc = clock64();
+    // 1. starting matrix in the warm basis
+    if (t < 64) {
+        int i = t >> 3, j = t & 7;
+        S.V0[t] = warm ? Vwarm[t] : ((i == j && i < n) ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    if (warm) {
+        mm8(n, Ah, false, S.V0, S.W, S.H);          // W = Ah V0
+        mm8(n, S.V0, true, S.W, S.A, S.H);          // A = V0^T Ah V0
+    } else {
+        if (t < 64) S.A[t] = Ah[t];
+        __syncthreads();
+    }
+    if (trace) trace_add_arr(trace, TR_E_WARM, tc);
+    // 2. FP32 Jacobi on A / max diag
+    int sweeps = 0;
+    if (warp == 0) {
+        double dg = (l < n) ? fabs(S.A[l * 8 + l]) : 0.0;
+        double dmax = gmax8(dg);
+        float sc = dmax > 0.0 ? float(rcp64(dmax)) : 1.0f;
+        for (int e = l; e < 64; e += 32) {
+            int i = e >> 3, j = e & 7;
+            bool in = i < n && j < n;
+            S.Af[e] = in ? float(S.A[e]) * sc : 0.0f;
+            S.Rf[e] = (i == j) ? 1.0f : 0.0f;
+        }
+        __syncwarp();
+        float *Ares, *Rres;
+        sweeps = jacobi32(n, S.Af, S.Af2, S.Rf, S.Rf2, 20, &Ares, &Rres);
+        if (Rres != S.Rf)
+            for (int e = l; e < 64; e += 32) S.Rf[e] = Rres[e];
+        if (trace && t == 0) trace[TR_E_SWEEPS] += sweeps;
+    }
+    __syncthreads();
+    if (trace) trace_add_arr(trace, TR_E_J32, tc);
+    // 3. V = V0 R (or R)
+    if (t < 64) S.W[t] = double(S.Rf[t]);
+    __syncthreads();
+    if (warm) mm8(n, S.V0, false, S.W, S.V, S.H);
+    else { if (t < 64) S.V[t] = S.W[t]; __syncthreads(); }
+    // 4. Newton-Schulz: V <- V (3 I - V^T V) / 2
+    mm8(n, S.V, true, S.V, S.A, S.H);               // G = V^T V
+    if (t < 64) { int i = t >> 3, j = t & 7; S.W[t] = (i == j ? 1.5 : 0.0) - 0.5 * S.A[t]; }
+    __syncthreads();
+    mm8(n, S.V, false, S.W, S.V0, S.H);             // V0 <- V T
+    if (trace) trace_add_arr(trace, TR_E_NS, tc);
+    // 5-6. Rayleigh-Ritz A1 = V^T Ah V and perturbation update
+    //    X_rc = A1_rc / (A1_cc - A1_rr), V <- V (I + X),
+    //    lam_c = A1_cc + sum_r A1_rc^2 / (A1_cc - A1_rr);
+    //    repeated once more when the first correction was not already tiny.
+    for (int pass = 0; pass < 2; ++pass) {
+        mm8(n, Ah, false, S.V0, S.W, S.H);
+        mm8(n, S.V0, true, S.W, S.A, S.H);
+        if (t < 64) {
+            int r = t >> 3, c = t & 7;
+            double x = 0.0;
+            if (r < n && c < n && r != c) {
+                double a = S.A[t];
+                double gap = S.A[c * 8 + c] - S.A[r * 8 + r];
+                float gf = float(gap), af = float(a);
+                if (fabsf(gf) > 1e3f * fabsf(af) && fabsf(gf) > 1e-30f) x = double(af * __frcp_rn(gf));
+            }
+            S.W[t] = x;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double lam = 0.0;
+            if (l < n) {
+                lam = S.A[l * 8 + l];
+                for (int r = 0; r < n; ++r)
+                    if (r != l) lam = fma(S.A[r * 8 + l], S.W[r * 8 + l], lam);
+            }
+            if (l < 8) S.vec[VLAM][l] = lam;
+            // largest correction decides whether a second pass is needed
+            float xm = 0.0f;
+            for (int e = l; e < 64; e += 32) xm = fmaxf(xm, fabsf(float(S.W[e])));
+            for (int o = 16; o; o >>= 1) xm = fmaxf(xm, __shfl_xor_sync(FULL, xm, o));
+            if (l == 0) S.si[7] = (xm > 1e-9f) ? 1 : 0;
+        }
+        __syncthreads();
+        mm8(n, S.V0, false, S.W, S.A, S.H);             // A = V X
+        if (t < 64) S.V0[t] += S.A[t];
+        __syncthreads();
+        if (trace && t == 0) trace[TR_E_REFINES] += 1;
+        if (!S.si[7]) break;
+    }
+    if (t < 64) S.V[t] = S.V0[t];
+    __syncthreads();
+    if (trace) trace_add_arr(trace, TR_E_RR, tc);
+    return sweeps;
+}
+
+// Coleman-Li scaling at the current x, g (lane values; lanes >= n: v = dv = 0).
+__device__ __forceinline__ void cl_scaling(const FitDesc& d, const FitState* st, const TrfSmem& S, int n,
+                                           double& v, double& dv, double& sx) {
+    int l = threadIdx.x & 31;
+    v = 0.0; dv = 0.0; sx = 1.0;
+    if (l < n) {
+        double x = S.vec[VX][l], g = S.vec[VG][l];
+        double lb = d.lb[l], ub = d.ub[l];
+        v = 1.0;
+        if (d.bounded) {
+            if (g < 0.0 && ub < INFINITY) { v = ub - x; dv = -1.0; }
+            else if (g > 0.0 && lb > -INFINITY) { v = x - lb; dv = 1.0; }
+        }
+        sx = d.jac_scale ? rcp64(st->scale_inv[l]) : d.xscale[l];
+    }
+}
+
+// Pass constants for evaluating xt relative to x (warp 0).
+template <int PREC>
+__device__ void prep_pass(const FitDesc& d, FitState* st, TrfSmem& S) {
+    int l = threadIdx.x & 31;
+    int n = d.n;
+    if (PREC == PREC_MIXED) {
+        if (l < n) {
+            double x = S.vec[VX][l], xt = S.vec[VXT][l];
+            float xf = float(x);
+            S.mp.x[l] = xf;
+            S.mp.xlo[l] = float(x - double(xf));
+            S.mp.xt[l] = float(xt);
+            S.mp.dx[l] = float(xt - x);
+        }
+        __syncwarp();
+        if (l == 0) {
+            for (int k = 0; k < PF; ++k) S.pfs[k] = 0.0f;
+            switch (d.model) {
+                case 0: MGauss1D::prep_mixed(S.mp, S.pfs); break;
+                case 1: MDexp::prep_mixed(S.mp, S.pfs); break;
+                case 2: MGauss2D::prep_mixed(S.mp, S.pfs); break;
+                case 3: MPoly2::prep_mixed(S.mp, S.pfs); break;
+            }
+        }
+        __syncwarp();
+        st->pf[l] = S.pfs[l];
+    } else {
+        if (l == 0) {
+            for (int k = 0; k < PD; ++k) S.pds[k] = 0.0;
+            switch (d.model) {
+                case 0: MGauss1D::prep_plain(S.vec[VXT], S.pds); break;
+                case 1: MDexp::prep_plain(S.vec[VXT], S.pds); break;
+                case 2: MGauss2D::prep_plain(S.vec[VXT], S.pds); break;
+                case 3: MPoly2::prep_plain(S.vec[VXT], S.pds); break;
+            }
+        }
+        __syncwarp();
+        if (l < PD) st->pd[l] = S.pds[l];
+    }
+    __syncwarp();
+}
+
+// Result record with pcov (R13) from an FP64-accurate eigen-decomposition of
+// the unscaled Gram at the solution.  All CTA threads call.
+__device__ void write_result(const FitDesc& d, FitState* st, FitResult* res, int status, TrfSmem& S) {
+    const int n = d.n, t = threadIdx.x;
+    if (t < n) res->popt[t] = st->x[t];
+    for (int k = t; k < KMAX; k += EVAL_THREADS) res->tot[k] = S.tot[k];
+    if (t == 0) { res->cost = st->f; res->nfev = st->nfev; res->njev = st->njev; res->fit_status = status; }
+    bool ok = (status >= 0) && d.m > n;
+    if (!ok) {
+        if (t < 64) res->pcov[t] = INFINITY;
+        __syncthreads();
+        return;
+    }
+    __syncthreads();
+    eig_fast(n, S.B, nullptr, S);
+    if (t < 32) {
+        int l = t;
+        double lam = (l < n) ? S.vec[VLAM][l] : 0.0;
+        double lmax = gmax8(l < n ? lam : -INFINITY);
+        double inv = (l < n && lmax > 0.0 && lam > lmax * (8.0 * n * EPS64)) ? rcp64(lam) : 0.0;
+        if (l < 8) S.vec[VTMP][l] = inv;
+    }
+    __syncthreads();
+    double scale = d.absolute_sigma ? 1.0 : 2.0 * st->f / double(d.m - n);
+    if (t < 64) {
+        int i = t >> 3, j = t & 7;
+        if (i < n && j < n) {
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc = fma(S.V[i * 8 + k] * S.vec[VTMP][k], S.V[j * 8 + k], acc);
+            res->pcov[i * n + j] = acc * scale;
+        }
+    }
+    __syncthreads();
+}
+
+// Scalar slots of TrfSmem::sd / si shared between the phases.
+enum { SD_F = 0, SD_DELTA, SD_ALPHA, SD_GNORM };
+enum { SI_STATUS = 0, SI_NFEV, SI_NJEV, SI_FACTOR, SI_GN };
+
+// One trust-region iteration for one fit.  S.tot holds the combined sums of
+// the evaluation at st->xt that just finished.
+template <int PREC>
+__device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem& S, int* running) {
+    const int n = d.n;
+    const int t = threadIdx.x, warp = t >> 5, l = t & 31;
+    const int NT = n_tri(n);
+    long long tclk = clock64();
+
+    // ================= phase 1 (warp 0): accept / reject, termination tests
+    if (warp == 0) {
+        if (l < n) {
+            S.vec[VX][l] = st->x[l];
+            S.vec[VXT][l] = st->xt[l];
+            S.vec[VG][l] = st->g[l];
+        }
+        const bool init = st->phase == PH_INIT;
+        const double* srcB = init ? S.tot : st->B;   // packed upper triangle
+        for (int e = l; e < 64; e += 32) {
+            int i = e >> 3, j = e & 7;
+            double b = 0.0;
+            if (i < n && j < n) { int a = min(i, j), c = max(i, j); b = srcB[a * n - a * (a - 1) / 2 + (c - a)]; }
+            S.B[e] = b;
+        }
+        __syncwarp();
+        const double f2n = S.tot[NT + n];
+        int status = FS_RUNNING;
+        double f = st->f, Delta = st->Delta, alpha = st->alpha;
+        int nfev = st->nfev, njev = st->njev, factor_valid = st->factor_valid;
+        bool take = false;
+        if (init) {
+            take = true;
+            f = 0.5 * f2n;
+            nfev = 1; njev = 1;
+            bool fin = (l >= NT + n + 1 || isfinite(S.tot[l])) && (l + 32 >= NT + n + 1 || isfinite(S.tot[l + 32]));
+            fin = __all_sync(FULL, fin);
+            if (st->bad_data) status = FS_INVALID_DATA;
+            else if (!fin) status = FS_NUMERICAL;
+        } else {
+            nfev += 1;
+            double f_new = 0.5 * f2n;
+            double actual = (PREC == PREC_MIXED) ? -0.5 * S.tot[NT + n + 1] : f - f_new;
+            double pred = st->predicted;
+            double gamma = (isfinite(f_new) && isfinite(actual) && pred > 0.0) ? actual * rcp64(pred) : -INFINITY;
+            bool accepted;
+            double Dn;
+            if (gamma > 0.75) { accepted = true; Dn = 2.0 * Delta; }
+            else if (gamma >= 0.25 && gamma <= 0.75) { accepted = true; Dn = Delta; }
+            else { accepted = false; Dn = 0.25 * st->s_norm; }
+            bool ftol_ok = accepted && actual < d.ftol * f;
+            bool xtol_ok = st->step_norm < st->xtol_thr;
+            if (accepted) { take = true; f = f_new; njev += 1; factor_valid = 0; }
+            Delta = Dn;
+            if (ftol_ok && xtol_ok) status = FS_FTOL_XTOL;
+            else if (ftol_ok) status = FS_FTOL;
+            else if (xtol_ok) status = FS_XTOL;
+        }
+        if (take) {
+            if (l < n) { S.vec[VX][l] = S.vec[VXT][l]; S.vec[VG][l] = S.tot[NT + l]; }
+            for (int e = l; e < 64; e += 32) {
+                int i = e >> 3, j = e & 7;
+                double b = 0.0;
+                if (i < n && j < n) { int a = min(i, j), c = max(i, j); b = S.tot[a * n - a * (a - 1) / 2 + (c - a)]; }
+                S.B[e] = b;
+            }
+            __syncwarp();
+            if (d.jac_scale && status == FS_RUNNING && l < n) {
+                double c = sqrt(S.B[l * 8 + l]);
+                if (!init) c = fmax(c, st->scale_inv[l]);
+                st->scale_inv[l] = (c == 0.0) ? 1.0 : c;
+            }
+            __syncwarp();
+        }
+        double gnorm = 0.0;
+        if (status == FS_RUNNING) {
+            double v, dv, sx;
+            cl_scaling(d, st, S, n, v, dv, sx);
+            if (init) {
+                double xl = (l < n) ? S.vec[VX][l] : 0.0;
+                double dd = (l < n) ? (d.bounded ? sqrt(v) : 1.0) * sx : 1.0;
+                double q = (l < n) ? xl * rcp64(dd) : 0.0;
+                Delta = sqrt(gsum8(q * q));
+                if (Delta == 0.0) Delta = 1.0;
+                alpha = 0.0;
+                factor_valid = 0;
+            }
+            double g = (l < n) ? S.vec[VG][l] : 0.0;
+            gnorm = gmax8(fabs(v * g));
+            if (gnorm < d.gtol) status = FS_GTOL;
+            else if (nfev >= d.max_nfev) status = FS_MAX_NFEV;
+        }
+        if (l == 0) {
+            S.sd[SD_F] = f; S.sd[SD_DELTA] = Delta; S.sd[SD_ALPHA] = alpha; S.sd[SD_GNORM] = gnorm;
+            S.si[SI_STATUS] = status; S.si[SI_NFEV] = nfev; S.si[SI_NJEV] = njev; S.si[SI_FACTOR] = factor_valid;
+            st->factor_valid = factor_valid;   // the eigen cache describes the current B only
+        }
+    }
+    __syncthreads();
+    trace_add(st, TR_LOGIC, tclk);
+
+    const int status = S.si[SI_STATUS];
+    if (status != FS_RUNNING) {
+        if (t == 0) { st->f = S.sd[SD_F]; st->nfev = S.si[SI_NFEV]; st->njev = S.si[SI_NJEV]; st->Delta = S.sd[SD_DELTA]; }
+        if (t < n) st->x[t] = S.vec[VX][t];
+        __syncthreads();
+        write_result(d, st, res, status, S);
+        trace_add(st, TR_FINISH, tclk);
+        if (t == 0) { st->run = RS_DONE; st->fit_status = status; atomicSub(running, 1); }
+        if (t < 24) res->trace[t] = double(st->trace[t]);
+        return;
+    }
+
+    // ================= phase 2 (warp 0): scaled model matrix Ah = D B D + diag(C)
+    if (warp == 0) {
+        double v, dv, sx;
+        cl_scaling(d, st, S, n, v, dv, sx);
+        double g = (l < n) ? S.vec[VG][l] : 0.0;
+        double dl = (l < n) ? (d.bounded ? sqrt(v) : 1.0) * sx : 0.0;
+        if (l < 8) {
+            S.vec[VD][l] = dl;
+            S.vec[VGH][l] = dl * g;
+            S.vec[VC][l] = (l < n && d.bounded) ? g * dv * sx * sx : 0.0;
+        }
+        __syncwarp();
+        for (int e = l; e < 64; e += 32) {
+            int i = e >> 3, j = e & 7;
+            double a = 0.0;
+            if (i < n && j < n) a = fma(S.vec[VD][i] * S.vec[VD][j], S.B[e], (i == j) ? S.vec[VC][i] : 0.0);
+            S.Ah[e] = a;
+        }
+    }
+    __syncthreads();
+
+    // ================= Gauss-Newton fast path (warp 0): when B_hat is safely
+    // full rank (no eigenvalue near the rank cutoff) and the trial step lies in
+    // the region, the step needs no eigen-decomposition.
+    // Guard: the refinement must contract (ratio ~ eps32 cond of the
+    // equilibrated matrix), and lambda_min >= min_diag / cond must stay far
+    // above the rank cutoff lambda_max 8 n eps64 (lambda_max <= n here), so
+    // that the pseudo-inverse of the eigen path would drop nothing.
+    if (warp == 0) {
+        float sc = 1.0f, mind = 0.0f;
+        bool ok = chol32(n, S.Ah, S.Lf, sc, mind);
+        ok = __all_sync(FULL, ok);
+        bool inside = false;
+        if (ok) {
+            double gh = (l < n) ? S.vec[VGH][l] : 0.0;
+            float d1, d2;
+            double pt = solve_refined(n, S.Ah, S.Lf, sc, -gh, S.vec[VTMP], d1, d2);
+            float cond = fmaxf(1.0f, __fdividef(d2, fmaxf(d1, 1e-37f) * 6e-8f));
+            ok = (d2 <= 1e-3f * d1 || d2 == 0.0f) && __fdividef(mind, cond) > 1e-11f;
+            double Delta = S.sd[SD_DELTA];
+            inside = gsum8(pt * pt) <= Delta * Delta;
+            if (l < 8) S.vec[VSTR][l] = pt;
+        }
+        if (l == 0) {
+            S.si[SI_GN] = (ok && inside) ? 1 : 0;
+            if (ok && inside) st->trace[TR_N_GN] += 1;
+        }
+    }
+    __syncthreads();
+    trace_add(st, TR_GN, tclk);
+
+    // ================= factorisation (all threads), reused after a rejection
+    if (S.si[SI_GN]) {
+        // not needed
+    } else if (!S.si[SI_FACTOR]) {
+        int sw = eig_fast(n, S.Ah, st->has_basis ? st->V : nullptr, S, st->trace);
+        if (t < 64) st->V[t] = S.V[t];
+        if (t < 8) st->lam[t] = S.vec[VLAM][t];
+        if (t == 0) { st->has_basis = 1; st->factor_valid = 1; st->jacobi_sweeps = sw; st->trace[TR_N_EIG] += 1; }
+    } else {
+        if (t < 64) S.V[t] = st->V[t];
+        if (t < 8) S.vec[VLAM][t] = st->lam[t];
+    }
+    __syncthreads();
+    trace_add(st, TR_EIGEN, tclk);
+
+    // ================= phase 3 (warp 0): step
+    if (warp == 0) {
+        double Delta = S.sd[SD_DELTA], alpha = S.sd[SD_ALPHA], gnorm = S.sd[SD_GNORM];
+        double gh = (l < n) ? S.vec[VGH][l] : 0.0;
+        double dl = (l < n) ? S.vec[VD][l] : 0.0;
+        const bool gn = S.si[SI_GN] != 0;
+        double theta = fmax(0.995, 1.0 - gnorm);
+        int a2it = 0;
+        if (gn) alpha = 0.0;
+        else {
+        // gV = V^T g_hat
+        double gV;
+        {
+            int i = l >> 2, j = l & 3;
+            double acc = 0.0;
+            if (i < n) {
+                if (j < n) acc = S.V[j * 8 + i] * S.vec[VGH][j];
+                if (j + 4 < n) acc = fma(S.V[(j + 4) * 8 + i], S.vec[VGH][j + 4], acc);
+            }
+            acc += __shfl_xor_sync(FULL, acc, 1);
+            acc += __shfl_xor_sync(FULL, acc, 2);
+            gV = __shfl_sync(FULL, acc, (l & 7) << 2);
+            if (l >= n) gV = 0.0;
+        }
+        double lam = (l < n) ? S.vec[VLAM][l] : 0.0;
+        double lmax = gmax8(l < n ? lam : -INFINITY);
+        bool keep = (l < n) && lmax > 0.0 && lam > lmax * (8.0 * n * EPS64);
+        if (!keep) { gV = 0.0; lam = 0.0; }
+        bool full_rank = __all_sync(FULL, keep || l >= n);
+        // Algorithm 1: Gauss-Newton trial step, else Algorithm 2
+        double comp = (gV != 0.0) ? gV * rcp64(lam) : 0.0;
+        double ptn2 = gsum8(comp * comp);
+        if (ptn2 <= Delta * Delta) {
+            alpha = 0.0;
+        } else {
+            double ghn = sqrt(gsum8(gh * gh));
+            alpha = lm_parameter(lam, gV, ghn, Delta, alpha, full_rank, &a2it);
+            comp = (gV != 0.0) ? gV * rcp64(lam + alpha) : 0.0;
+        }
+        vstore(S.vec[VTMP], n, comp);
+        double s_tr0 = -matvec8(S.V, S.vec[VTMP], n);
+        vstore(S.vec[VSTR], n, s_tr0);
+        }
+        const double s_tr = (l < n) ? S.vec[VSTR][l] : 0.0;
+        double sh = s_tr, qval;
+        int kind = 0;
+        if (d.bounded) {
+            double x = (l < n) ? S.vec[VX][l] : 0.0;
+            double lbl = (l < n) ? d.lb[l] : -INFINITY, ubl = (l < n) ? d.ub[l] : INFINITY;
+            double sfull = dl * s_tr;
+            bool inside = __all_sync(FULL, l >= n || (x + sfull >= lbl && x + sfull <= ubl));
+            qval = quad_value(S.Ah, S.vec[VGH], S.vec[VSTR], n);
+            if (!inside) {
+                bool hit;
+                double tau = step_to_bound(x, (l < n) ? sfull : 0.0, lbl, ubl, hit);
+                double sA = theta * tau * s_tr;                         // A: truncated
+                vstore(S.vec[VTMP], n, sA);
+                double best = quad_value(S.Ah, S.vec[VGH], S.vec[VTMP], n);
+                sh = sA; kind = 1;
+                double sb = tau * s_tr;                                 // B: reflected
+                double rh = hit ? -s_tr : s_tr;
+                double xb = x + dl * sb;
+                bool hit2;
+                double t_box = step_to_bound(xb, (l < n) ? dl * rh : 0.0, lbl, ubl, hit2);
+                double t_tr = tr_intersect(l < n ? sb : 0.0, l < n ? rh : 0.0, Delta);
+                double t_max = fmin(t_box, t_tr);
+                if (t_max > 0.0) {
+                    double t_lo = (1.0 - theta) * t_max;
+                    double t_hi = (t_box <= t_tr) ? theta * t_box : t_tr;
+                    if (t_lo <= t_hi) {
+                        vstore(S.vec[VTMP], n, sb);
+                        vstore(S.vec[VSH], n, rh);
+                        double tB;
+                        double vB = minimize_on_segment(S.Ah, S.vec[VGH], S.vec[VTMP], S.vec[VSH], nullptr, n, t_lo, t_hi, tB);
+                        if (vB < best) { best = vB; sh = sb + tB * rh; kind = 2; }
+                    }
+                }
+                double ag = -gh;                                        // C: scaled anti-gradient
+                double agn = sqrt(gsum8(ag * ag));
+                if (agn > 0.0) {
+                    double t_tr2 = Delta * rcp64(agn);
+                    bool hit3;
+                    double t_box2 = step_to_bound(x, (l < n) ? dl * ag : 0.0, lbl, ubl, hit3);
+                    double t_hi = (t_box2 < t_tr2) ? theta * t_box2 : t_tr2;
+                    vstore(S.vec[VTMP], n, 0.0);
+                    vstore(S.vec[VSH], n, ag);
+                    double tC;
+                    double vC = minimize_on_segment(S.Ah, S.vec[VGH], S.vec[VTMP], S.vec[VSH], nullptr, n, 0.0, t_hi, tC);
+                    if (vC < best) { best = vC; sh = tC * ag; kind = 3; }
+                }
+                qval = best;
+            }
+        } else {
+            qval = quad_value(S.Ah, S.vec[VGH], S.vec[VSTR], n);
+        }
+        if (l >= n) sh = 0.0;
+        double step = dl * sh;
+        double x = (l < n) ? S.vec[VX][l] : 0.0;
+        double xt = x + step;
+        if (d.bounded && l < n) {
+            if (xt <= d.lb[l]) xt = nextafter(d.lb[l], INFINITY);
+            if (xt >= d.ub[l]) xt = nextafter(d.ub[l], -INFINITY);
+        }
+        if (l < 8) S.vec[VXT][l] = (l < n) ? xt : 0.0;
+        // ||s_h||, ||w||, ||x|| for the next iteration's radius and xtol tests
+        double ss = gsum8(sh * sh), ww = gsum8(step * step), xx = gsum8(x * x);
+        double nv = (l == 0) ? ss : (l == 1) ? ww : xx;
+        nv = sqrt(nv);
+        double s_norm = __shfl_sync(FULL, nv, 0), w_norm = __shfl_sync(FULL, nv, 1), x_norm = __shfl_sync(FULL, nv, 2);
+        if (l < n) { st->x[l] = x; st->xt[l] = xt; st->g[l] = S.vec[VG][l]; st->s_h[l] = sh; }
+        for (int k = l; k < NT; k += 32) {
+            int a = 0, r = k;
+            while (r >= n - a) { r -= n - a; ++a; }
+            st->B[k] = S.B[a * 8 + a + r];
+        }
+        if (l == 0) {
+            st->f = S.sd[SD_F]; st->Delta = Delta; st->alpha = alpha; st->nfev = S.si[SI_NFEV];
+            st->njev = S.si[SI_NJEV]; st->predicted = -qval;
+            st->step_norm = w_norm; st->s_norm = s_norm; st->xtol_thr = d.xtol * (d.xtol + x_norm);
+            st->phase = PH_TRIAL; st->last_kind = kind; st->alg2_iters = a2it;
+            st->trace[TR_N_ALG2IT] += a2it;
+            st->trace[TR_N_BOUNDED] += (kind != 0);
+        }
+        __syncwarp();
+    }
+    trace_add(st, TR_STEP, tclk);
+    if (warp == 0) prep_pass<PREC>(d, st, S);
+    trace_add(st, TR_PREP, tclk);
+}
+
+}  // namespace gbfit

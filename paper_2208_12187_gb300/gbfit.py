@@ -50,7 +50,12 @@ class Options(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int64), ("fits", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("graph_rounds", ctypes.c_int64), ("passes", ctypes.c_int64), ("point_passes", ctypes.c_double),
-                ("eval_ms", ctypes.c_double), ("eval_launches", ctypes.c_int64)]
+                ("eval_ms", ctypes.c_double), ("eval_launches", ctypes.c_int64),
+                ("phase_cycles", ctypes.c_double * 24)]
+
+PHASES = ["tile", "combine", "logic", "eigen", "comb_fence", "step", "prep", "finish", "comb_group", "comb_final",
+          "eig_warm", "eig_j32", "eig_ns", "eig_rr", "j32_sweeps", "refine_passes", "gn_path", "n_gn", "n_eig",
+          "n_alg2_iters", "n_bounded_nonfull", "spare1", "spare2", "spare3"]
 
 
 _LIB = None
@@ -282,7 +287,9 @@ def stats() -> dict:
     """Process-wide counters (calls, fits, kernel launches, passes, profiled eval time)."""
     st = Stats()
     _check(load().gbfit_stats_get(ctypes.byref(st)))
-    return {name: getattr(st, name) for name, _ in Stats._fields_}
+    out = {name: getattr(st, name) for name, _ in Stats._fields_ if name != "phase_cycles"}
+    out["phase_cycles"] = dict(zip(PHASES, list(st.phase_cycles)))
+    return out
 
 
 def set_profiling(on: bool):

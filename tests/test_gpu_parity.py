@@ -107,9 +107,11 @@ def test_tr_subproblem_matches_oracle(seed):
         p, alpha, lg = gbfit.tr_subproblem(B, g, Delta, 0.0)
         le, V = np.linalg.eigh(B)
         pe, ae = trf.tr_solve(le, V, V.T @ g, np.linalg.norm(g), Delta, 0.0, True)
-        np.testing.assert_allclose(np.sort(lg), le, rtol=1e-12)
+        # FP64 results from FP32 rotations + FP64 refinement: eigenvalues to
+        # 1e-12 of the largest, the step to 1e-9 of its norm
+        np.testing.assert_allclose(np.sort(lg), le, rtol=0, atol=1e-12 * le.max())
         assert alpha == pytest.approx(ae, rel=1e-9, abs=1e-12)
-        np.testing.assert_allclose(p, pe, rtol=1e-9, atol=1e-12 * np.linalg.norm(pe))
+        assert np.linalg.norm(p - pe) <= 1e-9 * np.linalg.norm(pe)
 
 
 # ------------------------------------------------------------------ whole fits, plain FP64
