@@ -180,6 +180,34 @@ int gbfit_tr_subproblem(int n, const double* B, const double* g, double Delta, d
                         double* p, double* alpha, double* lam, void* cuda_stream);
 
 /*
+ * gbfit_evaluate without any device or pinned-host allocation (the paper has
+ * no counterpart; it exists for callers that may not allocate at call time:
+ * code inside host callbacks or allocation-free stream captures, under an
+ * allocator that owns all device memory, or in loops that cannot afford an
+ * allocation's implicit synchronisation).  Same arguments and output as
+ * gbfit_evaluate, with these differences:
+ *   - xdata, ydata and sigma must be device pointers (no staging copy);
+ *   - the pass's scratch (tile and group partial sums, arrival counters, the
+ *     one-fit job record) lives in a fixed file-scope device array of about
+ *     1.2 MB that every GPU loading the library keeps until the process exits;
+ *     at most 2048 reduction tiles fit, i.e. m <= 33,554,432 points at the
+ *     largest default tile (16384 points); larger requests fail with
+ *     GBFIT_E_INVALID_ARG and a message giving the limit;
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture;
+ *   - every call reuses the same array (each call re-initialises what must
+ *     start at zero); calls are serialised by a host lock and each returns
+ *     only after its results are back, but work of two calls that overlapped
+ *     on the GPU would race on the array.
+ */
+int gbfit_evaluate_noalloc(int model_id,
+                           const void* xdata, int64_t m, int x_layout, const int64_t* grid_wh,
+                           const void* ydata, const void* sigma, int dtype,
+                           const double* p, int precision, int tile_points,
+                           double* out, void* cuda_stream);
+
+/*
  * Runtime counters and per-launch timing (the per-operation timing the paper
  * reports in Section 4 / Fig. 3, taken here with CUDA events).
  * Counters are process-wide and accumulate over calls until reset.

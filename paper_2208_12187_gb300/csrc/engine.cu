@@ -672,3 +672,151 @@ int gbfit_tr_subproblem(int n, const double* B, const double* g, double Delta, d
 }
 
 }  // extern "C"
+
+// ====================================================================== allocation-free evaluation
+// gbfit_evaluate_noalloc serves callers that may not allocate memory on the
+// device at call time: code running where cudaMalloc / cudaFree are not
+// allowed or not wanted (inside a host callback, during a stream capture
+// that must not contain allocations, under a custom allocator that owns
+// all device memory, or in a latency-critical loop where an allocation's
+// implicit synchronisation is unacceptable).  The fused reduction pass needs
+// scratch memory for its per-tile and per-group partial sums, its arrival
+// counters and its one-fit job record; here all of it lives in the
+// file-scope device array below, of fixed size, which every GPU that loads
+// this library holds until the process exits.
+namespace {
+constexpr int NOALLOC_MAX_TILES = 2048;                                   // reduction tiles per call
+constexpr int NOALLOC_MAX_GROUPS = (NOALLOC_MAX_TILES + GROUP_TILES - 1) / GROUP_TILES;
+
+struct NoAllocLayout {
+    static constexpr size_t eng = 0;
+    static constexpr size_t desc = eng + ((sizeof(Engine) + 255) / 256) * 256;
+    static constexpr size_t state = desc + ((sizeof(FitDesc) + 255) / 256) * 256;
+    static constexpr size_t items = state + ((sizeof(FitState) + 255) / 256) * 256;
+    static constexpr size_t gcnt = items + ((NOALLOC_MAX_TILES * sizeof(WorkItem) + 255) / 256) * 256;
+    static constexpr size_t fcnt = gcnt + ((NOALLOC_MAX_GROUPS * sizeof(int) + 255) / 256) * 256;
+    static constexpr size_t res_hdr = fcnt + 256;                          // end of the uploaded image
+    static constexpr size_t res = res_hdr + 256;
+    static constexpr size_t tp = res + ((sizeof(FitResult) + 255) / 256) * 256;
+    static constexpr size_t tpd = tp + ((size_t(NOALLOC_MAX_TILES) * KMAX * sizeof(float) + 255) / 256) * 256;
+    static constexpr size_t gp = tpd + ((size_t(NOALLOC_MAX_TILES) * KMAX * sizeof(double) + 255) / 256) * 256;
+    static constexpr size_t end = gp + ((size_t(NOALLOC_MAX_GROUPS) * KMAX * sizeof(double) + 255) / 256) * 256;
+};
+constexpr size_t NOALLOC_SCRATCH_BYTES = NoAllocLayout::end;             // about 1.2 MB
+
+std::mutex g_noalloc_mu;
+char* g_noalloc_dev[64] = {};                                            // device address, per device
+alignas(256) char g_noalloc_host[NoAllocLayout::res_hdr];                // upload image (static, not heap)
+alignas(256) char g_noalloc_result[NoAllocLayout::tp - NoAllocLayout::res_hdr];
+}  // namespace
+
+// The scratch array.  In host code this name is only a host-side stand-in
+// for the symbol; its device address is obtained with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+extern "C" int gbfit_evaluate_noalloc(int model_id, const void* xdata, int64_t m, int x_layout,
+                                      const int64_t* grid_wh, const void* ydata, const void* sigma, int dtype,
+                                      const double* p, int precision, int tile_points, double* out,
+                                      void* cuda_stream) {
+    int n, rc;
+    if ((rc = check_common(model_id, x_layout, dtype, ydata, &n))) return rc;
+    if (!p || !out) return fail(GBFIT_E_INVALID_ARG, "p and out must not be NULL");
+    if (precision != GBFIT_PREC_FP64 && precision != GBFIT_PREC_MIXED) return fail(GBFIT_E_INVALID_ARG, "unknown precision %d", precision);
+    if (tile_points < 0 || tile_points > (1 << 24)) return fail(GBFIT_E_INVALID_ARG, "tile_points out of range");
+    if (m < n) return fail(GBFIT_E_INVALID_ARG, "m = %lld < n = %d", (long long)m, n);
+    int64_t gw = 0;
+    if (x_layout == GBFIT_X_GRID) {
+        if (!grid_wh || grid_wh[0] <= 0 || grid_wh[1] <= 0 || grid_wh[0] * grid_wh[1] != m)
+            return fail(GBFIT_E_INVALID_ARG, "grid_wh must give W*H == m");
+        gw = grid_wh[0];
+    } else if (!xdata) {
+        return fail(GBFIT_E_INVALID_ARG, "xdata is NULL");
+    }
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return fail(GBFIT_E_INVALID_ARG, "p[%d] is not finite", i);
+    const int tp = choose_tile(m, tile_points);
+    const int64_t ntiles = (m + tp - 1) / tp;
+    if (ntiles > NOALLOC_MAX_TILES)
+        return fail(GBFIT_E_INVALID_ARG,
+                    "m = %lld needs %lld reduction tiles of %d points; the allocation-free entry point holds at "
+                    "most %d tiles (m <= %lld points at the largest default tile)",
+                    (long long)m, (long long)ntiles, tp, NOALLOC_MAX_TILES, (long long)NOALLOC_MAX_TILES * 16384);
+    if (!is_device_ptr(ydata) || (xdata && x_layout != GBFIT_X_GRID && !is_device_ptr(xdata)) ||
+        (sigma && !is_device_ptr(sigma)))
+        return fail(GBFIT_E_INVALID_ARG, "the allocation-free entry point needs device-resident data arrays");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(GBFIT_E_CUDA, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_dev[dev]) {
+        // one-time set-up on this device (this device is current): the
+        // device address of the scratch array
+        void* ptr = nullptr;
+        CUDA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        g_noalloc_dev[dev] = (char*)ptr;
+    }
+    char* base = g_noalloc_dev[dev];
+    int sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int prec = precision;
+    int bps = eval_blocks_per_sm(prec);
+    if (bps < 1) bps = 1;
+    // ---- the job image: engine header, descriptor, initial state, work
+    //      items and zeroed arrival counters (everything that must start at
+    //      zero is part of the upload)
+    typedef NoAllocLayout LY;
+    memset(g_noalloc_host, 0, sizeof g_noalloc_host);
+    Engine E;
+    memset(&E, 0, sizeof E);
+    Engine* Ed = (Engine*)(base + LY::eng);
+    E.results = (FitResult*)(base + LY::res);
+    E.out = (int*)(base + LY::res_hdr);
+    E.desc = (FitDesc*)(base + LY::desc);
+    E.state = (FitState*)(base + LY::state);
+    E.items = (WorkItem*)(base + LY::items);
+    E.group_cnt = (int*)(base + LY::gcnt);
+    E.fit_cnt = (int*)(base + LY::fcnt);
+    E.tile_part = (float*)(base + LY::tp);
+    E.tile_part_d = (double*)(base + LY::tpd);
+    E.group_part = (double*)(base + LY::gp);
+    E.n_items = &Ed->sc[0]; E.running = &Ed->sc[1]; E.rounds = &Ed->sc[2];
+    E.max_rounds = &Ed->sc[3]; E.nfits_dev = &Ed->sc[4];
+    E.sc[0] = (int)ntiles; E.sc[1] = 1; E.sc[2] = 0; E.sc[3] = 2; E.sc[4] = 1;
+    memcpy(g_noalloc_host + LY::eng, &E, sizeof E);
+    gbfit_options o = defaults();
+    o.precision = prec;
+    o.tile_points = tile_points;
+    o.max_nfev = 1;
+    FitArgs a{model_id, n, x_layout, dtype, m, gw, xdata, nullptr, ydata, sigma, p, nullptr, nullptr};
+    FitDesc d;
+    fill_desc(d, a, o, false, m, tile_points);
+    size_t es = dtype == GBFIT_F64 ? 8 : 4;
+    d.x = x_layout == GBFIT_X_GRID ? nullptr : xdata;
+    d.x2 = (x_layout == GBFIT_X_SOA2) ? (const char*)xdata + (size_t)m * es : nullptr;
+    d.y = ydata;
+    d.w = sigma;
+    d.wkind = sigma ? W_SIGMA : W_NONE;        // 1/sigma formed in the kernel: no staging buffer
+    d.tile_base = 0;
+    d.group_base = 0;
+    memcpy(g_noalloc_host + LY::desc, &d, sizeof d);
+    FitState* st = (FitState*)(g_noalloc_host + LY::state);
+    st->run = RS_RUNNING;
+    st->phase = PH_INIT;
+    for (int i = 0; i < n; ++i) { st->x[i] = p[i]; st->xt[i] = p[i]; st->scale_inv[i] = 1.0; }
+    WorkItem* items = (WorkItem*)(g_noalloc_host + LY::items);
+    for (int t = 0; t < (int)ntiles; ++t) items[t] = WorkItem{0, t};
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    CUDA_TRY(cudaMemcpyAsync(base, g_noalloc_host, LY::res_hdr, cudaMemcpyHostToDevice, s));
+    void* args[] = {&Ed};
+    CUDA_TRY(cudaLaunchKernel(kernel_init_fits(prec), dim3(1), dim3(32), args, 0, s));
+    CUDA_TRY(cudaLaunchKernel(kernel_eval_round(prec), dim3(sms * bps), dim3(EVAL_THREADS), args, 0, s));
+    CUDA_TRY(cudaMemcpyAsync(g_noalloc_result, base + LY::res_hdr, sizeof g_noalloc_result,
+                             cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const FitResult* r = (const FitResult*)(g_noalloc_result + (LY::res - LY::res_hdr));
+    if (r->fit_status == -2) return fail(GBFIT_E_INVALID_ARG, "sigma <= 0 or non-finite x/y/sigma in the data");
+    const int K = n_tri(n) + n + 1;
+    for (int k = 0; k < K; ++k) out[k] = r->tot[k];
+    out[K - 1] = 0.5 * r->tot[K - 1];
+    return GBFIT_OK;
+}

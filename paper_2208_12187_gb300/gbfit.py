@@ -30,7 +30,7 @@ N_PARAMS = {0: 4, 1: 5, 2: 7, 3: 3}
 
 EXPORTS = ["gbfit_version", "gbfit_last_error", "gbfit_default_options", "gbfit_model_info",
            "gbfit_curve_fit", "gbfit_curve_fit_batch", "gbfit_evaluate", "gbfit_tr_subproblem",
-           "gbfit_stats_reset", "gbfit_stats_get", "gbfit_set_profiling"]
+           "gbfit_stats_reset", "gbfit_stats_get", "gbfit_set_profiling", "gbfit_evaluate_noalloc"]
 
 
 class GbfitError(RuntimeError):
@@ -83,6 +83,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
                                           ctypes.POINTER(Options), DP, DP, DP, IP, IP, P]
     lib.gbfit_evaluate.argtypes = [I, P, I64, I, ctypes.POINTER(ctypes.c_int64), P, P, I, DP, I, I, DP, P]
     lib.gbfit_tr_subproblem.argtypes = [I, DP, DP, D, D, DP, DP, DP, P]
+    lib.gbfit_evaluate_noalloc.argtypes = [I, P, I64, I, ctypes.POINTER(ctypes.c_int64), P, P, I, DP, I, I, DP, P]
     lib.gbfit_stats_get.argtypes = [ctypes.POINTER(Stats)]
     lib.gbfit_set_profiling.argtypes = [I]
     for name in EXPORTS:
@@ -295,3 +296,27 @@ def stats() -> dict:
 def set_profiling(on: bool):
     """Per-launch CUDA-event timing of evaluation passes (host-launched iterations)."""
     _check(load().gbfit_set_profiling(1 if on else 0))
+
+
+def evaluate_noalloc(model: int, xdata, ydata, p, sigma=None, grid_wh=None, precision="fp64", tile_points=0,
+                     stream=None):
+    """Same as evaluate(), through gbfit_evaluate_noalloc: no device or pinned
+    allocation at call time (data must already be on the device)."""
+    lib = load()
+    n = N_PARAMS[model]
+    yp, dt, ykeep = _array_info(ydata)
+    xp, _, xkeep = _array_info(xdata)
+    sp, _, skeep = _array_info(sigma)
+    m = int(ykeep.shape[0])
+    if grid_wh is not None:
+        layout, gw, xp = X_GRID, (ctypes.c_int64 * 2)(int(grid_wh[0]), int(grid_wh[1])), None
+    else:
+        layout, gw = (X_SOA2 if len(xkeep.shape) == 2 else X_VEC), None
+    pa = np.ascontiguousarray(np.asarray(p, dtype=np.float64))
+    nt = n * (n + 1) // 2
+    out = np.zeros(nt + n + 1)
+    prec = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision] if isinstance(precision, str) else int(precision)
+    rc = lib.gbfit_evaluate_noalloc(model, xp, m, layout, gw, yp, sp, dt, _dptr(pa), prec, int(tile_points),
+                                    _dptr(out), _stream_ptr(stream))
+    _check(rc)
+    return out[:nt], out[nt:nt + n], float(out[nt + n])
