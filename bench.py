@@ -21,6 +21,13 @@ A step is one whole fit (gbfit_curve_fit) from p0 to termination.
   cpu_baseline = the FP64 oracle (test infrastructure) on the same workload,
                on rank 0 only.
 --impl reference times that oracle as the reference arm.
+
+Extra modes (not the headline line):
+  --sweep     the 1D Gaussian size sweep, m = 1e3 ... 5e7, FP32 mixed and plain
+              FP64 paths: one JSON line per (m, precision) with point-iters/s
+  --batch     4,096 independent double-exponential fits of ragged m in one
+              batched launch: fits/s and nfev distribution
+  --no-extras only the timed fits of the headline workload (for ncu runs)
 """
 from __future__ import annotations
 
@@ -248,6 +255,11 @@ def run_ours(args, rank, local, world):
     pts_sum, = allreduce([pts], "sum", world)
     value = pts_sum / (ms_max / 1e3)
 
+    if args.no_extras:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms_max / args.steps,
+                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "note": "no extras"}))
+        return None
     # ---- roofline: per-launch CUDA-event timing of the evaluation pass
     gbfit.set_profiling(True)
     gbfit.stats_reset()
@@ -306,6 +318,89 @@ def run_ours(args, rank, local, world):
     return res
 
 
+def run_sweep(args):
+    """1D Gaussian + offset size sweep (config-0 generator), mixed and plain FP64."""
+    import torch
+    from paper_2208_12187_gb300 import build, gbfit, synth
+    build.build()
+    gbfit.load()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    sizes = [int(v) for v in args.sizes.split(",")]
+    if args.host_launch:
+        gbfit.set_profiling(True)   # iterations as plain kernel launches (for profilers)
+    for m in sizes:
+        pr = synth.gauss1d(m, seed=0)
+        for prec, dt in (("mixed", torch.float32), ("fp64", torch.float64)):
+            if prec not in args.precisions.split(","):
+                continue
+            x = torch.as_tensor(pr.x).to(dt).cuda()
+            y = torch.as_tensor(pr.y).to(dt).cuda()
+            fit = lambda: gbfit.curve_fit(pr.model, x, y, pr.p0, precision=prec, **TOL)
+            for _ in range(3):
+                fit()
+            gbfit.stats_reset()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ms, pts, nf = 0.0, 0.0, 0
+            steps = max(1, min(args.steps, int(2e8 // m) + 1))
+            for _ in range(steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0.record()
+                out = fit()
+                e1.record()
+                e1.synchronize()
+                ms += e0.elapsed_time(e1)
+                pts += m * out["nfev"]
+                nf = out["nfev"]
+            st = gbfit.stats()
+            it = max(st["passes"], 1)
+            cyc = st["phase_cycles"]
+            tile_share = cyc["tile"] / max(sum(v for k, v in cyc.items() if not k.startswith(("n_", "spare", "j32", "refine", "eig_", "comb_", "gn"))), 1)
+            print(json.dumps({"mode": "sweep", "model": "gauss1d", "m": m, "precision": prec, "nfev": nf,
+                              "fit_ms": ms / steps, "point_iters_per_s": pts / (ms / 1e3),
+                              "bytes_per_point": 8 if prec == "mixed" else 16,
+                              "hbm_gbs_equiv": pts * (8 if prec == "mixed" else 16) / (ms / 1e3) / 1e9,
+                              "own_tile_cycles_per_iter": cyc["tile"] / it,
+                              "step_cycles_per_iter": (cyc["logic"] + cyc["eigen"] + cyc["gn_path"] + cyc["step"] + cyc["prep"] + cyc["finish"]) / it,
+                              "combine_cycles_per_iter": cyc["combine"] / it}))
+            del x, y
+
+
+def run_batch(args):
+    """4,096 ragged double-exponential fits in one batched launch (mixed)."""
+    import torch
+    from paper_2208_12187_gb300 import build, gbfit, synth
+    build.build()
+    gbfit.load()
+    t0 = time.perf_counter()
+    bt = synth.dexp_batch(args.nfits, seed=7, dtype=np.float32)
+    gen_s = time.perf_counter() - t0
+    x = torch.as_tensor(bt.x).cuda()
+    y = torch.as_tensor(bt.y).cuda()
+    fit = lambda prec: gbfit.curve_fit_batch(bt.model, bt.offsets, x, y, bt.p0, lb=bt.lb, ub=bt.ub,
+                                             precision=prec, **TOL)
+    res = {}
+    for prec in ("mixed",):
+        fit(prec)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            e0.record()
+            out = fit(prec)
+            e1.record()
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        ms /= args.steps
+        nfev = out["nfev"]
+        res[prec] = {"fits_per_s": bt.nfits / (ms / 1e3), "ms_per_batch": ms,
+                     "point_iters_per_s": float(np.sum((bt.offsets[1:] - bt.offsets[:-1]) * nfev)) / (ms / 1e3),
+                     "nfev_p50": float(np.median(nfev)), "nfev_max": int(nfev.max()),
+                     "status_counts": {int(k): int(v) for k, v in zip(*np.unique(out["status"], return_counts=True))}}
+    print(json.dumps({"mode": "batch", "model": "dexp", "nfits": bt.nfits, "total_points": int(bt.offsets[-1]),
+                      "generate_s": gen_s, **res}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -316,7 +411,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per evaluation launch from an ncu capture of the current kernel")
+    ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--sizes", default="1000,10000,100000,1000000,10000000,50000000")
+    ap.add_argument("--batch", action="store_true")
+    ap.add_argument("--nfits", type=int, default=4096)
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--precisions", default="mixed,fp64")
+    ap.add_argument("--host-launch", action="store_true",
+                    help="sweep: launch iterations from the host instead of the graph (profiling)")
     args = ap.parse_args()
+    if args.sweep:
+        return run_sweep(args)
+    if args.batch:
+        return run_batch(args)
     rank, local, world = dist_setup(args)
     if args.impl == "reference":
         res = run_reference(args, rank, world)

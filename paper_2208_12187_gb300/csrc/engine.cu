@@ -208,6 +208,7 @@ int build_graph(Ctx* c) {
         kp.func = kernel_eval_round(P);
         kp.gridDim = dim3(c->grid_p[P]);
         kp.blockDim = dim3(EVAL_THREADS);
+        kp.sharedMemBytes = (unsigned)eval_dyn_smem(P);
         kp.kernelParams = args;
         cudaGraphNode_t nn;
         CUDA_TRY(cudaGraphAddKernelNode(&nn, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
@@ -342,7 +343,8 @@ int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::
         int cap = (max_nfev + 2) + 4;
         for (int r = 0; r < cap; ++r) {
             CUDA_TRY(cudaEventRecord(e0, s));
-            CUDA_TRY(cudaLaunchKernel(kernel_eval_round(prec), dim3(c->grid_p[prec]), dim3(EVAL_THREADS), a_eng, 0, s));
+            CUDA_TRY(cudaLaunchKernel(kernel_eval_round(prec), dim3(c->grid_p[prec]), dim3(EVAL_THREADS), a_eng,
+                                      eval_dyn_smem(prec), s));
             CUDA_TRY(cudaEventRecord(e1, s));
             CUDA_TRY(cudaMemcpyAsync(run_h, &Ed->sc[1], sizeof(int), cudaMemcpyDeviceToHost, s));
             CUDA_TRY(cudaStreamSynchronize(s));
@@ -809,7 +811,8 @@ extern "C" int gbfit_evaluate_noalloc(int model_id, const void* xdata, int64_t m
     CUDA_TRY(cudaMemcpyAsync(base, g_noalloc_host, LY::res_hdr, cudaMemcpyHostToDevice, s));
     void* args[] = {&Ed};
     CUDA_TRY(cudaLaunchKernel(kernel_init_fits(prec), dim3(1), dim3(32), args, 0, s));
-    CUDA_TRY(cudaLaunchKernel(kernel_eval_round(prec), dim3(sms * bps), dim3(EVAL_THREADS), args, 0, s));
+    CUDA_TRY(cudaLaunchKernel(kernel_eval_round(prec), dim3(sms * bps), dim3(EVAL_THREADS), args,
+                              eval_dyn_smem(prec), s));
     CUDA_TRY(cudaMemcpyAsync(g_noalloc_result, base + LY::res_hdr, sizeof g_noalloc_result,
                              cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));

@@ -97,29 +97,71 @@ struct PointCoord {
     }
 };
 
-template <class M, int PREC, typename DT, int LAYOUT, int WK>
-__device__ __forceinline__ void tile_points(const FitDesc& d, const float* pf, const double* pd,
-                                            int64_t i0, int64_t i1, bool check,
-                                            typename std::conditional<PREC == PREC_MIXED, float, double>::type
-                                                (&acc)[n_acc(M::N, PREC)],
-                                            int& bad) {
-    using AT = typename std::conditional<PREC == PREC_MIXED, float, double>::type;
+template <int PREC> struct AccT { using T = double; };
+template <> struct AccT<PREC_MIXED> { using T = float; };
+
+// One point: model value, residual and Jacobian row in registers, added to
+// the Gram / gradient / cost accumulators (slot layout in gbfit_internal.cuh).
+template <class M, int PREC, int WK>
+__device__ __forceinline__ void accum_point(const float* pfl, const double* pdl, typename AccT<PREC>::T X,
+                                            typename AccT<PREC>::T Y, typename AccT<PREC>::T yv,
+                                            typename AccT<PREC>::T sv, bool check,
+                                            typename AccT<PREC>::T (&acc)[n_acc(M::N, PREC)], int& bad) {
+    using AT = typename AccT<PREC>::T;
     constexpr int N = M::N;
     constexpr int NT = n_tri(N);
-    constexpr int K = n_acc(N, PREC);
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = AT(0);
-    float pfl[PF];
-    double pdl[PD];
-    if (PREC == PREC_MIXED) {
-#pragma unroll
-        for (int k = 0; k < PF; ++k) pfl[k] = pf[k];
-    } else {
-#pragma unroll
-        for (int k = 0; k < PD; ++k) pdl[k] = pd[k];
+    AT w = AT(1);
+    if (WK == W_ARRAY) w = sv;
+    if (WK == W_SIGMA) {
+        if (check && !(sv > AT(0) && isfinite(sv))) bad = 1;
+        if (PREC == PREC_MIXED) w = __fdividef(1.0f, float(sv)); else w = AT(1) / sv;
     }
-    // software-pipelined loads: the next point's data is requested before
-    // the current point is computed
+    if (check) {
+        if (!isfinite(X) || !isfinite(Y) || !isfinite(yv)) bad = 1;
+        if (WK == W_ARRAY && !(w > AT(0) && isfinite(w))) bad = 1;
+    }
+    AT Jw[N];
+    if constexpr (PREC == PREC_MIXED) {
+        float hb, dh, J[N];
+        M::eval_mixed(pfl, X, Y, hb, dh, J);
+        float r = w * (hb - yv);
+        float dr = w * dh;
+        float rn = r + dr;
+#pragma unroll
+        for (int a = 0; a < N; ++a) Jw[a] = w * J[a];
+        int idx = 0;
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int b = a; b < N; ++b) { acc[idx] = fmaf(Jw[a], Jw[b], acc[idx]); ++idx; }
+#pragma unroll
+        for (int a = 0; a < N; ++a) acc[NT + a] = fmaf(Jw[a], rn, acc[NT + a]);
+        acc[NT + N] = fmaf(rn, rn, acc[NT + N]);
+        acc[NT + N + 1] = fmaf(dr, fmaf(2.0f, r, dr), acc[NT + N + 1]);
+        acc[NT + N + 2] = fmaf(r, r, acc[NT + N + 2]);
+    } else {
+        double h, J[N];
+        M::eval_plain(pdl, X, Y, h, J);
+        double r = w * (h - yv);
+#pragma unroll
+        for (int a = 0; a < N; ++a) Jw[a] = w * J[a];
+        int idx = 0;
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int b = a; b < N; ++b) { acc[idx] = fma(Jw[a], Jw[b], acc[idx]); ++idx; }
+#pragma unroll
+        for (int a = 0; a < N; ++a) acc[NT + a] = fma(Jw[a], r, acc[NT + a]);
+        acc[NT + N] = fma(r, r, acc[NT + N]);
+    }
+}
+
+// Points [i0, i1) with register loads (software-pipelined one point ahead).
+template <class M, int PREC, typename DT, int LAYOUT, int WK>
+__device__ __forceinline__ void tile_points(const FitDesc& d, const float* pfl, const double* pdl,
+                                            int64_t i0, int64_t i1, bool check,
+                                            typename AccT<PREC>::T (&acc)[n_acc(M::N, PREC)], int& bad) {
+    using AT = typename AccT<PREC>::T;
     PointCoord pc;
     int64_t i = i0 + threadIdx.x;
     if (LAYOUT == X_GRID) pc.init(i, d.grid_w);
@@ -140,55 +182,130 @@ __device__ __forceinline__ void tile_points(const FitDesc& d, const float* pf, c
     for (; i < i1; i += EVAL_THREADS) {
         AT X = nX, Y = nY, yv = ny, sv = ns;
         if (i + EVAL_THREADS < i1) load(i + EVAL_THREADS, nX, nY, ny, ns);
-        AT w = AT(1);
-        if (WK == W_ARRAY) w = sv;
-        if (WK == W_SIGMA) {
-            if (check && !(sv > AT(0) && isfinite(sv))) bad = 1;
-            if (PREC == PREC_MIXED) w = __fdividef(1.0f, float(sv)); else w = AT(1) / sv;
-        }
-        if (check) {
-            if (!isfinite(X) || !isfinite(Y) || !isfinite(yv)) bad = 1;
-            if (WK == W_ARRAY && !(w > AT(0) && isfinite(w))) bad = 1;
-        }
-        AT Jw[N];
-        if constexpr (PREC == PREC_MIXED) {
-            float hb, dh, J[N];
-            M::eval_mixed(pfl, X, Y, hb, dh, J);
-            float r = w * (hb - yv);
-            float dr = w * dh;
-            float rn = r + dr;
-#pragma unroll
-            for (int a = 0; a < N; ++a) Jw[a] = w * J[a];
-            int idx = 0;
-#pragma unroll
-            for (int a = 0; a < N; ++a)
-#pragma unroll
-                for (int b = a; b < N; ++b) { acc[idx] = fmaf(Jw[a], Jw[b], acc[idx]); ++idx; }
-#pragma unroll
-            for (int a = 0; a < N; ++a) acc[NT + a] = fmaf(Jw[a], rn, acc[NT + a]);
-            acc[NT + N] = fmaf(rn, rn, acc[NT + N]);
-            acc[NT + N + 1] = fmaf(dr, fmaf(2.0f, r, dr), acc[NT + N + 1]);
-            acc[NT + N + 2] = fmaf(r, r, acc[NT + N + 2]);
-        } else {
-            double h, J[N];
-            M::eval_plain(pdl, X, Y, h, J);
-            double r = w * (h - yv);
-#pragma unroll
-            for (int a = 0; a < N; ++a) Jw[a] = w * J[a];
-            int idx = 0;
-#pragma unroll
-            for (int a = 0; a < N; ++a)
-#pragma unroll
-                for (int b = a; b < N; ++b) { acc[idx] = fma(Jw[a], Jw[b], acc[idx]); ++idx; }
-#pragma unroll
-            for (int a = 0; a < N; ++a) acc[NT + a] = fma(Jw[a], r, acc[NT + a]);
-            acc[NT + N] = fma(r, r, acc[NT + N]);
-        }
+        accum_point<M, PREC, WK>(pfl, pdl, X, Y, yv, sv, check, acc, bad);
     }
+}
+
+// ---- bulk-copy ring (mixed precision, FP32 data): each CTA streams its
+// tile through NST shared-memory stages of CHUNK points per array with
+// cp.async.bulk, completion tracked by one mbarrier per stage, so that
+// about NST-1 chunks (tens of KB per SM) are in flight while the threads
+// compute from shared memory.
+constexpr int CHUNK = 1024;
+constexpr int NST = 4;
+constexpr int RING_ARRAYS = 4;                       // x, x2, y, sigma at most
+constexpr size_t RING_BYTES = size_t(NST) * RING_ARRAYS * CHUNK * sizeof(float);
+constexpr long long MBAR_SPIN_LIMIT = 1ll << 22;     // bounded waits (error flag past the limit)
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (long long it = 0; it < MBAR_SPIN_LIMIT; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+struct RingState {
+    unsigned long long* bar;     // [NST] mbarriers
+    float* buf;                  // [NST][RING_ARRAYS][CHUNK]
+    unsigned seq;                // chunks consumed by this CTA so far (same in all threads)
+    int* fail;                   // shared flag: a bounded wait gave up
+};
+
+template <class M, int LAYOUT, int WK>
+__device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0, int64_t i1, bool check,
+                                 float (&acc)[n_acc(M::N, PREC_MIXED)], int& bad, RingState& R) {
+    const int t = threadIdx.x;
+    // arrays streamed: slot 0 x (or X row), 1 Y row, 2 y, 3 sigma
+    const float* src[RING_ARRAYS] = {LAYOUT == X_GRID ? nullptr : (const float*)d.x,
+                                     LAYOUT == X_SOA2 ? (const float*)d.x2 : nullptr, (const float*)d.y,
+                                     WK == W_SIGMA ? (const float*)d.w : nullptr};
+    // head up to 16-byte alignment of y; every streamed array must share it
+    int64_t h = (int64_t)(((16 - (reinterpret_cast<uintptr_t>(src[2] + i0) & 15)) & 15) / 4);
+    bool aligned = true;
+    for (int a = 0; a < RING_ARRAYS; ++a)
+        if (src[a] && (reinterpret_cast<uintptr_t>(src[a] + i0 + h) & 15)) aligned = false;
+    int64_t a0 = i0 + h;
+    if (!aligned || a0 >= i1) { tile_points<M, PREC_MIXED, float, LAYOUT, WK>(d, pfl, nullptr, i0, i1, check, acc, bad); return; }
+    const int nch = (int)((i1 - a0) / CHUNK);
+    const int64_t a1 = a0 + (int64_t)nch * CHUNK;
+    unsigned bytes = 0;
+    for (int a = 0; a < RING_ARRAYS; ++a) bytes += src[a] ? CHUNK * sizeof(float) : 0;
+    auto issue = [&](int c) {
+        unsigned g = R.seq + c;
+        int s = g % NST;
+        unsigned long long* bar = R.bar + s;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, bytes);
+        for (int a = 0; a < RING_ARRAYS; ++a)
+            if (src[a]) bulk_load(R.buf + (s * RING_ARRAYS + a) * CHUNK, src[a] + a0 + (int64_t)c * CHUNK,
+                                  CHUNK * sizeof(float), bar);
+    };
+    if (t == 0)
+        for (int c = 0; c < nch && c < NST; ++c) issue(c);
+    // head points with plain loads while the first chunks stream in
+    tile_points<M, PREC_MIXED, float, LAYOUT, WK>(d, pfl, nullptr, i0, a0, check, acc, bad);
+    PointCoord pc;
+    if (LAYOUT == X_GRID) pc.init(a0 + t, d.grid_w);
+    for (int c = 0; c < nch; ++c) {
+        unsigned g = R.seq + c;
+        int s = g % NST;
+        if (!mbar_wait(R.bar + s, (g / NST) & 1)) *R.fail = 1;
+        __syncthreads();
+        if (*R.fail) break;
+        const float* B = R.buf + s * RING_ARRAYS * CHUNK;
+#pragma unroll 2
+        for (int k = t; k < CHUNK; k += EVAL_THREADS) {
+            float X = 0.0f, Y = 0.0f;
+            if (LAYOUT == X_GRID) {
+                X = float(pc.X);
+                Y = float(pc.Y);
+                pc.advance(EVAL_THREADS);
+            } else {
+                X = B[0 * CHUNK + k];
+                if (LAYOUT == X_SOA2) Y = B[1 * CHUNK + k];
+            }
+            float yv = B[2 * CHUNK + k];
+            float sv = (WK == W_SIGMA) ? B[3 * CHUNK + k] : 1.0f;
+            accum_point<M, PREC_MIXED, WK>(pfl, nullptr, X, Y, yv, sv, check, acc, bad);
+        }
+        __syncthreads();                                   // stage free for reuse
+        if (t == 0 && c + NST < nch) issue(c + NST);
+    }
+    if (*R.fail) {
+        // give copies still in flight a bounded chance to land before leaving
+        for (int c = 0; c < nch; ++c) { unsigned g = R.seq + c; mbar_wait(R.bar + (g % NST), (g / NST) & 1); }
+    }
+    R.seq += nch;
+    // tail with plain loads
+    tile_points<M, PREC_MIXED, float, LAYOUT, WK>(d, pfl, nullptr, a1, i1, check, acc, bad);
 }
 
 // ------------------------------------------------------------------ shared memory of the round kernel
 struct RoundSmem {
+    unsigned long long mbar[NST];
+    int ring_fail;
     FitDesc desc;
     long long t_mark, t_fence, t_group;
     float pf[PF];
@@ -225,13 +342,30 @@ __device__ void combine_rows(const T* rows, int nrows, int K, double* scratch, d
 // ------------------------------------------------------------------ the round kernel
 template <class M, int PREC>
 __device__ void eval_tile_dispatch(const RoundSmem& sm, int64_t i0, int64_t i1, bool check, int& bad,
-                                   typename std::conditional<PREC == PREC_MIXED, float, double>::type
-                                       (&acc)[n_acc(M::N, PREC)]) {
+                                   typename AccT<PREC>::T (&acc)[n_acc(M::N, PREC)], RingState& R) {
+    using AT = typename AccT<PREC>::T;
     const FitDesc& d = sm.desc;
-    bool f64 = d.dtype == F64;
-#define GB_CASE(LAY, WKV)                                                                         \
-    if (f64) tile_points<M, PREC, double, LAY, WKV>(d, sm.pf, sm.pd, i0, i1, check, acc, bad);    \
-    else tile_points<M, PREC, float, LAY, WKV>(d, sm.pf, sm.pd, i0, i1, check, acc, bad);
+#pragma unroll
+    for (int k = 0; k < n_acc(M::N, PREC); ++k) acc[k] = AT(0);
+    float pfl[PF];
+    double pdl[PD];
+    if (PREC == PREC_MIXED) {
+#pragma unroll
+        for (int k = 0; k < PF; ++k) pfl[k] = sm.pf[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < PD; ++k) pdl[k] = sm.pd[k];
+    }
+    const bool f64 = d.dtype == F64;
+    // mixed precision on FP32 data streams through the bulk-copy ring
+#define GB_CASE(LAY, WKV)                                                                              \
+    if constexpr (PREC == PREC_MIXED && WKV != W_ARRAY) {                                              \
+        if (!f64) tile_points_ring<M, LAY, WKV>(d, pfl, i0, i1, check, acc, bad, R);                   \
+        else tile_points<M, PREC, double, LAY, WKV>(d, pfl, pdl, i0, i1, check, acc, bad);             \
+    } else {                                                                                           \
+        if (f64) tile_points<M, PREC, double, LAY, WKV>(d, pfl, pdl, i0, i1, check, acc, bad);         \
+        else tile_points<M, PREC, float, LAY, WKV>(d, pfl, pdl, i0, i1, check, acc, bad);              \
+    }
     int wk = d.wkind;
     if (M::N == 7) {
         if (d.layout == X_GRID) {
@@ -246,8 +380,8 @@ __device__ void eval_tile_dispatch(const RoundSmem& sm, int64_t i0, int64_t i1, 
 }
 
 template <class M, int PREC>
-__device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile) {
-    using AT = typename std::conditional<PREC == PREC_MIXED, float, double>::type;
+__device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, RingState& R) {
+    using AT = typename AccT<PREC>::T;
     constexpr int N = M::N;
     constexpr int K = n_acc(N, PREC);
     const FitDesc& d = sm.desc;
@@ -259,7 +393,8 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile) 
     long long t_tile = clock64();
     int bad = 0;
     AT acc[K];
-    eval_tile_dispatch<M, PREC>(sm, i0, i1, check, bad, acc);
+    eval_tile_dispatch<M, PREC>(sm, i0, i1, check, bad, acc, R);
+    if (sm.ring_fail && threadIdx.x == 0) atomicOr(&stp->bad_data, 2);   // a bounded wait gave up
     if (check) {
         int any = __syncthreads_or(bad);
         if (any && threadIdx.x == 0) atomicOr(&stp->bad_data, 1);
@@ -325,9 +460,25 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile) 
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(EVAL_THREADS) eval_round_kernel(const Engine* __restrict__ Ep) {
+__global__ void __launch_bounds__(EVAL_THREADS, 2) eval_round_kernel(const Engine* __restrict__ Ep) {
     __shared__ RoundSmem sm;
+    extern __shared__ __align__(128) float ring_buf[];
     const Engine E = *Ep;
+    RingState R;
+    R.bar = sm.mbar;
+    R.buf = ring_buf;
+    R.seq = 0;
+    R.fail = &sm.ring_fail;
+    if (PREC == PREC_MIXED) {
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < NST; ++s) mbar_init(&sm.mbar[s], 1);
+            sm.ring_fail = 0;
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    } else if (threadIdx.x == 0) {
+        sm.ring_fail = 0;
+    }
     int n_items = *E.n_items;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         WorkItem wi = E.items[it];
@@ -345,10 +496,10 @@ __global__ void __launch_bounds__(EVAL_THREADS) eval_round_kernel(const Engine* 
         }
         __syncthreads();
         switch (sm.desc.model) {
-            case 0: process_item<MGauss1D, PREC>(sm, E, wi.fit, wi.tile); break;
-            case 1: process_item<MDexp, PREC>(sm, E, wi.fit, wi.tile); break;
-            case 2: process_item<MGauss2D, PREC>(sm, E, wi.fit, wi.tile); break;
-            case 3: process_item<MPoly2, PREC>(sm, E, wi.fit, wi.tile); break;
+            case 0: process_item<MGauss1D, PREC>(sm, E, wi.fit, wi.tile, R); break;
+            case 1: process_item<MDexp, PREC>(sm, E, wi.fit, wi.tile, R); break;
+            case 2: process_item<MGauss2D, PREC>(sm, E, wi.fit, wi.tile, R); break;
+            case 3: process_item<MPoly2, PREC>(sm, E, wi.fit, wi.tile, R); break;
         }
         __syncthreads();
     }
@@ -445,9 +596,15 @@ void* kernel_init_fits(int prec) {
     return prec == PREC_MIXED ? (void*)init_fits_kernel<PREC_MIXED> : (void*)init_fits_kernel<PREC_FP64>;
 }
 void* kernel_round_end() { return (void*)round_end_kernel; }
+size_t eval_dyn_smem(int prec) { return prec == PREC_MIXED ? RING_BYTES : 0; }
 int eval_blocks_per_sm(int prec) {
     int b = 0;
-    if (prec == PREC_MIXED) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, eval_round_kernel<PREC_MIXED>, EVAL_THREADS, 0);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(eval_round_kernel<PREC_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RING_BYTES);
+        attr_set = true;
+    }
+    if (prec == PREC_MIXED) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, eval_round_kernel<PREC_MIXED>, EVAL_THREADS, RING_BYTES);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, eval_round_kernel<PREC_FP64>, EVAL_THREADS, 0);
     return b;
 }

@@ -10,6 +10,7 @@ void* kernel_eval_round(int prec);
 void* kernel_init_fits(int prec);
 void* kernel_round_end();
 int eval_blocks_per_sm(int prec);
+size_t eval_dyn_smem(int prec);
 cudaError_t launch_stage_weights(bool f64, const void* sigma, double* w, int64_t m, int blocks, cudaStream_t s);
 cudaError_t launch_tr_subproblem(int n, const double* B, const double* g, double Delta, double alpha0,
                                  double* p_out, double* alpha_out, double* lam_out, cudaStream_t s);
