@@ -407,6 +407,126 @@ def run_batch(args):
                       "generate_s": gen_s, **res}))
 
 
+def _serve_submit(srv, pr, k):
+    x = None if pr.layout == 2 else pr.x
+    return srv.submit(pr.model, x, pr.y, pr.p0, sigma=pr.sigma, lb=pr.lb, ub=pr.ub, grid_wh=pr.grid_wh, tag=k, **TOL)
+
+
+def serve_open_loop(st, idx, t_arr, args, precision="mixed", trace=None):
+    """Run the requests `idx` through one server, request j submitted once the
+    wall clock passes t_arr[j].  Latency = arrival -> result retired on the
+    host (includes queueing, the H2D copy of the request's data and every
+    iteration).  Returns (fits/s over the whole stream, latencies, results)."""
+    from paper_2208_12187_gb300 import gbfit
+    srv = gbfit.Server(hbm_budget_bytes=int(args.serve_budget_gb * (1 << 30)), max_slots=args.serve_slots,
+                       precision=precision, rounds_per_step=args.serve_rounds)
+    n = len(idx)
+    lat = np.zeros(n)
+    late = np.zeros(n)
+    res = [None] * n
+    k = 0
+    n_done = 0
+    busy = 0
+    T0 = time.perf_counter()
+    while n_done < n:
+        now = time.perf_counter() - T0
+        while k < n and t_arr[k] <= now:
+            _serve_submit(srv, st.request(int(idx[k])), k)
+            late[k] = time.perf_counter() - T0 - t_arr[k]
+            k += 1
+        if busy or k > n_done:
+            ts = time.perf_counter()
+            a, q = srv.step()
+            busy = a + q
+            if trace is not None:
+                trace.append((ts - T0, time.perf_counter() - ts, a, q))
+        elif k < n:
+            time.sleep(max(0.0, min(1e-3, t_arr[k] - (time.perf_counter() - T0))))
+        for r in srv.poll():
+            j = int(r["tag"])
+            res[j] = r
+            lat[j] = late[j] + (r["t_done"] - r["t_submit"])
+            n_done += 1
+    T = time.perf_counter() - T0
+    srv.close()
+    return n / T, lat, res
+
+
+def run_serve(args):
+    """Serving: open-loop Poisson stream of mixed-model, mixed-size requests
+    (40% gauss1d, 40% dexp, 20% gauss2d; m log-uniform in [1e3, 4e6]),
+    continuous batching under an HBM budget, against the plain
+    one-fit-at-a-time FP64 path on a sample of the same stream."""
+    import dataclasses
+    import torch
+    from paper_2208_12187_gb300 import build, gbfit, synth
+    build.build()
+    gbfit.load()
+    t0 = time.perf_counter()
+    st = synth.ServeStream(args.serve_requests, seed=11, n_data=2, dtype=np.float32)
+    pin = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    for key, pr in list(st.data.items()):
+        st.data[key] = dataclasses.replace(pr, x=pin(pr.x), y=pin(pr.y), sigma=pin(pr.sigma))
+    gen_s = time.perf_counter() - t0
+    N = len(st)
+    idx = np.arange(N)
+    base = {"mode": "serve", "requests": N, "mix": "40% gauss1d / 40% dexp / 20% gauss2d",
+            "m": "log-uniform [1e3, 4e6] (2D: nearest W x W rung)", "mean_m": float(st.m.mean()),
+            "budget_gb": args.serve_budget_gb, "slots": args.serve_slots, "rounds_per_step": args.serve_rounds,
+            "data": "synthetic fp32, pinned host buffers", "generate_s": gen_s}
+    pct = lambda lat: {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+    # warm-up (builds, first-touch of the pool)
+    serve_open_loop(st, idx[:64], np.zeros(64), args)
+    # saturation: every request present at t = 0
+    sat, lat, res = serve_open_loop(st, idx, np.zeros(N), args)
+    pts = float(sum(int(st.m[j]) * r["nfev"] for j, r in enumerate(res)))
+    bad = sum(r["status"] != 0 or r["fit_status"] < 1 for r in res)
+    print(json.dumps({**base, "arm": "served-mixed", "arrival": "all at t=0", "fits_per_s": sat,
+                      "point_iters_per_s": pts * sat / N, "not_converged": int(bad), **pct(lat)}), flush=True)
+    # plain FP64, one fit at a time, on a sample of the stream
+    S = min(args.serve_sample, N)
+    def plain(t_arr):
+        S = len(t_arr)
+        lat = np.zeros(S)
+        out = []
+        T0 = time.perf_counter()
+        for j in range(S):
+            now = time.perf_counter() - T0
+            if t_arr[j] > now:
+                time.sleep(t_arr[j] - now)
+            pr = st.request(j)
+            x = None if pr.layout == 2 else pr.x
+            out.append(gbfit.curve_fit(pr.model, x, pr.y, pr.p0, sigma=pr.sigma, lb=pr.lb, ub=pr.ub,
+                                       grid_wh=pr.grid_wh, precision="fp64", **TOL))
+            lat[j] = time.perf_counter() - T0 - t_arr[j]
+        return S / (time.perf_counter() - T0), lat, out
+    plain(np.zeros(min(S, 8)))
+    psat, plat, pout = plain(np.zeros(S))
+    err = []
+    for j in range(S):
+        a, b = res[j]["popt"], pout[j]["popt"]
+        err.append(float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1.0))))
+    err = np.array(err)
+    print(json.dumps({**base, "arm": "plain-fp64-one-at-a-time", "sample": S, "arrival": "all at t=0",
+                      "fits_per_s": psat, **pct(plat),
+                      "served_mixed_vs_plain_fp64_popt_rel": {"max": float(err.max()), "p99": float(np.percentile(err, 99)),
+                                                             "frac_le_1e-6": float(np.mean(err <= 1e-6))}}), flush=True)
+    # open loop: a sweep of arrival rates up to saturation of the served form,
+    # and the plain path at 80% of its own capacity (same rate for the served form)
+    for frac in [float(f) for f in args.serve_rates.split(",")]:
+        rate = frac * sat
+        t_arr = synth.ServeStream.arrivals(N, rate, seed=3)
+        thr, lat, _ = serve_open_loop(st, idx, t_arr, args)
+        print(json.dumps({**base, "arm": "served-mixed", "arrival": "poisson", "rate_per_s": rate,
+                          "rate_frac_of_saturation": frac, "fits_per_s": thr, **pct(lat)}), flush=True)
+    rate = 0.8 * psat
+    t_arr = synth.ServeStream.arrivals(S, rate, seed=4)
+    _, plat, _ = plain(t_arr)
+    _, slat, _ = serve_open_loop(st, idx[:S], t_arr, args)
+    print(json.dumps({**base, "arm": "both-at-plain-rate", "sample": S, "arrival": "poisson", "rate_per_s": rate,
+                      "plain_fp64": pct(plat), "served_mixed": pct(slat)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -423,6 +543,13 @@ def main():
     ap.add_argument("--nfits", type=int, default=4096)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--precisions", default="mixed,fp64")
+    ap.add_argument("--serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-sample", type=int, default=200)
+    ap.add_argument("--serve-budget-gb", type=float, default=16.0)
+    ap.add_argument("--serve-slots", type=int, default=4096)
+    ap.add_argument("--serve-rounds", type=int, default=4)
+    ap.add_argument("--serve-rates", default="0.25,0.5,0.8,0.95")
     ap.add_argument("--host-launch", action="store_true",
                     help="launch iterations from the host instead of the graph (for profilers)")
     args = ap.parse_args()
@@ -430,6 +557,8 @@ def main():
         return run_sweep(args)
     if args.batch:
         return run_batch(args)
+    if args.serve:
+        return run_serve(args)
     rank, local, world = dist_setup(args)
     if args.impl == "reference":
         res = run_reference(args, rank, world)

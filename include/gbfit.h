@@ -180,6 +180,66 @@ int gbfit_tr_subproblem(int n, const double* B, const double* g, double Delta, d
                         double* p, double* alpha, double* lam, void* cuda_stream);
 
 /*
+ * Serving: continuous batching of independent fit requests (many models and
+ * sizes) on one GPU.  The server owns a device pool of hbm_budget_bytes for
+ * request data and up to max_slots fit records that stay on the device while
+ * a fit runs.  Each gbfit_server_step: (1) retires fits that finished,
+ * releasing their memory and slot; (2) admits queued requests in arrival
+ * order while a slot is free and their data fits in the pool (copying it in);
+ * (3) runs `rounds_per_step` trust-region iterations for every admitted fit
+ * in shared launches (one evaluation kernel per iteration for all fits).
+ * A fit's reduction tiling depends only on its own m, so its result is the
+ * same, bit for bit, whatever else is being served.
+ */
+typedef struct gbfit_server gbfit_server;
+
+typedef struct gbfit_server_config {
+    size_t hbm_budget_bytes;   /* device pool for request data (x, y, sigma) and tile scratch */
+    int max_slots;             /* fits resident at once (default 4096)                         */
+    int precision;             /* GBFIT_PREC_*                                                 */
+    int rounds_per_step;       /* iterations per step (default 4)                              */
+    int reserved[4];
+} gbfit_server_config;
+
+typedef struct gbfit_request {
+    int model_id, x_layout, dtype, has_bounds;
+    int64_t m, grid_w, grid_h;           /* grid_w, grid_h for GBFIT_X_GRID                     */
+    const void* xdata;                   /* host or device; copied into the pool on admission   */
+    const void* ydata;
+    const void* sigma;                   /* may be NULL                                        */
+    double p0[GBFIT_MAX_PARAMS], lb[GBFIT_MAX_PARAMS], ub[GBFIT_MAX_PARAMS];
+    double ftol, xtol, gtol;
+    int max_nfev;
+    uint64_t tag;                        /* returned with the result                            */
+} gbfit_request;
+
+typedef struct gbfit_result_rec {
+    uint64_t ticket, tag;
+    int status;                          /* GBFIT_OK or a GBFIT_E_* code for this request       */
+    int fit_status, nfev, n_params;
+    double cost;
+    double popt[GBFIT_MAX_PARAMS];
+    double t_submit, t_admit, t_done;    /* seconds, host steady clock                          */
+} gbfit_result_rec;
+
+/* Create a server on the current device (allocates the pool once). */
+int gbfit_server_create(const gbfit_server_config* cfg, gbfit_server** out);
+
+/* Queue a request (its data pointers must stay valid until it is admitted).
+ * GBFIT_E_BUDGET if its data can never fit in the pool. */
+int gbfit_server_submit(gbfit_server* s, const gbfit_request* req, uint64_t* ticket);
+
+/* Retire, admit, and run one step of iterations; *n_active = fits resident
+ * after the step, *n_queued = requests still waiting.  Blocking. */
+int gbfit_server_step(gbfit_server* s, int* n_active, int* n_queued);
+
+/* Copy up to max finished results (oldest first) into out; *count = copied. */
+int gbfit_server_poll(gbfit_server* s, gbfit_result_rec* out, int max, int* count);
+
+/* Free the server and its pool. */
+int gbfit_server_destroy(gbfit_server* s);
+
+/*
  * gbfit_evaluate without any device or pinned-host allocation (the paper has
  * no counterpart; it exists for callers that may not allocate at call time:
  * code inside host callbacks or allocation-free stream captures, under an

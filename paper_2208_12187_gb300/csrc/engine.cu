@@ -70,9 +70,9 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Byte layout of one call's job buffer: what the host uploads ([0, res_hdr))
 // and what it reads back ([res_hdr, end)) are each one contiguous copy.
-struct Layout {
+struct JobLayout {
     size_t eng, desc, state, items, gcnt, fcnt, res_hdr, res, end;
-    Layout(size_t nf, size_t ntiles, size_t ngroups) {
+    JobLayout(size_t nf, size_t ntiles, size_t ngroups) {
         size_t o = 0;
         eng = o;     o += align256(sizeof(Engine));
         desc = o;    o += align256(nf * sizeof(FitDesc));
@@ -103,7 +103,7 @@ struct Ctx {
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
 
     Engine* eng_dev() const { return (Engine*)job; }
-    Engine engine(const Layout& L) const {
+    Engine engine(const JobLayout& L) const {
         Engine E;
         memset(&E, 0, sizeof E);
         Engine* ed = eng_dev();
@@ -164,7 +164,7 @@ int get_ctx(Ctx** out) {
     return GBFIT_OK;
 }
 
-int ensure(Ctx* c, const Layout& L, size_t ntiles, size_t ngroups) {
+int ensure(Ctx* c, const JobLayout& L, size_t ntiles, size_t ngroups) {
     bool job_changed = false, scratch_changed = false;
     int rc;
     if ((rc = grow_dev(c->job, c->cap_job, L.end, job_changed))) return rc;
@@ -301,7 +301,7 @@ int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::
         ngroups += d.n_groups;
         if (d.max_nfev > max_nfev) max_nfev = d.max_nfev;
     }
-    Layout L(nf, ntiles, ngroups);
+    JobLayout L(nf, ntiles, ngroups);
     int rc;
     if ((rc = ensure(c, L, ntiles, ngroups))) return rc;
     if (prec == PREC_MIXED) { if ((rc = build_graph<PREC_MIXED>(c))) return rc; }
@@ -823,3 +823,381 @@ extern "C" int gbfit_evaluate_noalloc(int model_id, const void* xdata, int64_t m
     out[K - 1] = 0.5 * r->tot[K - 1];
     return GBFIT_OK;
 }
+
+// ====================================================================== serving (continuous batching)
+#include <chrono>
+#include <deque>
+#include <map>
+
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over [0, capacity) in arbitrary units, with coalescing.
+struct RangeAlloc {
+    std::map<size_t, size_t> free_;   // offset -> size
+    size_t cap = 0, used = 0;
+    void reset(size_t c) { free_.clear(); free_[0] = c; cap = c; used = 0; }
+    bool alloc(size_t n, size_t align, size_t* off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            size_t o = (it->first + align - 1) / align * align;
+            size_t end = it->first + it->second;
+            if (o + n <= end) {
+                size_t fo = it->first, fs = it->second;
+                free_.erase(it);
+                if (o > fo) free_[fo] = o - fo;
+                if (o + n < fo + fs) free_[o + n] = fo + fs - (o + n);
+                *off = o;
+                used += n;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t n) {
+        used -= n;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) { it->second += nx->second; free_.erase(nx); }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) { pv->second += it->second; free_.erase(it); }
+        }
+    }
+};
+
+struct SrvPending { gbfit_request req; uint64_t ticket; double t_submit; };
+
+struct SrvSlot {
+    bool used = false;
+    uint64_t ticket = 0, tag = 0;
+    size_t data_off = 0, data_bytes = 0, tile0 = 0, ntiles = 0, group0 = 0, ngroups = 0;
+    double t_submit = 0, t_admit = 0;
+    int n = 0;
+};
+
+// Each array of a request starts on a 256-byte boundary of its pool region
+// (so that the bulk-copy ring can stream every array).
+size_t arr_bytes(const gbfit_request& r) { return ((size_t)r.m * (r.dtype == GBFIT_F64 ? 8 : 4) + 255) / 256 * 256; }
+size_t req_data_bytes(const gbfit_request& r) {
+    size_t xs = r.x_layout == GBFIT_X_GRID ? 0 : (r.x_layout == GBFIT_X_SOA2 ? 2 : 1);
+    return arr_bytes(r) * (xs + 1 + (r.sigma ? 1 : 0));
+}
+
+}  // namespace
+
+struct gbfit_server {
+    int device = 0, prec = PREC_MIXED, max_slots = 0, rounds = 4, grid = 0;
+    size_t budget = 0;
+    char* pool = nullptr;
+    RangeAlloc pool_alloc, tile_alloc, group_alloc;
+    size_t max_tiles = 0, max_groups = 0;
+    float* tile_part = nullptr;
+    double* tile_part_d = nullptr;
+    double* group_part = nullptr;
+    char* job = nullptr;
+    JobLayout* L = nullptr;
+    char* hbuf = nullptr;              // pinned staging (job image, results, flags)
+    size_t hcap = 0;
+    int* d_list = nullptr;             // device list of newly admitted slots
+    cudaStream_t stream = nullptr;
+    std::deque<SrvPending> queue;
+    std::vector<SrvSlot> slots;
+    std::deque<gbfit_result_rec> done;
+    uint64_t next_ticket = 1;
+    std::mutex mu;
+};
+
+extern "C" {
+
+int gbfit_server_create(const gbfit_server_config* cfg_in, gbfit_server** out) {
+    if (!out) return fail(GBFIT_E_INVALID_ARG, "out is NULL");
+    gbfit_server_config cfg;
+    memset(&cfg, 0, sizeof cfg);
+    if (cfg_in) cfg = *cfg_in;
+    if (cfg.hbm_budget_bytes == 0) cfg.hbm_budget_bytes = (size_t)1 << 30;
+    if (cfg.max_slots <= 0) cfg.max_slots = 4096;
+    if (cfg.rounds_per_step <= 0) cfg.rounds_per_step = 4;
+    if (cfg.precision != GBFIT_PREC_FP64 && cfg.precision != GBFIT_PREC_MIXED)
+        return fail(GBFIT_E_INVALID_ARG, "unknown precision %d", cfg.precision);
+    gbfit_server* s = new gbfit_server();
+    s->prec = cfg.precision;
+    s->max_slots = cfg.max_slots;
+    s->rounds = cfg.rounds_per_step;
+    s->budget = cfg.hbm_budget_bytes;
+    auto bail = [&](int rc) { gbfit_server_destroy(s); return rc; };
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess) return bail(fail(GBFIT_E_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)));
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    int bps = eval_blocks_per_sm(s->prec);
+    s->grid = sms * (bps < 1 ? 1 : bps);
+    // tile scratch: enough for the budget filled with the smallest tiles
+    s->max_tiles = s->budget / (size_t(TILE_MIN) * 8) + (size_t)s->max_slots;
+    s->max_groups = s->max_tiles / GROUP_TILES + (size_t)s->max_slots;
+    s->L = new JobLayout((size_t)s->max_slots, s->max_tiles, s->max_groups);
+    bool ch = false;
+    size_t cap = 0;
+    if (grow_dev(s->pool, cap, s->budget, ch)) return bail(GBFIT_E_OOM);
+    cap = 0;
+    if (grow_dev(s->job, cap, s->L->end, ch)) return bail(GBFIT_E_OOM);
+    cap = 0;
+    if (s->prec == PREC_MIXED) { if (grow_dev(s->tile_part, cap, s->max_tiles * KMAX, ch)) return bail(GBFIT_E_OOM); }
+    else { if (grow_dev(s->tile_part_d, cap, s->max_tiles * KMAX, ch)) return bail(GBFIT_E_OOM); }
+    cap = 0;
+    if (grow_dev(s->group_part, cap, s->max_groups * KMAX, ch)) return bail(GBFIT_E_OOM);
+    cap = 0;
+    if (grow_dev(s->d_list, cap, (size_t)s->max_slots, ch)) return bail(GBFIT_E_OOM);
+    s->hcap = s->L->end + (size_t)s->max_slots * 8 + 4096;   // + admit list, scalars, finished flags
+    e = cudaMallocHost((void**)&s->hbuf, s->hcap);
+    if (e != cudaSuccess) { s->hbuf = nullptr; return bail(fail(GBFIT_E_OOM, "cudaMallocHost: %s", cudaGetErrorString(e))); }
+    e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(fail(GBFIT_E_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
+    s->pool_alloc.reset(s->budget);
+    s->tile_alloc.reset(s->max_tiles);
+    s->group_alloc.reset(s->max_groups);
+    s->slots.resize(s->max_slots);
+    // device image: engine header and all slots marked done
+    memset(s->hbuf, 0, s->L->res_hdr);
+    Engine E;
+    memset(&E, 0, sizeof E);
+    char* job = s->job;
+    Engine* Ed = (Engine*)job;
+    E.results = (FitResult*)(job + s->L->res);
+    E.out = (int*)(job + s->L->res_hdr);
+    E.desc = (FitDesc*)(job + s->L->desc);
+    E.state = (FitState*)(job + s->L->state);
+    E.items = (WorkItem*)(job + s->L->items);
+    E.group_cnt = (int*)(job + s->L->gcnt);
+    E.fit_cnt = (int*)(job + s->L->fcnt);
+    E.tile_part = s->tile_part; E.tile_part_d = s->tile_part_d; E.group_part = s->group_part;
+    E.n_items = &Ed->sc[0]; E.running = &Ed->sc[1]; E.rounds = &Ed->sc[2];
+    E.max_rounds = &Ed->sc[3]; E.nfits_dev = &Ed->sc[4];
+    E.sc[3] = 1 << 30;
+    E.sc[4] = s->max_slots;
+    memcpy(s->hbuf, &E, sizeof E);
+    FitState* hs = (FitState*)(s->hbuf + s->L->state);
+    for (int k = 0; k < s->max_slots; ++k) hs[k].run = RS_DONE;
+    e = cudaMemcpyAsync(s->job, s->hbuf, s->L->res_hdr, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return bail(fail(GBFIT_E_CUDA, "server init: %s", cudaGetErrorString(e)));
+    *out = s;
+    return GBFIT_OK;
+}
+
+int gbfit_server_submit(gbfit_server* s, const gbfit_request* r, uint64_t* ticket) {
+    if (!s || !r) return fail(GBFIT_E_INVALID_ARG, "server and request must not be NULL");
+    int n, rc;
+    if ((rc = check_common(r->model_id, r->x_layout, r->dtype, r->ydata, &n))) return rc;
+    if (r->m < n) return fail(GBFIT_E_INVALID_ARG, "m = %lld < n = %d", (long long)r->m, n);
+    if (r->x_layout == GBFIT_X_GRID && (r->grid_w <= 0 || r->grid_h <= 0 || r->grid_w * r->grid_h != r->m))
+        return fail(GBFIT_E_INVALID_ARG, "grid_w * grid_h must equal m");
+    if (r->x_layout != GBFIT_X_GRID && !r->xdata) return fail(GBFIT_E_INVALID_ARG, "xdata is NULL");
+    FitArgs a{r->model_id, n, r->x_layout, r->dtype, r->m, r->grid_w, r->xdata, nullptr, r->ydata, r->sigma,
+              r->p0, r->has_bounds ? r->lb : nullptr, r->has_bounds ? r->ub : nullptr};
+    bool bounded;
+    if ((rc = check_params(a, &bounded))) return rc;
+    size_t need = req_data_bytes(*r);
+    int tp = choose_tile(r->m, 0);
+    size_t nt = (size_t)((r->m + tp - 1) / tp);
+    if (need > s->budget || nt > s->max_tiles)
+        return fail(GBFIT_E_BUDGET, "request needs %zu bytes; the server's pool holds %zu", need, s->budget);
+    std::lock_guard<std::mutex> g(s->mu);
+    SrvPending p;
+    p.req = *r;
+    p.ticket = s->next_ticket++;
+    p.t_submit = now_s();
+    s->queue.push_back(p);
+    if (ticket) *ticket = p.ticket;
+    return GBFIT_OK;
+}
+
+static int server_retire(gbfit_server* s) {
+    // which resident fits finished: the `run` word of every slot's state
+    int* flags = (int*)(s->hbuf + s->L->end + (size_t)s->max_slots * 4 + 256);
+    CUDA_TRY(cudaMemcpy2DAsync(flags, sizeof(int), s->job + s->L->state + offsetof(FitState, run), sizeof(FitState),
+                               sizeof(int), (size_t)s->max_slots, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    FitResult* hr = (FitResult*)(s->hbuf + s->L->res);
+    std::vector<int> fin;
+    for (int k = 0; k < s->max_slots; ++k)
+        if (s->slots[k].used && flags[k] == RS_DONE) {
+            fin.push_back(k);
+            CUDA_TRY(cudaMemcpyAsync(hr + k, s->job + s->L->res + (size_t)k * sizeof(FitResult), sizeof(FitResult),
+                                     cudaMemcpyDeviceToHost, s->stream));
+        }
+    if (fin.empty()) return GBFIT_OK;
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    double t = now_s();
+    for (int k : fin) {
+        SrvSlot& sl = s->slots[k];
+        gbfit_result_rec rec;
+        memset(&rec, 0, sizeof rec);
+        rec.ticket = sl.ticket;
+        rec.tag = sl.tag;
+        rec.fit_status = hr[k].fit_status;
+        rec.status = hr[k].fit_status == -2 ? GBFIT_E_INVALID_ARG : GBFIT_OK;
+        rec.nfev = hr[k].nfev;
+        rec.n_params = sl.n;
+        rec.cost = hr[k].cost;
+        for (int i = 0; i < sl.n; ++i) rec.popt[i] = hr[k].popt[i];
+        rec.t_submit = sl.t_submit;
+        rec.t_admit = sl.t_admit;
+        rec.t_done = t;
+        s->done.push_back(rec);
+        s->pool_alloc.release(sl.data_off, sl.data_bytes);
+        s->tile_alloc.release(sl.tile0, sl.ntiles);
+        s->group_alloc.release(sl.group0, sl.ngroups);
+        sl.used = false;
+    }
+    return GBFIT_OK;
+}
+
+int gbfit_server_step(gbfit_server* s, int* n_active, int* n_queued) {
+    if (!s) return fail(GBFIT_E_INVALID_ARG, "server is NULL");
+    std::lock_guard<std::mutex> g(s->mu);
+    int rc;
+    if ((rc = server_retire(s))) return rc;
+    // ---- admit in arrival order while a slot and memory are free
+    std::vector<int> admitted;
+    int free_slot = 0;
+    while (!s->queue.empty()) {
+        SrvPending& p = s->queue.front();
+        const gbfit_request& r = p.req;
+        while (free_slot < s->max_slots && s->slots[free_slot].used) ++free_slot;
+        if (free_slot >= s->max_slots) break;
+        int n = model_nparams(r.model_id);
+        size_t need = req_data_bytes(r);
+        int tp = choose_tile(r.m, 0);
+        size_t nt = (size_t)((r.m + tp - 1) / tp), ng = (nt + GROUP_TILES - 1) / GROUP_TILES;
+        size_t off, t0, g0;
+        if (!s->pool_alloc.alloc(need, 256, &off)) break;
+        if (!s->tile_alloc.alloc(nt, 1, &t0)) { s->pool_alloc.release(off, need); break; }
+        if (!s->group_alloc.alloc(ng, 1, &g0)) { s->pool_alloc.release(off, need); s->tile_alloc.release(t0, nt); break; }
+        // copy the data into the pool: x rows, y, sigma
+        size_t es = r.dtype == GBFIT_F64 ? 8 : 4;
+        size_t xs = r.x_layout == GBFIT_X_GRID ? 0 : (r.x_layout == GBFIT_X_SOA2 ? 2 : 1);
+        char* base = s->pool + off;
+        size_t ab = arr_bytes(r), raw = (size_t)r.m * es;
+        size_t bx = ab * xs, by = ab;
+        for (size_t k = 0; k < xs; ++k)     // caller's x is [xs][m] contiguous
+            CUDA_TRY(cudaMemcpyAsync(base + k * ab, (const char*)r.xdata + k * raw, raw, cudaMemcpyDefault, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(base + bx, r.ydata, raw, cudaMemcpyDefault, s->stream));
+        if (r.sigma) CUDA_TRY(cudaMemcpyAsync(base + bx + by, r.sigma, raw, cudaMemcpyDefault, s->stream));
+        gbfit_options o = defaults();
+        o.precision = s->prec;
+        o.ftol = r.ftol > 0 ? r.ftol : 1e-8;
+        o.xtol = r.xtol > 0 ? r.xtol : 1e-8;
+        o.gtol = r.gtol > 0 ? r.gtol : 1e-8;
+        o.max_nfev = r.max_nfev;
+        FitArgs a{r.model_id, n, r.x_layout, r.dtype, r.m, r.grid_w, nullptr, nullptr, nullptr, nullptr,
+                  r.p0, r.has_bounds ? r.lb : nullptr, r.has_bounds ? r.ub : nullptr};
+        bool bounded = false;
+        for (int i = 0; i < n && r.has_bounds; ++i)
+            if (std::isfinite(r.lb[i]) || std::isfinite(r.ub[i])) bounded = true;
+        FitDesc d;
+        fill_desc(d, a, o, bounded, r.m, 0);
+        d.x = xs ? base : nullptr;
+        d.x2 = xs == 2 ? base + ab : nullptr;
+        d.y = base + bx;
+        d.w = r.sigma ? base + bx + by : nullptr;
+        d.wkind = r.sigma ? W_SIGMA : W_NONE;    // 1/sigma formed in the kernel
+        d.tile_base = (int64_t)t0;
+        d.group_base = (int64_t)g0;
+        FitState* st = (FitState*)(s->hbuf + s->L->state) + free_slot;
+        memset(st, 0, sizeof(FitState));
+        st->run = RS_RUNNING;
+        st->phase = PH_INIT;
+        for (int i = 0; i < n; ++i) { st->x[i] = r.p0[i]; st->xt[i] = r.p0[i]; st->scale_inv[i] = 1.0; }
+        FitDesc* hd = (FitDesc*)(s->hbuf + s->L->desc) + free_slot;
+        *hd = d;
+        CUDA_TRY(cudaMemcpyAsync(s->job + s->L->desc + (size_t)free_slot * sizeof(FitDesc), hd, sizeof(FitDesc),
+                                 cudaMemcpyHostToDevice, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(s->job + s->L->state + (size_t)free_slot * sizeof(FitState), st, sizeof(FitState),
+                                 cudaMemcpyHostToDevice, s->stream));
+        SrvSlot& sl = s->slots[free_slot];
+        sl.used = true;
+        sl.ticket = p.ticket;
+        sl.tag = r.tag;
+        sl.data_off = off; sl.data_bytes = need;
+        sl.tile0 = t0; sl.ntiles = nt; sl.group0 = g0; sl.ngroups = ng;
+        sl.t_submit = p.t_submit;
+        sl.t_admit = now_s();
+        sl.n = n;
+        admitted.push_back(free_slot);
+        s->queue.pop_front();
+    }
+    // ---- counters of new fits start at zero; pass constants at p0
+    Engine* Ed = (Engine*)s->job;
+    if (!admitted.empty()) {
+        int* hl = (int*)(s->hbuf + s->L->end);
+        for (size_t k = 0; k < admitted.size(); ++k) {
+            hl[k] = admitted[k];
+            SrvSlot& sl = s->slots[admitted[k]];
+            CUDA_TRY(cudaMemsetAsync(s->job + s->L->gcnt + sl.group0 * sizeof(int), 0, sl.ngroups * sizeof(int), s->stream));
+            CUDA_TRY(cudaMemsetAsync(s->job + s->L->fcnt + (size_t)admitted[k] * sizeof(int), 0, sizeof(int), s->stream));
+        }
+        CUDA_TRY(cudaMemcpyAsync(s->d_list, hl, admitted.size() * sizeof(int), cudaMemcpyHostToDevice, s->stream));
+        int cnt = (int)admitted.size();
+        void* a_init[] = {&Ed, &s->d_list, &cnt};
+        CUDA_TRY(cudaLaunchKernel(kernel_init_slots(s->prec), dim3(cnt < 1024 ? cnt : 1024), dim3(32), a_init, 0, s->stream));
+    }
+    // ---- compacted work list of every resident fit, then the shared rounds
+    int active = 0;
+    WorkItem* hi = (WorkItem*)(s->hbuf + s->L->items);
+    size_t ni = 0;
+    for (int k = 0; k < s->max_slots; ++k)
+        if (s->slots[k].used) {
+            ++active;
+            for (size_t t = 0; t < s->slots[k].ntiles; ++t) hi[ni++] = WorkItem{k, (int)t};
+        }
+    if (active > 0) {
+        CUDA_TRY(cudaMemcpyAsync(s->job + s->L->items, hi, ni * sizeof(WorkItem), cudaMemcpyHostToDevice, s->stream));
+        int sc2[2] = {(int)ni, active};
+        memcpy(s->hbuf + s->L->end + (size_t)s->max_slots * 4, sc2, sizeof sc2);
+        CUDA_TRY(cudaMemcpyAsync(&Ed->sc[0], s->hbuf + s->L->end + (size_t)s->max_slots * 4, sizeof sc2,
+                                 cudaMemcpyHostToDevice, s->stream));
+        void* a_eval[] = {&Ed};
+        for (int r = 0; r < s->rounds; ++r)
+            CUDA_TRY(cudaLaunchKernel(kernel_eval_round(s->prec), dim3(s->grid), dim3(EVAL_THREADS), a_eval,
+                                      eval_dyn_smem(s->prec), s->stream));
+        {
+            std::lock_guard<std::mutex> gs(g_stats_mu);
+            g_stats.kernel_launches += s->rounds + (admitted.empty() ? 0 : 1);
+        }
+    }
+    if ((rc = server_retire(s))) return rc;
+    int act = 0;
+    for (int k = 0; k < s->max_slots; ++k) act += s->slots[k].used;
+    if (n_active) *n_active = act;
+    if (n_queued) *n_queued = (int)s->queue.size();
+    return GBFIT_OK;
+}
+
+int gbfit_server_poll(gbfit_server* s, gbfit_result_rec* out, int max, int* count) {
+    if (!s || (!out && max > 0)) return fail(GBFIT_E_INVALID_ARG, "bad poll arguments");
+    std::lock_guard<std::mutex> g(s->mu);
+    int c = 0;
+    while (c < max && !s->done.empty()) { out[c++] = s->done.front(); s->done.pop_front(); }
+    if (count) *count = c;
+    return GBFIT_OK;
+}
+
+int gbfit_server_destroy(gbfit_server* s) {
+    if (!s) return GBFIT_OK;
+    if (s->stream) { cudaStreamSynchronize(s->stream); cudaStreamDestroy(s->stream); }
+    if (s->pool) cudaFree(s->pool);
+    if (s->job) cudaFree(s->job);
+    if (s->tile_part) cudaFree(s->tile_part);
+    if (s->tile_part_d) cudaFree(s->tile_part_d);
+    if (s->group_part) cudaFree(s->group_part);
+    if (s->d_list) cudaFree(s->d_list);
+    if (s->hbuf) cudaFreeHost(s->hbuf);
+    delete s->L;
+    delete s;
+    return GBFIT_OK;
+}
+
+}  // extern "C"

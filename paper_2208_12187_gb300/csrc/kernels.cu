@@ -522,6 +522,24 @@ __global__ void init_fits_kernel(const Engine* __restrict__ Ep) {
     }
 }
 
+// Pass constants at p0 for the listed fits only (serving: newly admitted
+// fits join while others are mid-fit).
+template <int PREC>
+__global__ void init_slots_kernel(const Engine* __restrict__ Ep, const int* __restrict__ slots, int count) {
+    __shared__ TrfSmem S;
+    const Engine E = *Ep;
+    for (int k = blockIdx.x; k < count; k += gridDim.x) {
+        int f = slots[k];
+        const FitDesc& d = E.desc[f];
+        FitState* st = E.state + f;
+        int l = threadIdx.x;
+        if (l < 8) { S.vec[VX][l] = (l < d.n) ? st->x[l] : 0.0; S.vec[VXT][l] = S.vec[VX][l]; }
+        __syncwarp();
+        prep_pass<PREC>(d, st, S);
+        __syncwarp();
+    }
+}
+
 __global__ void round_end_kernel(const Engine* __restrict__ Ep, cudaGraphConditionalHandle h) {
     const Engine E = *Ep;
     int r = ++(*E.rounds);
@@ -596,6 +614,9 @@ void* kernel_init_fits(int prec) {
     return prec == PREC_MIXED ? (void*)init_fits_kernel<PREC_MIXED> : (void*)init_fits_kernel<PREC_FP64>;
 }
 void* kernel_round_end() { return (void*)round_end_kernel; }
+void* kernel_init_slots(int prec) {
+    return prec == PREC_MIXED ? (void*)init_slots_kernel<PREC_MIXED> : (void*)init_slots_kernel<PREC_FP64>;
+}
 size_t eval_dyn_smem(int prec) { return prec == PREC_MIXED ? RING_BYTES : 0; }
 int eval_blocks_per_sm(int prec) {
     int b = 0;

@@ -30,7 +30,9 @@ N_PARAMS = {0: 4, 1: 5, 2: 7, 3: 3}
 
 EXPORTS = ["gbfit_version", "gbfit_last_error", "gbfit_default_options", "gbfit_model_info",
            "gbfit_curve_fit", "gbfit_curve_fit_batch", "gbfit_evaluate", "gbfit_tr_subproblem",
-           "gbfit_stats_reset", "gbfit_stats_get", "gbfit_set_profiling", "gbfit_evaluate_noalloc"]
+           "gbfit_stats_reset", "gbfit_stats_get", "gbfit_set_profiling", "gbfit_evaluate_noalloc",
+           "gbfit_server_create", "gbfit_server_submit", "gbfit_server_step", "gbfit_server_poll",
+           "gbfit_server_destroy"]
 
 
 class GbfitError(RuntimeError):
@@ -56,6 +58,27 @@ class Stats(ctypes.Structure):
 PHASES = ["tile", "combine", "logic", "eigen", "comb_fence", "step", "prep", "finish", "comb_group", "comb_final",
           "eig_warm", "eig_j32", "eig_ns", "eig_rr", "j32_sweeps", "refine_passes", "gn_path", "n_gn", "n_eig",
           "n_alg2_iters", "n_bounded_nonfull", "spare1", "spare2", "spare3"]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("precision", ctypes.c_int),
+                ("rounds_per_step", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("model_id", ctypes.c_int), ("x_layout", ctypes.c_int), ("dtype", ctypes.c_int),
+                ("has_bounds", ctypes.c_int), ("m", ctypes.c_int64), ("grid_w", ctypes.c_int64),
+                ("grid_h", ctypes.c_int64), ("xdata", ctypes.c_void_p), ("ydata", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p), ("p0", ctypes.c_double * 8), ("lb", ctypes.c_double * 8),
+                ("ub", ctypes.c_double * 8), ("ftol", ctypes.c_double), ("xtol", ctypes.c_double),
+                ("gtol", ctypes.c_double), ("max_nfev", ctypes.c_int), ("tag", ctypes.c_uint64)]
+
+
+class ResultRec(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int),
+                ("fit_status", ctypes.c_int), ("nfev", ctypes.c_int), ("n_params", ctypes.c_int),
+                ("cost", ctypes.c_double), ("popt", ctypes.c_double * 8), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
 _LIB = None
@@ -85,6 +108,11 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.gbfit_tr_subproblem.argtypes = [I, DP, DP, D, D, DP, DP, DP, P]
     lib.gbfit_evaluate_noalloc.argtypes = [I, P, I64, I, ctypes.POINTER(ctypes.c_int64), P, P, I, DP, I, I, DP, P]
     lib.gbfit_stats_get.argtypes = [ctypes.POINTER(Stats)]
+    lib.gbfit_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]
+    lib.gbfit_server_submit.argtypes = [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    lib.gbfit_server_step.argtypes = [ctypes.c_void_p, IP, IP]
+    lib.gbfit_server_poll.argtypes = [ctypes.c_void_p, ctypes.POINTER(ResultRec), I, IP]
+    lib.gbfit_server_destroy.argtypes = [ctypes.c_void_p]
     lib.gbfit_set_profiling.argtypes = [I]
     for name in EXPORTS:
         getattr(lib, name)
@@ -320,3 +348,77 @@ def evaluate_noalloc(model: int, xdata, ydata, p, sigma=None, grid_wh=None, prec
                                     _dptr(out), _stream_ptr(stream))
     _check(rc)
     return out[:nt], out[nt:nt + n], float(out[nt + n])
+
+
+class Server:
+    """Continuous-batching fit server (gbfit_server_*): submit requests at any
+    time, call step() to retire finished fits, admit queued ones and run
+    shared iterations, poll() for results."""
+
+    def __init__(self, hbm_budget_bytes=1 << 30, max_slots=4096, precision="mixed", rounds_per_step=4):
+        lib = load()
+        cfg = ServerConfig()
+        cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        cfg.max_slots = int(max_slots)
+        cfg.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision] if isinstance(precision, str) else int(precision)
+        cfg.rounds_per_step = int(rounds_per_step)
+        h = ctypes.c_void_p()
+        _check(lib.gbfit_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, model, xdata, ydata, p0, sigma=None, lb=None, ub=None, grid_wh=None, ftol=1e-8, xtol=1e-8,
+               gtol=1e-8, max_nfev=0, tag=0) -> int:
+        n = N_PARAMS[model]
+        r = Request()
+        yp, dt, yk = _array_info(ydata)
+        xp, _, xk = _array_info(xdata)
+        sp, _, sk = _array_info(sigma)
+        r.model_id, r.dtype, r.m = model, dt, int(yk.shape[0])
+        if grid_wh is not None:
+            r.x_layout, r.grid_w, r.grid_h, r.xdata = X_GRID, int(grid_wh[0]), int(grid_wh[1]), None
+        else:
+            r.x_layout = X_SOA2 if len(xk.shape) == 2 else X_VEC
+            r.xdata = xp
+        r.ydata, r.sigma = yp, sp
+        for i in range(n):
+            r.p0[i] = float(p0[i])
+        if lb is not None or ub is not None:
+            r.has_bounds = 1
+            lbv, ubv = _bounds(n, -np.inf if lb is None else lb, np.inf if ub is None else ub)
+            for i in range(n):
+                r.lb[i], r.ub[i] = lbv[i], ubv[i]
+        r.ftol, r.xtol, r.gtol, r.max_nfev, r.tag = ftol, xtol, gtol, int(max_nfev), int(tag)
+        t = ctypes.c_uint64()
+        _check(load().gbfit_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        self._keep[t.value] = (xk, yk, sk)
+        return t.value
+
+    def step(self):
+        a, q = ctypes.c_int(), ctypes.c_int()
+        _check(load().gbfit_server_step(self._h, ctypes.byref(a), ctypes.byref(q)))
+        return a.value, q.value
+
+    def poll(self, max_results=4096):
+        buf = (ResultRec * max_results)()
+        c = ctypes.c_int()
+        _check(load().gbfit_server_poll(self._h, buf, max_results, ctypes.byref(c)))
+        out = []
+        for k in range(c.value):
+            rr = buf[k]
+            self._keep.pop(rr.ticket, None)
+            out.append(dict(ticket=rr.ticket, tag=rr.tag, status=rr.status, fit_status=rr.fit_status,
+                            nfev=rr.nfev, cost=rr.cost, popt=np.array(rr.popt[:rr.n_params]),
+                            t_submit=rr.t_submit, t_admit=rr.t_admit, t_done=rr.t_done))
+        return out
+
+    def close(self):
+        if self._h:
+            load().gbfit_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -246,3 +246,66 @@ def dexp_batch(nfits: int = 4096, seed: int = 0, m_lo: int = 200, m_hi: int = 20
     ub = np.full((nfits, 5), np.inf)
     return Batch(MODEL_DEXP, np.concatenate(xs).astype(dtype), np.concatenate(ys).astype(dtype),
                  None, offsets, np.array(p0s), lb, ub, np.array(truths))
+
+
+# ---------------------------------------------------------------- serving stream
+SERVE_MIX = ((MODEL_GAUSS1D, 0.4), (MODEL_DEXP, 0.4), (MODEL_GAUSS2D, 0.2))
+
+
+class ServeStream:
+    """Request stream of the serving workload.
+
+    Each request draws its model 40% gauss1d / 40% dexp / 20% gauss2d and its
+    size m log-uniform in [m_lo, m_hi].  So that a stream of tens of thousands
+    of requests costs seconds to draw, the observations come from a few
+    pre-drawn datasets per model (`n_data` variants, each its own seed):
+      * 1D models: the first m points of a dataset of m_hi points (the points
+        are i.i.d., so any prefix is a valid draw of the same recipe);
+      * gauss2d: a W x W pixel grid, W taken from a sqrt(2) ladder between
+        sqrt(m_lo) and sqrt(m_hi), the rung nearest sqrt(m) in log scale
+        (so 2D sizes are discrete, within a factor 2^(1/4) of the draw).
+    Arrival times are drawn separately (`arrivals`).
+    """
+
+    def __init__(self, n_requests: int, seed: int = 0, m_lo: float = 1e3, m_hi: float = 4e6, n_data: int = 4,
+                 dtype=np.float32):
+        rng = np.random.default_rng(seed)
+        ids = [mdl for mdl, _ in SERVE_MIX]
+        self.models = rng.choice(ids, p=[w for _, w in SERVE_MIX], size=n_requests)
+        self.m = log_uniform_int(rng, m_lo, m_hi, n_requests)
+        self.variant = rng.integers(0, n_data, size=n_requests)
+        self.m_hi = int(m_hi)
+        self.data = {}
+        for v in range(n_data):
+            self.data[(MODEL_GAUSS1D, v)] = gauss1d(self.m_hi, seed=1000 + v, dtype=dtype)
+            self.data[(MODEL_DEXP, v)] = dexp(self.m_hi, seed=2000 + v, dtype=dtype)
+        w_lo, w_hi = math.sqrt(m_lo), math.sqrt(m_hi)
+        k = int(math.floor(2.0 * math.log2(w_hi / w_lo) + 1e-9))
+        self.ladder = sorted({int(round(w_lo * 2.0 ** (i / 2.0))) for i in range(k + 1)} | {int(math.floor(w_hi))})
+        for v in range(n_data):
+            for W in self.ladder:
+                self.data[(MODEL_GAUSS2D, v, W)] = gauss2d_grid(W, seed=3000 + 97 * v + W, dtype=dtype)
+        for k2 in range(n_requests):
+            if self.models[k2] == MODEL_GAUSS2D:
+                lw = 0.5 * math.log(float(self.m[k2]))
+                W = min(self.ladder, key=lambda w: abs(math.log(w) - lw))
+                self.m[k2] = W * W
+
+    def __len__(self) -> int:
+        return int(self.models.shape[0])
+
+    def request(self, k: int) -> Problem:
+        mdl, v, m = int(self.models[k]), int(self.variant[k]), int(self.m[k])
+        if mdl == MODEL_GAUSS2D:
+            return self.data[(mdl, v, int(round(math.sqrt(m))))]
+        pr = self.data[(mdl, v)]
+        return Problem(mdl, pr.x[:m], LAYOUT_VEC, None, pr.y[:m], None if pr.sigma is None else pr.sigma[:m],
+                       pr.p0, pr.lb, pr.ub, pr.truth)
+
+    @staticmethod
+    def arrivals(n: int, rate: float, seed: int = 0) -> np.ndarray:
+        """Open-loop Poisson arrival times (s) at `rate` requests/s; rate=inf: all at t=0."""
+        if not np.isfinite(rate):
+            return np.zeros(n)
+        rng = np.random.default_rng(seed)
+        return np.cumsum(rng.exponential(1.0 / rate, size=n))
