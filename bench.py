@@ -373,38 +373,75 @@ def run_sweep(args):
 
 
 def run_batch(args):
-    """4,096 ragged double-exponential fits in one batched launch (mixed)."""
+    """4,096 ragged double-exponential fits in one batched launch (mixed), with
+    tile shapes from the autotuner, against the plain FP64 one-fit-at-a-time
+    path on a sample; popt error of the batch against the FP64 oracle on a sample."""
     import torch
+    from oracle import trf
     from paper_2208_12187_gb300 import build, gbfit, synth
     build.build()
     gbfit.load()
     t0 = time.perf_counter()
     bt = synth.dexp_batch(args.nfits, seed=7, dtype=np.float32)
     gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    tab = gbfit.autotune(bt.model, "mixed", m_max=200_000)
+    tune_s = time.perf_counter() - t0
+    shapes = {int(b): [int(tab["tile_points"][bt.model][gbfit.PREC_MIXED][b]),
+                       int(tab["group_tiles"][bt.model][gbfit.PREC_MIXED][b])] for b in range(7, 18)}
     x = torch.as_tensor(bt.x).cuda()
     y = torch.as_tensor(bt.y).cuda()
     fit = lambda prec: gbfit.curve_fit_batch(bt.model, bt.offsets, x, y, bt.p0, lb=bt.lb, ub=bt.ub,
                                              precision=prec, **TOL)
-    res = {}
-    for prec in ("mixed",):
-        fit(prec)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ms = 0.0
-        for _ in range(args.steps):
-            torch.cuda.synchronize()
-            e0.record()
-            out = fit(prec)
-            e1.record()
-            e1.synchronize()
-            ms += e0.elapsed_time(e1)
-        ms /= args.steps
-        nfev = out["nfev"]
-        res[prec] = {"fits_per_s": bt.nfits / (ms / 1e3), "ms_per_batch": ms,
-                     "point_iters_per_s": float(np.sum((bt.offsets[1:] - bt.offsets[:-1]) * nfev)) / (ms / 1e3),
-                     "nfev_p50": float(np.median(nfev)), "nfev_max": int(nfev.max()),
-                     "status_counts": {int(k): int(v) for k, v in zip(*np.unique(out["status"], return_counts=True))}}
+    fit("mixed")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        e0.record()
+        out = fit("mixed")
+        e1.record()
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    ms /= args.steps
+    nfev = out["nfev"]
+    m = bt.offsets[1:] - bt.offsets[:-1]
+    res = {"fits_per_s": bt.nfits / (ms / 1e3), "ms_per_batch": ms,
+           "point_iters_per_s": float(np.sum(m * nfev)) / (ms / 1e3),
+           "nfev_p50": float(np.median(nfev)), "nfev_max": int(nfev.max()),
+           "status_counts": {int(k): int(v) for k, v in zip(*np.unique(out["status"], return_counts=True))}}
+    # plain FP64, one fit at a time (same device data), on a sample
+    S = min(args.serve_sample, bt.nfits)
+    for k in range(4):
+        a, b = int(bt.offsets[k]), int(bt.offsets[k + 1])
+        gbfit.curve_fit(bt.model, x[a:b], y[a:b], bt.p0[k], lb=bt.lb[k], ub=bt.ub[k], precision="fp64", **TOL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = []
+    for k in range(S):
+        a, b = int(bt.offsets[k]), int(bt.offsets[k + 1])
+        plain.append(gbfit.curve_fit(bt.model, x[a:b], y[a:b], bt.p0[k], lb=bt.lb[k], ub=bt.ub[k],
+                                     precision="fp64", **TOL)["popt"])
+    torch.cuda.synchronize()
+    plain_fps = S / (time.perf_counter() - t0)
+    # popt error of the batched mixed fits: against the FP64 oracle (sample) and the plain FP64 GPU path
+    K = min(args.oracle_sample, bt.nfits)
+    e_or = np.array([relerr_vec(out["popt"][k], trf.curve_fit_problem(bt.fit(k).astype(np.float64), **TOL)["popt"])
+                     for k in range(K)])
+    e_pl = np.array([relerr_vec(out["popt"][k], plain[k]) for k in range(S)])
+    err = lambda e: {"max": float(e.max()), "p50": float(np.median(e)), "frac_le_1e-6": float(np.mean(e <= 1e-6))}
     print(json.dumps({"mode": "batch", "model": "dexp", "nfits": bt.nfits, "total_points": int(bt.offsets[-1]),
-                      "generate_s": gen_s, **res}))
+                      "m": "log-uniform [200, 200000]", "data": "synthetic fp32", "generate_s": gen_s,
+                      "autotune_s": tune_s, "tuned_shapes_log2m_to_tile_group": shapes, "mixed_batched": res,
+                      "plain_fp64_one_at_a_time": {"fits_per_s": plain_fps, "sample": S},
+                      "batched_over_plain_fits_per_s": res["fits_per_s"] / plain_fps,
+                      "popt_rel_err_vs_oracle": {**err(e_or), "sample": K},
+                      "popt_rel_err_vs_plain_fp64_gpu": {**err(e_pl), "sample": S}}))
+
+
+def relerr_vec(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1.0)))
 
 
 def _serve_submit(srv, pr, k):
@@ -463,6 +500,10 @@ def run_serve(args):
     build.build()
     gbfit.load()
     t0 = time.perf_counter()
+    for mdl in (synth.MODEL_GAUSS1D, synth.MODEL_DEXP, synth.MODEL_GAUSS2D):
+        gbfit.autotune(mdl, "mixed", m_max=4_000_000)
+    tune_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
     st = synth.ServeStream(args.serve_requests, seed=11, n_data=2, dtype=np.float32)
     pin = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     for key, pr in list(st.data.items()):
@@ -473,7 +514,7 @@ def run_serve(args):
     base = {"mode": "serve", "requests": N, "mix": "40% gauss1d / 40% dexp / 20% gauss2d",
             "m": "log-uniform [1e3, 4e6] (2D: nearest W x W rung)", "mean_m": float(st.m.mean()),
             "budget_gb": args.serve_budget_gb, "slots": args.serve_slots, "rounds_per_step": args.serve_rounds,
-            "data": "synthetic fp32, pinned host buffers", "generate_s": gen_s}
+            "data": "synthetic fp32, pinned host buffers", "generate_s": gen_s, "autotune_s": tune_s}
     pct = lambda lat: {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3)}
     # warm-up (builds, first-touch of the pool)
     serve_open_loop(st, idx[:64], np.zeros(64), args)
@@ -543,6 +584,7 @@ def main():
     ap.add_argument("--nfits", type=int, default=4096)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--precisions", default="mixed,fp64")
+    ap.add_argument("--oracle-sample", type=int, default=64)
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-sample", type=int, default=200)

@@ -93,7 +93,8 @@ typedef struct gbfit_options {
     int absolute_sigma;        /* 1: pcov not rescaled by 2 cost / (m - n)                       */
     int precision;             /* GBFIT_PREC_*                                                   */
     int tile_points;           /* points per reduction tile; 0 = library choice                  */
-    int reserved[4];
+    int group_tiles;           /* tiles per first-level combine group; 0 = library choice        */
+    int reserved[3];
 } gbfit_options;
 
 /* Library version (GBFIT_VERSION). */
@@ -157,6 +158,54 @@ int gbfit_curve_fit_batch(int model_id, int nfits, const int64_t* offsets,
                           void* cuda_stream);
 
 /*
+ * Tiling of batched and served fits (no paper counterpart: the paper's JAX
+ * kernels are shaped per problem by its compiler).  A fit's evaluation pass
+ * is cut into reduction tiles of tile_points points (one CTA reduces one
+ * tile to a row of partial sums); rows are combined in groups of
+ * group_tiles, then across groups.  The best shape depends on the model, the
+ * precision mode and m.  The library keeps one table indexed
+ * [model_id][precision][floor(log2 m)] (the last bucket also takes larger m);
+ * gbfit_curve_fit_batch and the server read it for every fit whose options
+ * leave tile_points / group_tiles at 0, so a fit's shape depends only on its
+ * own m and the installed table.  Single fits (gbfit_curve_fit) instead
+ * spread m over every SM.  Defaults: mixed 32768 points, FP64 4096 points,
+ * groups of 32 (a fit smaller than its tile is one tile).
+ */
+#define GBFIT_TUNE_BUCKETS 32
+typedef struct gbfit_tune_table {
+    int32_t tile_points[GBFIT_NUM_MODELS][2][GBFIT_TUNE_BUCKETS];   /* [model][precision][log2 m] */
+    int32_t group_tiles[GBFIT_NUM_MODELS][2][GBFIT_TUNE_BUCKETS];
+} gbfit_tune_table;
+
+/* Copy out the installed table. */
+int gbfit_tune_get(gbfit_tune_table* out);
+
+/* Install a table (host memory, copied).  Each tile_points must be a multiple
+ * of 256 in [256, 2^24], each group_tiles in [1, 1024]; otherwise
+ * GBFIT_E_INVALID_ARG and the installed table is unchanged.  Servers created
+ * earlier keep admitting with the table installed when they admit. */
+int gbfit_tune_set(const gbfit_tune_table* in);
+
+/* The shape a batched or served fit of m points gets from the installed table. */
+int gbfit_tune_shape(int model_id, int precision, int64_t m, int* tile_points, int* group_tiles);
+
+/*
+ * Autotuner: for every bucket b whose middle size m_b = 1.5 * 2^b lies in
+ * [2^10, m_max], times batched fits of model_id with m_b points each (as many
+ * fits as fill points_per_run points, at most 4096; points_per_run <= 0
+ * means 2^25) for candidate shapes: tile_points 2^10 .. 2^18 (and one tile
+ * per fit), group_tiles 8, 32, 128.  Every fit runs exactly 4 evaluations on
+ * synthetic calibration data drawn on the device (FP32 for the mixed mode,
+ * FP64 for the plain one), timed with CUDA events; the fastest shape of each
+ * bucket is installed (buckets below 2^10 take bucket 10's, buckets above
+ * m_max keep their entries).  out (optional) receives the resulting table.
+ * Allocates and frees device memory for the calibration data; takes about
+ * a second per bucket.  Errors: GBFIT_E_INVALID_ARG, GBFIT_E_OOM, GBFIT_E_CUDA.
+ */
+int gbfit_autotune(int model_id, int precision, int64_t m_max, int64_t points_per_run,
+                   gbfit_tune_table* out, void* cuda_stream);
+
+/*
  * Evaluate the fused reduction once at parameters p (no iteration): the
  * packed upper triangle of B = J^T J (n(n+1)/2), g = J^T r (n) and cost
  * f = r^T r / 2, all FP64, for the given precision mode (paper Eqs. msqe,
@@ -188,8 +237,9 @@ int gbfit_tr_subproblem(int n, const double* B, const double* g, double Delta, d
  * order while a slot is free and their data fits in the pool (copying it in);
  * (3) runs `rounds_per_step` trust-region iterations for every admitted fit
  * in shared launches (one evaluation kernel per iteration for all fits).
- * A fit's reduction tiling depends only on its own m, so its result is the
- * same, bit for bit, whatever else is being served.
+ * A fit's reduction tiling depends only on its own m (through the tile
+ * table, gbfit_tune_shape), so its result is the same, bit for bit, whatever
+ * else is being served.
  */
 typedef struct gbfit_server gbfit_server;
 
@@ -291,7 +341,8 @@ typedef struct gbfit_stats {
                                  (count), 15 refinement passes (count), 16 Gauss-Newton
                                  fast path, 17 fast-path steps (count), 18 eigen
                                  decompositions (count), 19 Algorithm 2 iterations
-                                 (count), 20 bounded non-full steps (count), 21-23 spare */
+                                 (count), 20 bounded non-full steps (count), 21 item start to
+                                 tile start, 22 tile loop (of 0), 23 spare */
 } gbfit_stats;
 
 /* Zero the counters. */

@@ -247,6 +247,42 @@ int choose_tile(int64_t m, int user) {
     return (int)t;
 }
 
+// ---- tile table of batched and served fits (gbfit_tune_*)
+std::mutex g_tune_mu;
+gbfit_tune_table g_tune = [] {
+    gbfit_tune_table t;
+    for (int mo = 0; mo < GBFIT_NUM_MODELS; ++mo)
+        for (int b = 0; b < GBFIT_TUNE_BUCKETS; ++b) {
+            t.tile_points[mo][PREC_MIXED][b] = 32768;
+            t.tile_points[mo][PREC_FP64][b] = 4096;
+            t.group_tiles[mo][PREC_MIXED][b] = t.group_tiles[mo][PREC_FP64][b] = GROUP_TILES;
+        }
+    return t;
+}();
+
+int tune_bucket(int64_t m) {
+    int b = 0;
+    while (b + 1 < GBFIT_TUNE_BUCKETS && (m >> (b + 1)) > 0) ++b;
+    return b;
+}
+
+// Shape of a batched / served fit: user values where given, else the table;
+// a fit smaller than its tile is one tile.
+void multi_shape(int model, int prec, int64_t m, int user_tile, int user_group, int* tile, int* group) {
+    int t, g;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        int b = tune_bucket(m);
+        t = g_tune.tile_points[model][prec][b];
+        g = g_tune.group_tiles[model][prec][b];
+    }
+    if (user_tile > 0) t = ((user_tile + EVAL_THREADS - 1) / EVAL_THREADS) * EVAL_THREADS;
+    else if (t >= m) t = (int)(((m + EVAL_THREADS - 1) / EVAL_THREADS) * EVAL_THREADS);
+    if (user_group > 0) g = user_group;
+    *tile = t;
+    *group = g;
+}
+
 struct FitArgs {
     int model, n, layout, dtype;
     int64_t m, grid_w;
@@ -275,6 +311,7 @@ int check_opts(const gbfit_options* o, int n) {
         for (int i = 0; i < n; ++i)
             if (!(o->x_scale[i] > 0) || !std::isfinite(o->x_scale[i])) return fail(GBFIT_E_INVALID_ARG, "x_scale[%d] must be > 0", i);
     if (o->tile_points < 0 || o->tile_points > (1 << 24)) return fail(GBFIT_E_INVALID_ARG, "tile_points out of range");
+    if (o->group_tiles < 0 || o->group_tiles > 1024) return fail(GBFIT_E_INVALID_ARG, "group_tiles out of range");
     return GBFIT_OK;
 }
 
@@ -418,14 +455,21 @@ int stage_data(Ctx* c, const void* x, size_t xbytes, const void* y, size_t ybyte
     return GBFIT_OK;
 }
 
-int fill_desc(FitDesc& d, const FitArgs& a, const gbfit_options& o, bool bounded, int64_t m, int tile_user) {
+// multi: the fit runs beside others (batched or served) and takes its shape
+// from the tile table; otherwise its tiles spread over every SM.
+int fill_desc(FitDesc& d, const FitArgs& a, const gbfit_options& o, bool bounded, int64_t m, bool multi) {
     memset(&d, 0, sizeof d);
     d.model = a.model; d.n = a.n; d.layout = a.layout; d.dtype = a.dtype;
     d.prec = o.precision; d.bounded = bounded ? 1 : 0; d.jac_scale = o.x_scale_jac ? 1 : 0;
     d.m = m; d.grid_w = a.grid_w;
-    d.tile_points = choose_tile(m, tile_user);
+    if (multi) {
+        multi_shape(a.model, o.precision, m, o.tile_points, o.group_tiles, &d.tile_points, &d.group_tiles);
+    } else {
+        d.tile_points = choose_tile(m, o.tile_points);
+        d.group_tiles = o.group_tiles > 0 ? o.group_tiles : GROUP_TILES;
+    }
     d.n_tiles = (int)((m + d.tile_points - 1) / d.tile_points);
-    d.n_groups = (d.n_tiles + GROUP_TILES - 1) / GROUP_TILES;
+    d.n_groups = (d.n_tiles + d.group_tiles - 1) / d.group_tiles;
     d.max_nfev = o.max_nfev > 0 ? o.max_nfev : 100 * a.n;
     for (int i = 0; i < NMAX; ++i) {
         d.lb[i] = (a.lb && i < a.n) ? a.lb[i] : -INFINITY;
@@ -516,7 +560,7 @@ static int single_fit(int model_id, const void* xdata, int64_t m, int x_layout, 
     if ((rc = stage_data(c, x_layout == GBFIT_X_GRID ? nullptr : xdata, xbytes, ydata, (size_t)m * es, sigma,
                          (size_t)m * es, s, &sd))) return rc;
     std::vector<FitDesc> hd(1);
-    fill_desc(hd[0], a, o, bounded, m, o.tile_points);
+    fill_desc(hd[0], a, o, bounded, m, false);
     const void* x2 = (x_layout == GBFIT_X_SOA2) ? (const char*)sd.x + (size_t)m * es : nullptr;
     if (sigma && o.precision == GBFIT_PREC_FP64) {
         bool changed = false;
@@ -612,7 +656,7 @@ int gbfit_curve_fit_batch(int model_id, int nfits, const int64_t* offsets, const
         int64_t a0 = offsets[f], mf = offsets[f + 1] - offsets[f];
         FitArgs a{model_id, n, x_layout, dtype, mf, 0, nullptr, nullptr, ydata, sigma,
                   p0 + (size_t)f * n, lb ? lb + (size_t)f * n : nullptr, ub ? ub + (size_t)f * n : nullptr};
-        fill_desc(hd[f], a, o, bnd[f], mf, o.tile_points);
+        fill_desc(hd[f], a, o, bnd[f], mf, true);
         const char* xb = (const char*)sd.x + a0 * es;
         const void* x2 = x_layout == GBFIT_X_SOA2 ? (const char*)sd.x + (total + a0) * es : nullptr;
         set_data(c, hd[f], xb, x2, (const char*)sd.y + a0 * es, sigma ? (const char*)sd.sigma + a0 * es : nullptr, a0, s);
@@ -630,6 +674,152 @@ int gbfit_curve_fit_batch(int model_id, int nfits, const int64_t* offsets, const
         if (fit_status) fit_status[f] = r.fit_status;
     }
     return GBFIT_OK;
+}
+
+int gbfit_tune_get(gbfit_tune_table* out) {
+    if (!out) return fail(GBFIT_E_INVALID_ARG, "out is NULL");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    *out = g_tune;
+    return GBFIT_OK;
+}
+
+int gbfit_tune_set(const gbfit_tune_table* in) {
+    if (!in) return fail(GBFIT_E_INVALID_ARG, "table is NULL");
+    for (int mo = 0; mo < GBFIT_NUM_MODELS; ++mo)
+        for (int p = 0; p < 2; ++p)
+            for (int b = 0; b < GBFIT_TUNE_BUCKETS; ++b) {
+                int t = in->tile_points[mo][p][b], g = in->group_tiles[mo][p][b];
+                if (t < EVAL_THREADS || t > (1 << 24) || t % EVAL_THREADS)
+                    return fail(GBFIT_E_INVALID_ARG, "tile_points[%d][%d][%d] = %d is not a multiple of %d in [%d, 2^24]",
+                                mo, p, b, t, EVAL_THREADS, EVAL_THREADS);
+                if (g < 1 || g > 1024) return fail(GBFIT_E_INVALID_ARG, "group_tiles[%d][%d][%d] = %d", mo, p, b, g);
+            }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune = *in;
+    return GBFIT_OK;
+}
+
+int gbfit_tune_shape(int model_id, int precision, int64_t m, int* tile_points, int* group_tiles) {
+    if (model_id < 0 || model_id >= GBFIT_NUM_MODELS) return fail(GBFIT_E_INVALID_ARG, "unknown model %d", model_id);
+    if (precision != GBFIT_PREC_FP64 && precision != GBFIT_PREC_MIXED) return fail(GBFIT_E_INVALID_ARG, "unknown precision %d", precision);
+    if (m < 1) return fail(GBFIT_E_INVALID_ARG, "m must be >= 1");
+    int t, g;
+    multi_shape(model_id, precision, m, 0, 0, &t, &g);
+    if (tile_points) *tile_points = t;
+    if (group_tiles) *group_tiles = g;
+    return GBFIT_OK;
+}
+
+int gbfit_autotune(int model_id, int precision, int64_t m_max, int64_t points_per_run, gbfit_tune_table* out,
+                   void* cuda_stream) {
+    if (model_id < 0 || model_id >= GBFIT_NUM_MODELS) return fail(GBFIT_E_INVALID_ARG, "unknown model %d", model_id);
+    if (precision != GBFIT_PREC_FP64 && precision != GBFIT_PREC_MIXED) return fail(GBFIT_E_INVALID_ARG, "unknown precision %d", precision);
+    if (m_max < 1 || m_max > ((int64_t)1 << 31)) return fail(GBFIT_E_INVALID_ARG, "m_max out of range");
+    const int64_t ppr = points_per_run > 0 ? points_per_run : ((int64_t)1 << 25);
+    const int n = model_nparams(model_id);
+    const bool f64 = precision == GBFIT_PREC_FP64;
+    const size_t es = f64 ? 8 : 4;
+    const int layout = model_xdims(model_id) == 2 ? GBFIT_X_SOA2 : GBFIT_X_VEC;
+    Ctx* c;
+    int rc;
+    if ((rc = get_ctx(&c))) return rc;
+    std::lock_guard<std::mutex> lock(c->mu);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int64_t cap = std::max(ppr, m_max);
+    char *xb = nullptr, *yb = nullptr;
+    cudaError_t e = cudaMalloc((void**)&xb, (size_t)cap * es * (layout == GBFIT_X_SOA2 ? 2 : 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&yb, (size_t)cap * es);
+    if (e != cudaSuccess) {
+        cudaFree(xb);
+        return fail(GBFIT_E_OOM, "autotune calibration data: %s", cudaGetErrorString(e));
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto cleanup = [&](int r) { cudaFree(xb); cudaFree(yb); cudaEventDestroy(e0); cudaEventDestroy(e1); return r; };
+    gbfit_tune_table tab;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tab = g_tune;
+    }
+    int first_b = -1;
+    for (int b = 10; b < GBFIT_TUNE_BUCKETS; ++b) {
+        const int64_t mb = (int64_t)3 << (b - 1);
+        if (mb > m_max) break;
+        const int64_t nf = std::max<int64_t>(1, std::min<int64_t>(4096, ppr / mb));
+        // calibration parameters (the 2D centre and widths follow the grid side)
+        double truth[NMAX] = {0};
+        const double Wd = std::ceil(std::sqrt((double)mb));
+        switch (model_id) {
+            case 0: { double t[] = {5.0, 0.3, 1.2, 0.5}; std::copy(t, t + 4, truth); break; }
+            case 1: { double t[] = {4.0, 0.8, 6.0, 9.0, 0.5}; std::copy(t, t + 5, truth); break; }
+            case 2: { double t[] = {980.0, 0.5 * Wd, 0.48 * Wd, 0.06 * Wd, 0.035 * Wd, 0.4, 20.0}; std::copy(t, t + 7, truth); break; }
+            default: { double t[] = {1.5, -0.7, 0.25}; std::copy(t, t + 3, truth); break; }
+        }
+        e = launch_synth_fill(model_id, f64, xb, layout == GBFIT_X_SOA2 ? xb + (size_t)cap * es : nullptr, yb,
+                              nf * mb, mb, 1234u + (uint32_t)b, c->sms * 8, truth, s);
+        if (e != cudaSuccess) return cleanup(fail(GBFIT_E_CUDA, "autotune data: %s", cudaGetErrorString(e)));
+        std::vector<double> p0(n);
+        for (int i = 0; i < n; ++i) p0[i] = truth[i] * 1.05;
+        if (model_id == 2) { p0[1] = truth[1] + 1.0; p0[2] = truth[2] - 1.0; p0[5] = truth[5] + 0.02; }
+        std::vector<std::vector<double>> p0s(nf, p0);
+        gbfit_options o = defaults();
+        o.precision = precision;
+        o.ftol = o.xtol = o.gtol = 0.0;
+        o.max_nfev = 4;
+        // candidates: powers of two up to 2^18 below 2 m, and one tile per fit
+        std::vector<int> tiles;
+        for (int k = 10; k <= 18; ++k)
+            if (((int64_t)1 << k) < mb) tiles.push_back(1 << k);
+        if (mb <= ((int64_t)1 << 18)) tiles.push_back((int)((mb + EVAL_THREADS - 1) / EVAL_THREADS * EVAL_THREADS));
+        float best = 1e30f;
+        int bt = tiles.back(), bg = GROUP_TILES;
+        for (int tp : tiles) {
+            int64_t ntl = (mb + tp - 1) / tp;
+            std::vector<int> groups = ntl > 8 ? std::vector<int>{8, 32, 128} : std::vector<int>{GROUP_TILES};
+            for (int g : groups) {
+                o.tile_points = tp;
+                o.group_tiles = g;
+                std::vector<FitDesc> hd(nf);
+                for (int64_t f = 0; f < nf; ++f) {
+                    FitArgs a{model_id, n, layout, f64 ? GBFIT_F64 : GBFIT_F32, mb, 0, nullptr, nullptr, nullptr, nullptr,
+                              p0.data(), nullptr, nullptr};
+                    fill_desc(hd[f], a, o, false, mb, true);
+                    hd[f].x = xb + (size_t)(f * mb) * es;
+                    hd[f].x2 = layout == GBFIT_X_SOA2 ? xb + (size_t)(cap + f * mb) * es : nullptr;
+                    hd[f].y = yb + (size_t)(f * mb) * es;
+                    hd[f].w = nullptr;
+                    hd[f].wkind = W_NONE;
+                }
+                float ms = 0.0f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    std::vector<FitResult> hr;
+                    std::vector<FitDesc> hdc = hd;
+                    e = cudaEventRecord(e0, s);
+                    if (e == cudaSuccess && (rc = run_fits(c, precision, hdc, p0s, hr, s, nullptr))) return cleanup(rc);
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    if (e != cudaSuccess) return cleanup(fail(GBFIT_E_CUDA, "autotune timing: %s", cudaGetErrorString(e)));
+                }
+                if (ms < best) { best = ms; bt = tp; bg = g; }
+            }
+        }
+        tab.tile_points[model_id][precision][b] = bt;
+        tab.group_tiles[model_id][precision][b] = bg;
+        if (first_b < 0) first_b = b;
+    }
+    if (first_b >= 0)
+        for (int b = 0; b < first_b; ++b) {
+            tab.tile_points[model_id][precision][b] = tab.tile_points[model_id][precision][first_b];
+            tab.group_tiles[model_id][precision][b] = tab.group_tiles[model_id][precision][first_b];
+        }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune = tab;
+    }
+    if (out) *out = tab;
+    return cleanup(GBFIT_OK);
 }
 
 int gbfit_stats_reset(void) {
@@ -688,7 +878,7 @@ int gbfit_tr_subproblem(int n, const double* B, const double* g, double Delta, d
 // this library holds until the process exits.
 namespace {
 constexpr int NOALLOC_MAX_TILES = 2048;                                   // reduction tiles per call
-constexpr int NOALLOC_MAX_GROUPS = (NOALLOC_MAX_TILES + GROUP_TILES - 1) / GROUP_TILES;
+constexpr int NOALLOC_MAX_GROUPS = (NOALLOC_MAX_TILES + GROUP_TILES - 1) / GROUP_TILES;   // default groups
 
 struct NoAllocLayout {
     static constexpr size_t eng = 0;
@@ -791,7 +981,7 @@ extern "C" int gbfit_evaluate_noalloc(int model_id, const void* xdata, int64_t m
     o.max_nfev = 1;
     FitArgs a{model_id, n, x_layout, dtype, m, gw, xdata, nullptr, ydata, sigma, p, nullptr, nullptr};
     FitDesc d;
-    fill_desc(d, a, o, false, m, tile_points);
+    fill_desc(d, a, o, false, m, false);
     size_t es = dtype == GBFIT_F64 ? 8 : 4;
     d.x = x_layout == GBFIT_X_GRID ? nullptr : xdata;
     d.x2 = (x_layout == GBFIT_X_SOA2) ? (const char*)xdata + (size_t)m * es : nullptr;
@@ -934,9 +1124,19 @@ int gbfit_server_create(const gbfit_server_config* cfg_in, gbfit_server** out) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
     int bps = eval_blocks_per_sm(s->prec);
     s->grid = sms * (bps < 1 ? 1 : bps);
-    // tile scratch: enough for the budget filled with the smallest tiles
-    s->max_tiles = s->budget / (size_t(TILE_MIN) * 8) + (size_t)s->max_slots;
-    s->max_groups = s->max_tiles / GROUP_TILES + (size_t)s->max_slots;
+    // tile scratch: enough for the budget filled with the smallest tiles and
+    // groups of the tile table (at 8 bytes per point)
+    int min_tile = 1 << 24, min_group = 1024;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (int mo = 0; mo < GBFIT_NUM_MODELS; ++mo)
+            for (int b = 0; b < GBFIT_TUNE_BUCKETS; ++b) {
+                min_tile = std::min(min_tile, (int)g_tune.tile_points[mo][s->prec][b]);
+                min_group = std::min(min_group, (int)g_tune.group_tiles[mo][s->prec][b]);
+            }
+    }
+    s->max_tiles = s->budget / (size_t(min_tile) * 8) + (size_t)s->max_slots;
+    s->max_groups = s->max_tiles / (size_t)min_group + (size_t)s->max_slots;
     s->L = new JobLayout((size_t)s->max_slots, s->max_tiles, s->max_groups);
     bool ch = false;
     size_t cap = 0;
@@ -1000,7 +1200,8 @@ int gbfit_server_submit(gbfit_server* s, const gbfit_request* r, uint64_t* ticke
     bool bounded;
     if ((rc = check_params(a, &bounded))) return rc;
     size_t need = req_data_bytes(*r);
-    int tp = choose_tile(r->m, 0);
+    int tp, gt;
+    multi_shape(r->model_id, s->prec, r->m, 0, 0, &tp, &gt);
     size_t nt = (size_t)((r->m + tp - 1) / tp);
     if (need > s->budget || nt > s->max_tiles)
         return fail(GBFIT_E_BUDGET, "request needs %zu bytes; the server's pool holds %zu", need, s->budget);
@@ -1070,8 +1271,20 @@ int gbfit_server_step(gbfit_server* s, int* n_active, int* n_queued) {
         if (free_slot >= s->max_slots) break;
         int n = model_nparams(r.model_id);
         size_t need = req_data_bytes(r);
-        int tp = choose_tile(r.m, 0);
-        size_t nt = (size_t)((r.m + tp - 1) / tp), ng = (nt + GROUP_TILES - 1) / GROUP_TILES;
+        gbfit_options o = defaults();
+        o.precision = s->prec;
+        o.ftol = r.ftol > 0 ? r.ftol : 1e-8;
+        o.xtol = r.xtol > 0 ? r.xtol : 1e-8;
+        o.gtol = r.gtol > 0 ? r.gtol : 1e-8;
+        o.max_nfev = r.max_nfev;
+        FitArgs a{r.model_id, n, r.x_layout, r.dtype, r.m, r.grid_w, nullptr, nullptr, nullptr, nullptr,
+                  r.p0, r.has_bounds ? r.lb : nullptr, r.has_bounds ? r.ub : nullptr};
+        bool bounded = false;
+        for (int i = 0; i < n && r.has_bounds; ++i)
+            if (std::isfinite(r.lb[i]) || std::isfinite(r.ub[i])) bounded = true;
+        FitDesc d;
+        fill_desc(d, a, o, bounded, r.m, true);
+        size_t nt = (size_t)d.n_tiles, ng = (size_t)d.n_groups;
         size_t off, t0, g0;
         if (!s->pool_alloc.alloc(need, 256, &off)) break;
         if (!s->tile_alloc.alloc(nt, 1, &t0)) { s->pool_alloc.release(off, need); break; }
@@ -1086,19 +1299,6 @@ int gbfit_server_step(gbfit_server* s, int* n_active, int* n_queued) {
             CUDA_TRY(cudaMemcpyAsync(base + k * ab, (const char*)r.xdata + k * raw, raw, cudaMemcpyDefault, s->stream));
         CUDA_TRY(cudaMemcpyAsync(base + bx, r.ydata, raw, cudaMemcpyDefault, s->stream));
         if (r.sigma) CUDA_TRY(cudaMemcpyAsync(base + bx + by, r.sigma, raw, cudaMemcpyDefault, s->stream));
-        gbfit_options o = defaults();
-        o.precision = s->prec;
-        o.ftol = r.ftol > 0 ? r.ftol : 1e-8;
-        o.xtol = r.xtol > 0 ? r.xtol : 1e-8;
-        o.gtol = r.gtol > 0 ? r.gtol : 1e-8;
-        o.max_nfev = r.max_nfev;
-        FitArgs a{r.model_id, n, r.x_layout, r.dtype, r.m, r.grid_w, nullptr, nullptr, nullptr, nullptr,
-                  r.p0, r.has_bounds ? r.lb : nullptr, r.has_bounds ? r.ub : nullptr};
-        bool bounded = false;
-        for (int i = 0; i < n && r.has_bounds; ++i)
-            if (std::isfinite(r.lb[i]) || std::isfinite(r.ub[i])) bounded = true;
-        FitDesc d;
-        fill_desc(d, a, o, bounded, r.m, 0);
         d.x = xs ? base : nullptr;
         d.x2 = xs == 2 ? base + ab : nullptr;
         d.y = base + bx;

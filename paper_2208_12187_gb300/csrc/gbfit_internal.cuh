@@ -44,7 +44,7 @@ struct FitDesc {
     int64_t group_base;    // first row in the group-partial buffer / group counters
     double lb[NMAX], ub[NMAX], xscale[NMAX];
     double ftol, xtol, gtol;
-    int absolute_sigma, pad_;
+    int absolute_sigma, group_tiles;
 };
 
 // Mutable per-fit state, kept on the device across iterations.

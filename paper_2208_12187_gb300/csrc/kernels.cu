@@ -23,6 +23,8 @@
 
 namespace gbfit {
 
+__constant__ double c_synth_truth[4][NMAX];   // autotuner calibration parameters per model
+
 // ------------------------------------------------------------------ warp/block reduction
 // Reduce-scatter across the warp: after 5 halvings lane l holds the warp sum
 // of ceil(K/32) slots.  Costs about K shuffles instead of 5 K.
@@ -226,6 +228,15 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     return false;
 }
 
+// Arrival on a combine counter: one gpu-scope acq_rel atomic by one thread
+// after a CTA barrier releases the CTA's partial-sum stores (cumulativity
+// through the barrier) and, for the last arriver, acquires everyone else's.
+__device__ __forceinline__ int arrive_acq_rel(int* ctr) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(ctr) : "memory");
+    return old;
+}
+
 struct RingState {
     unsigned long long* bar;     // [NST] mbarriers
     float* buf;                  // [NST][RING_ARRAYS][CHUNK]
@@ -307,7 +318,7 @@ struct RoundSmem {
     unsigned long long mbar[NST];
     int ring_fail;
     FitDesc desc;
-    long long t_mark, t_fence, t_group;
+    long long t_mark, t_fence, t_group, t_loop;
     float pf[PF];
     double pd[PD];
     int flag[4];
@@ -321,14 +332,26 @@ struct RoundSmem {
 
 // Sum rows [0, nrows) of a [rows][KMAX] array into out[0..K) in a fixed order
 // using all threads: thread t handles slot t % K over rows = part (mod P).
+// Loads go out in batches of 8 rows per thread before any add, so that one
+// L2 round trip covers a batch (rows were written by other CTAs: __ldcg).
 template <typename T>
 __device__ void combine_rows(const T* rows, int nrows, int K, double* scratch, double* out) {
+    constexpr int BATCH = 8;
     int P = EVAL_THREADS / K;
     int t = threadIdx.x;
     int k = t % K, part = t / K;
     double s = 0.0;
     if (part < P)
-        for (int r = part; r < nrows; r += P) s += double(__ldcg(rows + (int64_t)r * KMAX + k));   // L2: written by other CTAs
+        for (int r0 = part; r0 < nrows; r0 += BATCH * P) {
+            T v[BATCH];
+#pragma unroll
+            for (int u = 0; u < BATCH; ++u) {
+                int r = r0 + u * P;
+                v[u] = r < nrows ? __ldcg(rows + (int64_t)r * KMAX + k) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < BATCH; ++u) s += double(v[u]);
+        }
     scratch[t] = s;
     __syncthreads();
     if (t < K) {
@@ -380,7 +403,7 @@ __device__ void eval_tile_dispatch(const RoundSmem& sm, int64_t i0, int64_t i1, 
 }
 
 template <class M, int PREC>
-__device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, RingState& R) {
+__device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, RingState& R, long long t_item) {
     using AT = typename AccT<PREC>::T;
     constexpr int N = M::N;
     constexpr int K = n_acc(N, PREC);
@@ -394,6 +417,7 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
     int bad = 0;
     AT acc[K];
     eval_tile_dispatch<M, PREC>(sm, i0, i1, check, bad, acc, R);
+    if (threadIdx.x == 0) sm.t_loop = clock64();
     if (sm.ring_fail && threadIdx.x == 0) atomicOr(&stp->bad_data, 2);   // a bounded wait gave up
     if (check) {
         int any = __syncthreads_or(bad);
@@ -409,18 +433,16 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
         else E.tile_part_d[row * KMAX + threadIdx.x] = double(tsum);
     }
     // ---- last arriver of the group combines the group
-    __threadfence();
     __syncthreads();
-    int group = tile / GROUP_TILES;
-    int g0 = group * GROUP_TILES;
-    int gsize = min(GROUP_TILES, d.n_tiles - g0);
+    int group = tile / d.group_tiles;
+    int g0 = group * d.group_tiles;
+    int gsize = min(d.group_tiles, d.n_tiles - g0);
     if (threadIdx.x == 0) {
-        int old = atomicAdd(&E.group_cnt[d.group_base + group], 1);
+        int old = arrive_acq_rel(&E.group_cnt[d.group_base + group]);
         sm.flag[2] = (old == gsize - 1);
     }
     __syncthreads();
     if (!sm.flag[2]) return;
-    __threadfence();
     if (threadIdx.x == 0) sm.t_fence = clock64();
     double* gout = E.group_part + (d.group_base + group) * KMAX;
     if (PREC == PREC_MIXED)
@@ -434,25 +456,25 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
     if (d.n_groups > 1) {
         // second level: the last group of the fit combines the group sums
         if (threadIdx.x < K) gout[threadIdx.x] = sm.trf.tot[threadIdx.x];
-        __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
-            int old = atomicAdd(&E.fit_cnt[fit], 1);
+            int old = arrive_acq_rel(&E.fit_cnt[fit]);
             sm.flag[3] = (old == d.n_groups - 1);
         }
         __syncthreads();
         if (!sm.flag[3]) return;
-        __threadfence();
         combine_rows<double>(E.group_part + d.group_base * KMAX, d.n_groups, K, sm.comb, sm.trf.tot);
     }
     if (threadIdx.x == 0) {
         E.fit_cnt[fit] = 0;
         long long now = clock64();
-        stp->trace[TR_COMBINE] += (unsigned long long)(now - sm.t_mark);
-        stp->trace[TR_C_FENCE] += (unsigned long long)(sm.t_fence - sm.t_mark);
-        stp->trace[TR_C_GROUP] += (unsigned long long)(sm.t_group - sm.t_fence);
-        stp->trace[TR_C_FINAL] += (unsigned long long)(now - sm.t_group);
-        stp->trace[TR_TILE] += (unsigned long long)(sm.t_mark - t_tile);
+        trace_bump(stp->trace, TR_COMBINE, (unsigned long long)(now - sm.t_mark));
+        trace_bump(stp->trace, TR_C_FENCE, (unsigned long long)(sm.t_fence - sm.t_mark));
+        trace_bump(stp->trace, TR_C_GROUP, (unsigned long long)(sm.t_group - sm.t_fence));
+        trace_bump(stp->trace, TR_C_FINAL, (unsigned long long)(now - sm.t_group));
+        trace_bump(stp->trace, TR_TILE, (unsigned long long)(sm.t_mark - t_tile));
+        trace_bump(stp->trace, TR_PRE_TILE, (unsigned long long)(t_tile - t_item));
+        trace_bump(stp->trace, TR_TILE_LOOP, (unsigned long long)(sm.t_loop - t_tile));
     }
     __syncthreads();
     trf_step<PREC>(d, stp, E.results + fit, sm.trf, E.running);
@@ -481,6 +503,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) eval_round_kernel(const Engin
     }
     int n_items = *E.n_items;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        long long t_item = clock64();
         WorkItem wi = E.items[it];
         FitState* stp = E.state + wi.fit;
         if (threadIdx.x == 0) { sm.flag[0] = stp->run; sm.flag[1] = stp->phase; }
@@ -496,10 +519,10 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) eval_round_kernel(const Engin
         }
         __syncthreads();
         switch (sm.desc.model) {
-            case 0: process_item<MGauss1D, PREC>(sm, E, wi.fit, wi.tile, R); break;
-            case 1: process_item<MDexp, PREC>(sm, E, wi.fit, wi.tile, R); break;
-            case 2: process_item<MGauss2D, PREC>(sm, E, wi.fit, wi.tile, R); break;
-            case 3: process_item<MPoly2, PREC>(sm, E, wi.fit, wi.tile, R); break;
+            case 0: process_item<MGauss1D, PREC>(sm, E, wi.fit, wi.tile, R, t_item); break;
+            case 1: process_item<MDexp, PREC>(sm, E, wi.fit, wi.tile, R, t_item); break;
+            case 2: process_item<MGauss2D, PREC>(sm, E, wi.fit, wi.tile, R, t_item); break;
+            case 3: process_item<MPoly2, PREC>(sm, E, wi.fit, wi.tile, R, t_item); break;
         }
         __syncthreads();
     }
@@ -634,6 +657,56 @@ cudaError_t launch_stage_weights(bool f64, const void* sigma, double* w, int64_t
     else stage_weights_kernel<float><<<blocks, 256, 0, s>>>((const float*)sigma, w, m);
     return cudaGetLastError();
 }
+// ---- calibration data for the autotuner: point i of a fit of `period`
+// points, coordinates from a counter-based hash (splitmix64 finaliser),
+// observations = model at fixed parameters plus a small hashed perturbation.
+// Only the timing of the passes over these data matters.
+__device__ __forceinline__ double hash_unit(uint64_t k) {
+    k += 0x9E3779B97F4A7C15ull;
+    k = (k ^ (k >> 30)) * 0xBF58476D1CE4E5B9ull;
+    k = (k ^ (k >> 27)) * 0x94D049BB133111EBull;
+    k ^= k >> 31;
+    return double(k >> 11) * (1.0 / 9007199254740992.0);
+}
+
+template <typename DT>
+__global__ void synth_fill_kernel(int model, DT* x, DT* x2, DT* y, int64_t total, int64_t period, uint32_t seed) {
+    const double* pt = c_synth_truth[model];
+    double pd[PD];
+    switch (model) {
+        case 0: MGauss1D::prep_plain(pt, pd); break;
+        case 1: MDexp::prep_plain(pt, pd); break;
+        case 2: MGauss2D::prep_plain(pt, pd); break;
+        default: MPoly2::prep_plain(pt, pd); break;
+    }
+    int64_t W = (int64_t)ceil(sqrt((double)period));
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        double u = hash_unit(2 * (uint64_t)i + ((uint64_t)seed << 40));
+        double v = hash_unit(2 * (uint64_t)i + 1 + ((uint64_t)seed << 40));
+        int64_t j = i % period;
+        double X = 0.0, Y = 0.0, h, J[NMAX];
+        switch (model) {
+            case 0: X = -10.0 + 20.0 * u; MGauss1D::eval_plain(pd, X, Y, h, J); break;
+            case 1: X = 50.0 * u; MDexp::eval_plain(pd, X, Y, h, J); break;
+            case 2: X = double(j % W); Y = double(j / W); MGauss2D::eval_plain(pd, X, Y, h, J); break;
+            default: X = -3.0 + 6.0 * u; MPoly2::eval_plain(pd, X, Y, h, J); break;
+        }
+        x[i] = DT(X);
+        if (x2) x2[i] = DT(Y);
+        y[i] = DT(h * (1.0 + 0.01 * (v - 0.5)));
+    }
+}
+
+cudaError_t launch_synth_fill(int model, bool f64, void* x, void* x2, void* y, int64_t total, int64_t period,
+                              uint32_t seed, int blocks, const double* truth, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyToSymbolAsync(c_synth_truth, truth, sizeof(double) * NMAX, sizeof(double) * NMAX * model,
+                                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (f64) synth_fill_kernel<double><<<blocks, 256, 0, s>>>(model, (double*)x, (double*)x2, (double*)y, total, period, seed);
+    else synth_fill_kernel<float><<<blocks, 256, 0, s>>>(model, (float*)x, (float*)x2, (float*)y, total, period, seed);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tr_subproblem(int n, const double* B, const double* g, double Delta, double alpha0,
                                  double* p_out, double* alpha_out, double* lam_out, cudaStream_t s) {
     tr_subproblem_kernel<<<1, 128, 0, s>>>(n, B, g, Delta, alpha0, p_out, alpha_out, lam_out);

@@ -13,6 +13,8 @@ void* kernel_init_slots(int prec);
 int eval_blocks_per_sm(int prec);
 size_t eval_dyn_smem(int prec);
 cudaError_t launch_stage_weights(bool f64, const void* sigma, double* w, int64_t m, int blocks, cudaStream_t s);
+cudaError_t launch_synth_fill(int model, bool f64, void* x, void* x2, void* y, int64_t total, int64_t period,
+                              uint32_t seed, int blocks, const double* truth, cudaStream_t s);
 cudaError_t launch_tr_subproblem(int n, const double* B, const double* g, double Delta, double alpha0,
                                  double* p_out, double* alpha_out, double* lam_out, cudaStream_t s);
 }  // namespace gbfit

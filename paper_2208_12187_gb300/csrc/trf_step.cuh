@@ -19,15 +19,21 @@
 
 namespace gbfit {
 
+// Trace counters are bumped with reductions that return nothing (RED), so
+// that the step never waits on an L2 round trip for its own bookkeeping.
+__device__ __forceinline__ void trace_bump(unsigned long long* trace, int phase, unsigned long long v) {
+    atomicAdd(trace + phase, v);
+}
+
 __device__ __forceinline__ void trace_add(FitState* st, int phase, long long& t) {
     long long now = clock64();
-    if (threadIdx.x == 0) st->trace[phase] += (unsigned long long)(now - t);
+    if (threadIdx.x == 0) trace_bump(st->trace, phase, (unsigned long long)(now - t));
     t = now;
 }
 
 __device__ __forceinline__ void trace_add_arr(unsigned long long* trace, int phase, long long& t) {
     long long now = clock64();
-    if (threadIdx.x == 0) trace[phase] += (unsigned long long)(now - t);
+    if (threadIdx.x == 0) trace_bump(trace, phase, (unsigned long long)(now - t));
     t = now;
 }
 
@@ -243,7 +249,7 @@ __device__ int eig_fast(int n, const double* Ah, const double* Vwarm, TrfSmem& S
         sweeps = jacobi32(n, S.Af, S.Af2, S.Rf, S.Rf2, 20, &Ares, &Rres);
         if (Rres != S.Rf)
             for (int e = l; e < 64; e += 32) S.Rf[e] = Rres[e];
-        if (trace && t == 0) trace[TR_E_SWEEPS] += sweeps;
+        if (trace && t == 0) trace_bump(trace, TR_E_SWEEPS, sweeps);
     }
     __syncthreads();
     if (trace) trace_add_arr(trace, TR_E_J32, tc);
@@ -295,7 +301,7 @@ __device__ int eig_fast(int n, const double* Ah, const double* Vwarm, TrfSmem& S
         mm8(n, S.V0, false, S.W, S.A, S.H);             // A = V X
         if (t < 64) S.V0[t] += S.A[t];
         __syncthreads();
-        if (trace && t == 0) trace[TR_E_REFINES] += 1;
+        if (trace && t == 0) trace_bump(trace, TR_E_REFINES, 1);
         if (!S.si[7]) break;
     }
     if (t < 64) S.V[t] = S.V0[t];
@@ -510,7 +516,8 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
         write_result(d, st, res, status, S);
         trace_add(st, TR_FINISH, tclk);
         if (t == 0) { st->run = RS_DONE; st->fit_status = status; atomicSub(running, 1); }
-        if (t < 24) res->trace[t] = double(st->trace[t]);
+        __syncthreads();
+        if (t < 24) res->trace[t] = double(__ldcg(st->trace + t));
         return;
     }
 
@@ -559,7 +566,7 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
         }
         if (l == 0) {
             S.si[SI_GN] = (ok && inside) ? 1 : 0;
-            if (ok && inside) st->trace[TR_N_GN] += 1;
+            if (ok && inside) trace_bump(st->trace, TR_N_GN, 1);
         }
     }
     __syncthreads();
@@ -572,7 +579,7 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
         int sw = eig_fast(n, S.Ah, st->has_basis ? st->V : nullptr, S, st->trace);
         if (t < 64) st->V[t] = S.V[t];
         if (t < 8) st->lam[t] = S.vec[VLAM][t];
-        if (t == 0) { st->has_basis = 1; st->factor_valid = 1; st->jacobi_sweeps = sw; st->trace[TR_N_EIG] += 1; }
+        if (t == 0) { st->has_basis = 1; st->factor_valid = 1; st->jacobi_sweeps = sw; trace_bump(st->trace, TR_N_EIG, 1); }
     } else {
         if (t < 64) S.V[t] = st->V[t];
         if (t < 8) S.vec[VLAM][t] = st->lam[t];
@@ -700,8 +707,8 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             st->njev = S.si[SI_NJEV]; st->predicted = -qval;
             st->step_norm = w_norm; st->s_norm = s_norm; st->xtol_thr = d.xtol * (d.xtol + x_norm);
             st->phase = PH_TRIAL; st->last_kind = kind; st->alg2_iters = a2it;
-            st->trace[TR_N_ALG2IT] += a2it;
-            st->trace[TR_N_BOUNDED] += (kind != 0);
+            trace_bump(st->trace, TR_N_ALG2IT, a2it);
+            trace_bump(st->trace, TR_N_BOUNDED, kind != 0);
         }
         __syncwarp();
     }

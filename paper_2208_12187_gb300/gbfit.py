@@ -32,7 +32,7 @@ EXPORTS = ["gbfit_version", "gbfit_last_error", "gbfit_default_options", "gbfit_
            "gbfit_curve_fit", "gbfit_curve_fit_batch", "gbfit_evaluate", "gbfit_tr_subproblem",
            "gbfit_stats_reset", "gbfit_stats_get", "gbfit_set_profiling", "gbfit_evaluate_noalloc",
            "gbfit_server_create", "gbfit_server_submit", "gbfit_server_step", "gbfit_server_poll",
-           "gbfit_server_destroy"]
+           "gbfit_server_destroy", "gbfit_tune_get", "gbfit_tune_set", "gbfit_tune_shape", "gbfit_autotune"]
 
 
 class GbfitError(RuntimeError):
@@ -45,8 +45,15 @@ class Options(ctypes.Structure):
     _fields_ = [("ftol", ctypes.c_double), ("xtol", ctypes.c_double), ("gtol", ctypes.c_double),
                 ("max_nfev", ctypes.c_int), ("x_scale_jac", ctypes.c_int),
                 ("x_scale", ctypes.POINTER(ctypes.c_double)), ("absolute_sigma", ctypes.c_int),
-                ("precision", ctypes.c_int), ("tile_points", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("precision", ctypes.c_int), ("tile_points", ctypes.c_int), ("group_tiles", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
+
+TUNE_BUCKETS = 32
+
+
+class TuneTable(ctypes.Structure):
+    _fields_ = [("tile_points", ctypes.c_int32 * TUNE_BUCKETS * 2 * 4),
+                ("group_tiles", ctypes.c_int32 * TUNE_BUCKETS * 2 * 4)]
 
 
 class Stats(ctypes.Structure):
@@ -57,7 +64,7 @@ class Stats(ctypes.Structure):
 
 PHASES = ["tile", "combine", "logic", "eigen", "comb_fence", "step", "prep", "finish", "comb_group", "comb_final",
           "eig_warm", "eig_j32", "eig_ns", "eig_rr", "j32_sweeps", "refine_passes", "gn_path", "n_gn", "n_eig",
-          "n_alg2_iters", "n_bounded_nonfull", "spare1", "spare2", "spare3"]
+          "n_alg2_iters", "n_bounded_nonfull", "pre_tile", "tile_loop", "spare3"]
 
 
 class ServerConfig(ctypes.Structure):
@@ -113,6 +120,10 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.gbfit_server_step.argtypes = [ctypes.c_void_p, IP, IP]
     lib.gbfit_server_poll.argtypes = [ctypes.c_void_p, ctypes.POINTER(ResultRec), I, IP]
     lib.gbfit_server_destroy.argtypes = [ctypes.c_void_p]
+    lib.gbfit_tune_get.argtypes = [ctypes.POINTER(TuneTable)]
+    lib.gbfit_tune_set.argtypes = [ctypes.POINTER(TuneTable)]
+    lib.gbfit_tune_shape.argtypes = [I, I, I64, IP, IP]
+    lib.gbfit_autotune.argtypes = [I, I, I64, I64, ctypes.POINTER(TuneTable), P]
     lib.gbfit_set_profiling.argtypes = [I]
     for name in EXPORTS:
         getattr(lib, name)
@@ -163,7 +174,7 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
 
 
-def _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points):
+def _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles=0):
     o = Options()
     load().gbfit_default_options(ctypes.byref(o))
     o.ftol, o.xtol, o.gtol = ftol, xtol, gtol
@@ -179,6 +190,7 @@ def _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, 
     o.absolute_sigma = int(bool(absolute_sigma))
     o.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision] if isinstance(precision, str) else int(precision)
     o.tile_points = int(tile_points)
+    o.group_tiles = int(group_tiles)
     return o, keep
 
 
@@ -190,7 +202,7 @@ def _bounds(n, lb, ub):
 
 def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None, ub=None,
               grid_wh=None, ftol=1e-8, xtol=1e-8, gtol=1e-8, max_nfev=None, x_scale=1.0,
-              absolute_sigma=False, precision="mixed", tile_points=0, stream=None) -> dict:
+              absolute_sigma=False, precision="mixed", tile_points=0, group_tiles=0, stream=None) -> dict:
     """Fit `model` by the GPU trust-region-reflective method (gbfit_curve_fit).
 
     xdata: [m] (1D models), [2, m] (2D explicit coordinates) or None with
@@ -214,7 +226,7 @@ def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None
         gw = None
     p0a = np.ascontiguousarray(np.asarray(p0, dtype=np.float64))
     lbv, ubv = _bounds(n, lb, ub)
-    opt, okeep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points)
+    opt, okeep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles)
     popt = np.zeros(n)
     pcov = np.zeros(n * n)
     cost = ctypes.c_double()
@@ -230,8 +242,9 @@ def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None
 
 def curve_fit_batch(model: int, offsets, xdata, ydata, p0, sigma=None, lb=None, ub=None,
                     ftol=1e-8, xtol=1e-8, gtol=1e-8, max_nfev=None, x_scale=1.0,
-                    absolute_sigma=False, precision="mixed", tile_points=0, stream=None) -> dict:
-    """Many independent fits over concatenated data (gbfit_curve_fit_batch)."""
+                    absolute_sigma=False, precision="mixed", tile_points=0, group_tiles=0, stream=None) -> dict:
+    """Many independent fits over concatenated data (gbfit_curve_fit_batch).
+    tile_points / group_tiles 0: each fit's shape from the tile table."""
     lib = load()
     n = N_PARAMS[model]
     off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
@@ -243,7 +256,7 @@ def curve_fit_batch(model: int, offsets, xdata, ydata, p0, sigma=None, lb=None, 
     p0a = np.ascontiguousarray(np.asarray(p0, dtype=np.float64).reshape(nf, n))
     lba = None if lb is None else np.ascontiguousarray(np.broadcast_to(np.asarray(lb, np.float64), (nf, n)))
     uba = None if ub is None else np.ascontiguousarray(np.broadcast_to(np.asarray(ub, np.float64), (nf, n)))
-    opt, okeep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points)
+    opt, okeep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles)
     popt = np.zeros((nf, n))
     pcov = np.zeros((nf, n, n))
     cost = np.zeros(nf)
@@ -348,6 +361,42 @@ def evaluate_noalloc(model: int, xdata, ydata, p, sigma=None, grid_wh=None, prec
                                     _dptr(out), _stream_ptr(stream))
     _check(rc)
     return out[:nt], out[nt:nt + n], float(out[nt + n])
+
+
+def _prec_code(precision):
+    return {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision] if isinstance(precision, str) else int(precision)
+
+
+def tune_get() -> dict:
+    """The installed tile table: {"tile_points": int32[4, 2, 32], "group_tiles": ...}
+    indexed [model][precision][floor(log2 m)]."""
+    t = TuneTable()
+    _check(load().gbfit_tune_get(ctypes.byref(t)))
+    return {"tile_points": np.ctypeslib.as_array(t.tile_points).copy(),
+            "group_tiles": np.ctypeslib.as_array(t.group_tiles).copy()}
+
+
+def tune_set(table: dict):
+    t = TuneTable()
+    np.ctypeslib.as_array(t.tile_points)[...] = np.asarray(table["tile_points"], dtype=np.int32)
+    np.ctypeslib.as_array(t.group_tiles)[...] = np.asarray(table["group_tiles"], dtype=np.int32)
+    _check(load().gbfit_tune_set(ctypes.byref(t)))
+
+
+def tune_shape(model: int, precision, m: int):
+    """(tile_points, group_tiles) a batched or served fit of m points gets."""
+    tp, gt = ctypes.c_int(), ctypes.c_int()
+    _check(load().gbfit_tune_shape(model, _prec_code(precision), int(m), ctypes.byref(tp), ctypes.byref(gt)))
+    return tp.value, gt.value
+
+
+def autotune(model: int, precision="mixed", m_max: int = 1 << 22, points_per_run: int = 0, stream=None) -> dict:
+    """Time candidate tile shapes per size bucket and install the fastest (gbfit_autotune)."""
+    t = TuneTable()
+    _check(load().gbfit_autotune(model, _prec_code(precision), int(m_max), int(points_per_run), ctypes.byref(t),
+                                 _stream_ptr(stream)))
+    return {"tile_points": np.ctypeslib.as_array(t.tile_points).copy(),
+            "group_tiles": np.ctypeslib.as_array(t.group_tiles).copy()}
 
 
 class Server:

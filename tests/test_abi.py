@@ -74,3 +74,29 @@ def test_too_few_points_rejected(lib):
     with pytest.raises(gbfit.GbfitError) as e:
         gbfit.curve_fit(gbfit.MODEL_GAUSS1D, np.zeros(0), np.zeros(0), [1, 0, 1, 0])
     assert e.value.code == gbfit.E_INVALID_ARG
+
+
+def test_tune_table_host_api():
+    """Tile table: defaults, lookup by log2 bucket, one tile for small fits, validation."""
+    saved = gbfit.tune_get()
+    tp = saved["tile_points"]
+    assert tp.shape == (4, 2, gbfit.TUNE_BUCKETS)
+    assert gbfit.tune_shape(gbfit.MODEL_DEXP, "mixed", 1 << 20) == (int(tp[1, 1, 20]), int(saved["group_tiles"][1, 1, 20]))
+    assert gbfit.tune_shape(gbfit.MODEL_DEXP, "mixed", 1000)[0] == 1024          # a fit smaller than its tile: one tile
+    bad = {k: v.copy() for k, v in saved.items()}
+    bad["tile_points"][0, 0, 5] = 1000                                            # not a multiple of 256
+    with pytest.raises(gbfit.GbfitError) as e:
+        gbfit.tune_set(bad)
+    assert e.value.code == gbfit.E_INVALID_ARG
+    assert np.array_equal(gbfit.tune_get()["tile_points"], tp)                    # unchanged after a refusal
+    new = {k: v.copy() for k, v in saved.items()}
+    new["tile_points"][2, 1, :] = 4096
+    new["group_tiles"][2, 1, :] = 8
+    try:
+        gbfit.tune_set(new)
+        assert gbfit.tune_shape(gbfit.MODEL_GAUSS2D, "mixed", 1 << 22) == (4096, 8)
+        assert gbfit.tune_shape(gbfit.MODEL_GAUSS2D, "mixed", 3000) == (3072, 8)
+    finally:
+        gbfit.tune_set(saved)
+    with pytest.raises(gbfit.GbfitError):
+        gbfit.tune_shape(9, "mixed", 100)

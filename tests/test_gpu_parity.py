@@ -239,7 +239,9 @@ def test_batch_matches_alone_and_oracle():
                                 precision="fp64", **TOL)
     for k in (0, 7, 23, 47):
         pr = bt.fit(k)
-        alone = gbfit.curve_fit(pr.model, dev(pr.x), dev(pr.y), pr.p0, lb=pr.lb, ub=pr.ub, precision="fp64", **TOL)
+        tp, gt = gbfit.tune_shape(pr.model, "fp64", pr.m)                # the shape the batch gave this fit
+        alone = gbfit.curve_fit(pr.model, dev(pr.x), dev(pr.y), pr.p0, lb=pr.lb, ub=pr.ub, precision="fp64",
+                                tile_points=tp, group_tiles=gt, **TOL)
         np.testing.assert_array_equal(out["popt"][k], alone["popt"])     # bit-identical in the mix
         ref = trf.curve_fit_problem(pr, **TOL)
         assert out["nfev"][k] == ref["nfev"]
@@ -256,6 +258,27 @@ def test_batch_mixed_matches_oracle():
         errs.append(relerr(out["popt"][k], ref["popt"]))
     assert np.median(errs) <= 1e-6
     assert np.all(out["status"] >= 0)
+
+
+def test_autotune_installs_valid_shapes_and_fits_still_match():
+    saved = gbfit.tune_get()
+    try:
+        tab = gbfit.autotune(gbfit.MODEL_DEXP, "mixed", m_max=1 << 15, points_per_run=1 << 20)
+        tp = tab["tile_points"][gbfit.MODEL_DEXP][gbfit.PREC_MIXED]
+        gt = tab["group_tiles"][gbfit.MODEL_DEXP][gbfit.PREC_MIXED]
+        assert np.all(tp % 256 == 0) and np.all(tp >= 256) and np.all((gt >= 1) & (gt <= 1024))
+        # buckets above m_max and other models / precisions are untouched
+        assert np.array_equal(tp[15:], saved["tile_points"][gbfit.MODEL_DEXP][gbfit.PREC_MIXED][15:])
+        assert np.array_equal(tab["tile_points"][gbfit.MODEL_GAUSS1D], saved["tile_points"][gbfit.MODEL_GAUSS1D])
+        assert gbfit.tune_shape(gbfit.MODEL_DEXP, "mixed", 3 << 13) == (min(int(tp[14]), 3 << 13), int(gt[14]))
+        bt = synth.dexp_batch(16, seed=13, m_lo=1000, m_hi=30_000, dtype=np.float32)
+        out = gbfit.curve_fit_batch(bt.model, bt.offsets, dev(bt.x, torch.float32), dev(bt.y, torch.float32), bt.p0,
+                                    lb=bt.lb, ub=bt.ub, precision="mixed", **TOL)
+        errs = [relerr(out["popt"][k], trf.curve_fit_problem(bt.fit(k), **TOL)["popt"]) for k in range(bt.nfits)]
+        assert np.median(errs) <= 1e-6
+    finally:
+        gbfit.tune_set(saved)
+    assert np.array_equal(gbfit.tune_get()["tile_points"], saved["tile_points"])
 
 
 # ------------------------------------------------------------------ edge cases

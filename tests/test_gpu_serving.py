@@ -3,7 +3,8 @@
 A stream of requests of three models and many sizes is served through a
 small pool (forcing queueing) and few slots; more requests arrive while
 others are running.  Each result must equal, bit for bit, the same fit run
-alone through gbfit_curve_fit (a fit's tiling depends only on its own m),
+alone through gbfit_curve_fit with the same reduction shape (a served fit's
+shape depends only on its own m, through the tile table),
 and match the FP64 oracle (plain: 1e-8, mixed: 1e-6 relative on popt).
 """
 import numpy as np
@@ -75,9 +76,11 @@ def test_served_equals_alone_and_oracle(precision, dtype, rel):
         assert r["status"] == 0 and r["fit_status"] in (1, 2, 3, 4)
         assert r["t_submit"] <= r["t_admit"] <= r["t_done"]
         x = None if pr.layout == synth.LAYOUT_GRID else torch.as_tensor(pr.x).cuda()
+        tp, gt = gbfit.tune_shape(pr.model, precision, pr.m)     # the shape the server gave this fit
         alone = gbfit.curve_fit(pr.model, x, torch.as_tensor(pr.y).cuda(), pr.p0,
                                 sigma=None if pr.sigma is None else torch.as_tensor(pr.sigma).cuda(),
-                                lb=pr.lb, ub=pr.ub, grid_wh=pr.grid_wh, precision=precision, **TOL)
+                                lb=pr.lb, ub=pr.ub, grid_wh=pr.grid_wh, precision=precision,
+                                tile_points=tp, group_tiles=gt, **TOL)
         np.testing.assert_array_equal(r["popt"], alone["popt"])
         assert r["nfev"] == alone["nfev"]
         ref = trf.curve_fit_problem(pr, **TOL)
