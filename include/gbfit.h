@@ -326,11 +326,12 @@ typedef struct gbfit_stats {
     int64_t calls;            /* gbfit_curve_fit / _batch / _evaluate calls            */
     int64_t fits;             /* fits completed                                        */
     int64_t kernel_launches;  /* kernels the library executed (graph nodes included)   */
-    int64_t graph_rounds;     /* WHILE-body trips of the iteration graph               */
+    int64_t graph_rounds;     /* rounds of the persistent loop kernel (one evaluation of
+                                 every running fit each)                              */
     int64_t passes;           /* data passes = sum over fits of nfev                   */
     double point_passes;      /* sum over fits of m * nfev                             */
-    double eval_ms;           /* profiling on: summed CUDA-event time of evaluation launches */
-    int64_t eval_launches;    /* profiling on: evaluation launches timed               */
+    double eval_ms;           /* profiling on: summed CUDA-event time of loop-kernel launches */
+    int64_t eval_launches;    /* profiling on: loop-kernel launches timed              */
     double phase_cycles[24];  /* summed over fits and iterations (SM cycles unless noted):
                                  0 own tile, 1 combine, 2 accept/terminate logic,
                                  3 n x n eigen-decomposition, 4 combine: store, fence and
@@ -343,6 +344,8 @@ typedef struct gbfit_stats {
                                  decompositions (count), 19 Algorithm 2 iterations
                                  (count), 20 bounded non-full steps (count), 21 item start to
                                  tile start, 22 tile loop (of 0), 23 spare */
+    double host_ms;           /* host wall time inside the run of fits (job set-up, launch,
+                                 wait for the device, result copy)                    */
 } gbfit_stats;
 
 /* Zero the counters. */

@@ -1,16 +1,14 @@
-// Host side of libgbfit: argument checking, device workspace, the cached
-// iteration graph and the extern "C" entry points declared in gbfit.h.
+// Host side of libgbfit: argument checking, device workspace and the
+// extern "C" entry points declared in gbfit.h.
 //
-// One fit or a batch of fits runs as ONE graph launch:
-//   init_fits_kernel (pass constants at p0)
-//   WHILE (any fit running && rounds < cap) {
-//       eval_round_kernel x UNROLL      (one TRF iteration of every running fit each)
-//       round_end_kernel                (sets the WHILE condition)
-//   }
-// followed by one device-to-host copy of the per-fit results.  Several
-// iterations per WHILE trip amortise the conditional node (~5 us per trip on
-// GB300 against ~0.6 us per chained kernel node); an iteration launched after
-// a fit has finished costs that fit nothing but an early exit.
+// One fit or a batch of fits runs as ONE cooperative launch of the
+// persistent loop kernel (fit_loop_kernel): pass constants at p0, then
+// rounds (one TRF iteration of every running fit each) separated by a
+// grid-wide barrier, until no fit runs or the round cap is reached.  One
+// host-to-device copy of the job image before it, one device-to-host copy of
+// the per-fit results after it.  On GB300 a kernel boundary plus a graph
+// WHILE trip cost several microseconds per iteration; the barrier costs
+// about one.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -27,7 +25,6 @@ using namespace gbfit;
 
 namespace {
 
-constexpr int UNROLL = 4;
 constexpr int TILE_MIN = 2048, TILE_MAX = 16384, TILE_SPLIT = 304;
 
 thread_local std::string g_err;
@@ -71,7 +68,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Byte layout of one call's job buffer: what the host uploads ([0, res_hdr))
 // and what it reads back ([res_hdr, end)) are each one contiguous copy.
 struct JobLayout {
-    size_t eng, desc, state, items, gcnt, fcnt, res_hdr, res, end;
+    size_t eng, desc, state, items, gcnt, fcnt, smcnt, res_hdr, res, end;
     JobLayout(size_t nf, size_t ntiles, size_t ngroups) {
         size_t o = 0;
         eng = o;     o += align256(sizeof(Engine));
@@ -80,6 +77,7 @@ struct JobLayout {
         items = o;   o += align256(ntiles * sizeof(WorkItem));
         gcnt = o;    o += align256(ngroups * sizeof(int));
         fcnt = o;    o += align256(nf * sizeof(int));
+        smcnt = o;   o += align256(SM_IDS * sizeof(int));
         res_hdr = o; o += 256;
         res = o;     o += align256(nf * sizeof(FitResult));
         end = o;
@@ -98,9 +96,14 @@ struct Ctx {
     double* small = nullptr;      // subproblem scratch
     // pinned host staging
     char* hbuf = nullptr; size_t hcap = 0;
-    // graphs per precision
-    cudaGraph_t graph[2] = {nullptr, nullptr};
-    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    // one-node graphs holding the cooperative loop launch, per precision (a
+    // graph launch costs the host less than a direct cooperative launch);
+    // bound to the job buffer's address
+    cudaGraphExec_t loop_exec[2] = {nullptr, nullptr};
+    void drop_graphs() {
+        for (int p = 0; p < 2; ++p)
+            if (loop_exec[p]) { cudaGraphExecDestroy(loop_exec[p]); loop_exec[p] = nullptr; }
+    }
 
     Engine* eng_dev() const { return (Engine*)job; }
     Engine engine(const JobLayout& L) const {
@@ -114,17 +117,11 @@ struct Ctx {
         E.items = (WorkItem*)(job + L.items);
         E.group_cnt = (int*)(job + L.gcnt);
         E.fit_cnt = (int*)(job + L.fcnt);
+        E.sm_cnt = (int*)(job + L.smcnt);
         E.tile_part = tile_part; E.tile_part_d = tile_part_d; E.group_part = group_part;
         E.n_items = &ed->sc[0]; E.running = &ed->sc[1]; E.rounds = &ed->sc[2];
         E.max_rounds = &ed->sc[3]; E.nfits_dev = &ed->sc[4];
         return E;
-    }
-    void drop_graphs() {
-        for (int p = 0; p < 2; ++p) {
-            if (exec[p]) cudaGraphExecDestroy(exec[p]);
-            if (graph[p]) cudaGraphDestroy(graph[p]);
-            exec[p] = nullptr; graph[p] = nullptr;
-        }
     }
     int pinned(size_t need) {
         if (need <= hcap) return GBFIT_OK;
@@ -171,63 +168,38 @@ int ensure(Ctx* c, const JobLayout& L, size_t ntiles, size_t ngroups) {
     if ((rc = grow_dev(c->tile_part, c->cap_tp, ntiles * KMAX, scratch_changed))) return rc;
     if ((rc = grow_dev(c->tile_part_d, c->cap_tpd, ntiles * KMAX, scratch_changed))) return rc;
     if ((rc = grow_dev(c->group_part, c->cap_gp, ngroups * KMAX, scratch_changed))) return rc;
-    if (job_changed) c->drop_graphs();   // kernels are bound to the job buffer's address
+    if (job_changed) c->drop_graphs();
     return GBFIT_OK;
 }
 
-template <int P>
-int build_graph(Ctx* c) {
-    if (c->exec[P]) return GBFIT_OK;
-    cudaGraph_t g;
-    CUDA_TRY(cudaGraphCreate(&g, 0));
-    Engine* E = c->eng_dev();
-    cudaGraphNode_t n_init;
-    {
-        void* args[] = {&E};
+// The cooperative loop launch (pass constants at p0, then rounds) as a
+// cached one-node graph.
+int loop_graph(Ctx* c, int prec, cudaGraphExec_t* out) {
+    if (!c->loop_exec[prec]) {
+        cudaGraph_t g;
+        CUDA_TRY(cudaGraphCreate(&g, 0));
+        Engine* Ed = c->eng_dev();
+        int do_init = 1;
+        void* args[] = {&Ed, &do_init};
         cudaKernelNodeParams kp = {};
-        kp.func = kernel_init_fits(P);
-        kp.gridDim = dim3(256);
-        kp.blockDim = dim3(32);
-        kp.kernelParams = args;
-        CUDA_TRY(cudaGraphAddKernelNode(&n_init, g, nullptr, 0, &kp));
-    }
-    cudaGraphConditionalHandle h;
-    CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t n_cond;
-    CUDA_TRY(cudaGraphAddNode(&n_cond, g, &n_init, nullptr, 1, &cp));
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    cudaGraphNode_t prev = nullptr;
-    for (int u = 0; u < UNROLL; ++u) {
-        void* args[] = {&E};
-        cudaKernelNodeParams kp = {};
-        kp.func = kernel_eval_round(P);
-        kp.gridDim = dim3(c->grid_p[P]);
+        kp.func = kernel_fit_loop(prec);
+        kp.gridDim = dim3(c->grid_p[prec]);
         kp.blockDim = dim3(EVAL_THREADS);
-        kp.sharedMemBytes = (unsigned)eval_dyn_smem(P);
+        kp.sharedMemBytes = (unsigned)eval_dyn_smem(prec);
         kp.kernelParams = args;
-        cudaGraphNode_t nn;
-        CUDA_TRY(cudaGraphAddKernelNode(&nn, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
-        prev = nn;
+        cudaGraphNode_t node;
+        cudaError_t e = cudaGraphAddKernelNode(&node, g, nullptr, 0, &kp);
+        cudaLaunchAttributeValue v;
+        memset(&v, 0, sizeof v);
+        v.cooperative = 1;
+        if (e == cudaSuccess) e = cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributeCooperative, &v);
+        cudaGraphExec_t ex = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(GBFIT_E_CUDA, "loop graph: %s", cudaGetErrorString(e));
+        c->loop_exec[prec] = ex;
     }
-    {
-        void* args[] = {&E, &h};
-        cudaKernelNodeParams kp = {};
-        kp.func = kernel_round_end();
-        kp.gridDim = dim3(1);
-        kp.blockDim = dim3(1);
-        kp.kernelParams = args;
-        cudaGraphNode_t nn;
-        CUDA_TRY(cudaGraphAddKernelNode(&nn, body, &prev, 1, &kp));
-    }
-    cudaGraphExec_t ex;
-    CUDA_TRY(cudaGraphInstantiate(&ex, g, 0));
-    c->graph[P] = g;
-    c->exec[P] = ex;
+    *out = c->loop_exec[prec];
     return GBFIT_OK;
 }
 
@@ -328,6 +300,7 @@ gbfit_options defaults() {
 // job buffer, one graph launch, one device-to-host copy of the results.
 int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::vector<double>>& p0s,
              std::vector<FitResult>& hr, cudaStream_t s, int* rounds_out) {
+    const auto t_host0 = std::chrono::steady_clock::now();
     size_t nf = hd.size();
     size_t ntiles = 0, ngroups = 0;
     int max_nfev = 1;
@@ -341,8 +314,6 @@ int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::
     JobLayout L(nf, ntiles, ngroups);
     int rc;
     if ((rc = ensure(c, L, ntiles, ngroups))) return rc;
-    if (prec == PREC_MIXED) { if ((rc = build_graph<PREC_MIXED>(c))) return rc; }
-    else { if ((rc = build_graph<PREC_FP64>(c))) return rc; }
     if ((rc = c->pinned(L.end))) return rc;
     char* hb = c->hbuf;
     memset(hb, 0, L.res_hdr);
@@ -350,7 +321,7 @@ int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::
     E.sc[0] = (int)ntiles;
     E.sc[1] = (int)nf;
     E.sc[2] = 0;
-    E.sc[3] = (max_nfev + 2) / UNROLL + 3;
+    E.sc[3] = max_nfev + 4;             // rounds = evaluations of a fit, plus slack
     E.sc[4] = (int)nf;
     memcpy(hb + L.eng, &E, sizeof E);
     memcpy(hb + L.desc, hd.data(), nf * sizeof(FitDesc));
@@ -365,58 +336,47 @@ int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::
         for (int t = 0; t < hd[f].n_tiles; ++t) hi[k++] = WorkItem{(int)f, t};
     }
     CUDA_TRY(cudaMemcpyAsync(c->job, hb, L.res_hdr, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(c->job + L.res_hdr, 0, 4 * sizeof(int), s));   // out[]: running, rounds, abort
     double eval_ms = 0.0;
-    int64_t eval_launches = 0, launches = 0;
-    if (g_profiling) {
-        // measurement mode: same kernels, host-launched, each evaluation timed with events
-        Engine* Ed = c->eng_dev();
-        void* a_eng[] = {&Ed};
-        CUDA_TRY(cudaLaunchKernel(kernel_init_fits(prec), dim3(256), dim3(32), a_eng, 0, s));
-        launches += 1;
-        cudaEvent_t e0, e1;
-        CUDA_TRY(cudaEventCreate(&e0));
-        CUDA_TRY(cudaEventCreate(&e1));
-        int* run_h = (int*)(hb + L.res_hdr);
-        int cap = (max_nfev + 2) + 4;
-        for (int r = 0; r < cap; ++r) {
+    int64_t eval_launches = 0;
+    {
+        cudaGraphExec_t ex;
+        if ((rc = loop_graph(c, prec, &ex))) return rc;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (g_profiling) {
+            CUDA_TRY(cudaEventCreate(&e0));
+            CUDA_TRY(cudaEventCreate(&e1));
             CUDA_TRY(cudaEventRecord(e0, s));
-            CUDA_TRY(cudaLaunchKernel(kernel_eval_round(prec), dim3(c->grid_p[prec]), dim3(EVAL_THREADS), a_eng,
-                                      eval_dyn_smem(prec), s));
+        }
+        CUDA_TRY(cudaGraphLaunch(ex, s));
+        if (g_profiling) {
             CUDA_TRY(cudaEventRecord(e1, s));
-            CUDA_TRY(cudaMemcpyAsync(run_h, &Ed->sc[1], sizeof(int), cudaMemcpyDeviceToHost, s));
-            CUDA_TRY(cudaStreamSynchronize(s));
+            CUDA_TRY(cudaEventSynchronize(e1));
             float ms = 0.f;
             CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            eval_ms += ms;
-            eval_launches += 1;
-            launches += 1;
-            if (*run_h == 0) break;
+            eval_ms = ms;
+            eval_launches = 1;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        CUDA_TRY(cudaMemcpyAsync(c->job + L.res_hdr, &Ed->sc[1], 2 * sizeof(int), cudaMemcpyDeviceToDevice, s));
-    } else {
-        CUDA_TRY(cudaGraphLaunch(c->exec[prec], s));
     }
     CUDA_TRY(cudaMemcpyAsync(hb + L.res_hdr, c->job + L.res_hdr, L.end - L.res_hdr, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     const int* outsc = (const int*)(hb + L.res_hdr);
     int running = outsc[0], rounds = outsc[1];
+    if (outsc[2]) return fail(GBFIT_E_TIMEOUT, "a round barrier of the loop kernel timed out");
     hr.resize(nf);
     memcpy(hr.data(), hb + L.res, nf * sizeof(FitResult));
     if (rounds_out) *rounds_out = rounds;
     {
         std::lock_guard<std::mutex> g(g_stats_mu);
         g_stats.calls += 1;
+        g_stats.host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count();
         g_stats.fits += (int64_t)nf;
-        if (g_profiling) {
-            g_stats.kernel_launches += launches;
-            g_stats.eval_ms += eval_ms;
-            g_stats.eval_launches += eval_launches;
-        } else {
-            g_stats.kernel_launches += 1 + (int64_t)rounds * (UNROLL + 1);
-            g_stats.graph_rounds += rounds;
-        }
+        g_stats.kernel_launches += 1;
+        g_stats.graph_rounds += rounds;
+        g_stats.eval_ms += eval_ms;
+        g_stats.eval_launches += eval_launches;
         for (size_t f = 0; f < nf; ++f) {
             for (int k = 0; k < 24; ++k) g_stats.phase_cycles[k] += hr[f].trace[k];
             g_stats.passes += hr[f].nfev;
@@ -1172,6 +1132,7 @@ int gbfit_server_create(const gbfit_server_config* cfg_in, gbfit_server** out) {
     E.items = (WorkItem*)(job + s->L->items);
     E.group_cnt = (int*)(job + s->L->gcnt);
     E.fit_cnt = (int*)(job + s->L->fcnt);
+    E.sm_cnt = (int*)(job + s->L->smcnt);
     E.tile_part = s->tile_part; E.tile_part_d = s->tile_part_d; E.group_part = s->group_part;
     E.n_items = &Ed->sc[0]; E.running = &Ed->sc[1]; E.rounds = &Ed->sc[2];
     E.max_rounds = &Ed->sc[3]; E.nfits_dev = &Ed->sc[4];
@@ -1355,17 +1316,23 @@ int gbfit_server_step(gbfit_server* s, int* n_active, int* n_queued) {
         }
     if (active > 0) {
         CUDA_TRY(cudaMemcpyAsync(s->job + s->L->items, hi, ni * sizeof(WorkItem), cudaMemcpyHostToDevice, s->stream));
-        int sc2[2] = {(int)ni, active};
-        memcpy(s->hbuf + s->L->end + (size_t)s->max_slots * 4, sc2, sizeof sc2);
-        CUDA_TRY(cudaMemcpyAsync(&Ed->sc[0], s->hbuf + s->L->end + (size_t)s->max_slots * 4, sizeof sc2,
-                                 cudaMemcpyHostToDevice, s->stream));
-        void* a_eval[] = {&Ed};
-        for (int r = 0; r < s->rounds; ++r)
-            CUDA_TRY(cudaLaunchKernel(kernel_eval_round(s->prec), dim3(s->grid), dim3(EVAL_THREADS), a_eval,
-                                      eval_dyn_smem(s->prec), s->stream));
+        // loop scalars: items, running, rounds done, round cap, fits, barrier (count, generation, control)
+        int sc8[8] = {(int)ni, active, 0, s->rounds, s->max_slots, 0, 0, 0};
+        int* hsc = (int*)(s->hbuf + s->L->end + (size_t)s->max_slots * 4);
+        memcpy(hsc, sc8, sizeof sc8);
+        CUDA_TRY(cudaMemcpyAsync(&Ed->sc[0], hsc, sizeof sc8, cudaMemcpyHostToDevice, s->stream));
+        CUDA_TRY(cudaMemsetAsync(s->job + s->L->res_hdr, 0, 4 * sizeof(int), s->stream));
+        int do_init = 0;
+        void* a_loop[] = {&Ed, &do_init};
+        CUDA_TRY(cudaLaunchCooperativeKernel(kernel_fit_loop(s->prec), dim3(s->grid), dim3(EVAL_THREADS), a_loop,
+                                             eval_dyn_smem(s->prec), s->stream));
+        int* hout = hsc + 8;
+        CUDA_TRY(cudaMemcpyAsync(hout, s->job + s->L->res_hdr, 3 * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        if (hout[2]) return fail(GBFIT_E_TIMEOUT, "a round barrier of the loop kernel timed out");
         {
             std::lock_guard<std::mutex> gs(g_stats_mu);
-            g_stats.kernel_launches += s->rounds + (admitted.empty() ? 0 : 1);
+            g_stats.kernel_launches += 1 + (admitted.empty() ? 0 : 1);
         }
     }
     if ((rc = server_retire(s))) return rc;

@@ -48,7 +48,7 @@ struct FitDesc {
 };
 
 // Mutable per-fit state, kept on the device across iterations.
-struct FitState {
+struct alignas(16) FitState {
     // --- read by the evaluation pass ---
     int run;               // RunState
     int phase;             // Phase of the pending evaluation
@@ -67,10 +67,14 @@ struct FitState {
     double lam[NMAX];
     double predicted, step_norm, s_norm, xtol_thr;
     double s_h[NMAX];      // scaled step of the pending trial
+    double pad1;           // (the prefix above is a whole number of 16-byte words)
+    // --- (the step reads everything above from a shared-memory copy) ---
     unsigned long long trace[24];  // SM cycles / counts per phase of the step, summed over iterations
 };
 
 struct WorkItem { int fit; int tile; };
+
+constexpr int SM_IDS = 1024;                     // bound on %nsmid for the per-SM CTA counters
 
 struct FitResult;
 
@@ -93,6 +97,7 @@ struct Engine {
     int* rounds;           // graph bodies executed since launch
     int* max_rounds;       // cap on graph bodies (guarantees the WHILE loop ends)
     int* nfits_dev;        // number of fits of the current launch
+    int* sm_cnt;           // [SM_IDS] CTAs per SM of the loop kernel (zero between launches)
     int sc[8];             // the scalars the pointers above refer to
 };
 

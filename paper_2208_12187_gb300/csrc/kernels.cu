@@ -9,8 +9,9 @@
 //       trust-region step for it (trf_step), which prepares the next
 //       evaluation point.  No CTA waits for another: the hand-off is an
 //       atomic arrival counter (last arriver continues).
-//   round_end_kernel  sets the CUDA-graph WHILE condition (any fit running
-//       and under the round cap).
+//   fit_loop_kernel<PREC>  the same rounds in one cooperative launch,
+//       separated by a grid-wide barrier (bounded waits), until no fit runs
+//       or the round cap is reached.
 //   stage_weights_kernel  w = 1/sigma in FP64 for the plain path.
 //   tr_subproblem_kernel  one subproblem solve (test entry point).
 #include <cstdint>
@@ -315,6 +316,7 @@ __device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0,
 
 // ------------------------------------------------------------------ shared memory of the round kernel
 struct RoundSmem {
+    Engine eng;                        // the launch's engine record (kept out of registers)
     unsigned long long mbar[NST];
     int ring_fail;
     FitDesc desc;
@@ -322,6 +324,7 @@ struct RoundSmem {
     float pf[PF];
     double pd[PD];
     int flag[4];
+    int ctl;
     union {
         float redf[8 * KMAX];
         double redd[8 * KMAX];
@@ -443,6 +446,7 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
     }
     __syncthreads();
     if (!sm.flag[2]) return;
+    if (d.n_groups == 1) prefetch_state(stp, sm.trf);      // this CTA runs the step
     if (threadIdx.x == 0) sm.t_fence = clock64();
     double* gout = E.group_part + (d.group_base + group) * KMAX;
     if (PREC == PREC_MIXED)
@@ -463,6 +467,7 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
         }
         __syncthreads();
         if (!sm.flag[3]) return;
+        prefetch_state(stp, sm.trf);
         combine_rows<double>(E.group_part + d.group_base * KMAX, d.n_groups, K, sm.comb, sm.trf.tot);
     }
     if (threadIdx.x == 0) {
@@ -481,12 +486,16 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
     __syncthreads();
 }
 
+// Copy the engine record into shared memory (round_setup's barrier publishes it).
+__device__ __forceinline__ void stage_engine(RoundSmem& sm, const Engine* Ep) {
+    const int* src = (const int*)Ep;
+    int* dst = (int*)&sm.eng;
+    for (int k = threadIdx.x; k < (int)(sizeof(Engine) / 4); k += blockDim.x) dst[k] = src[k];
+}
+
+// Ring barriers and flags at the start of a round kernel.
 template <int PREC>
-__global__ void __launch_bounds__(EVAL_THREADS, 2) eval_round_kernel(const Engine* __restrict__ Ep) {
-    __shared__ RoundSmem sm;
-    extern __shared__ __align__(128) float ring_buf[];
-    const Engine E = *Ep;
-    RingState R;
+__device__ __forceinline__ void round_setup(RoundSmem& sm, float* ring_buf, RingState& R) {
     R.bar = sm.mbar;
     R.buf = ring_buf;
     R.seq = 0;
@@ -497,12 +506,17 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) eval_round_kernel(const Engin
             sm.ring_fail = 0;
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
-        __syncthreads();
     } else if (threadIdx.x == 0) {
         sm.ring_fail = 0;
     }
+    __syncthreads();
+}
+
+// One round: this CTA's share of the work items (grid-stride from `first`).
+template <int PREC>
+__device__ __forceinline__ void run_items(RoundSmem& sm, const Engine& E, RingState& R, int first) {
     int n_items = *E.n_items;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    for (int it = first; it < n_items; it += gridDim.x) {
         long long t_item = clock64();
         WorkItem wi = E.items[it];
         FitState* stp = E.state + wi.fit;
@@ -526,6 +540,146 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) eval_round_kernel(const Engin
         }
         __syncthreads();
     }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(EVAL_THREADS, 2) eval_round_kernel(const Engine* __restrict__ Ep) {
+    __shared__ RoundSmem sm;
+    extern __shared__ __align__(128) float ring_buf[];
+    stage_engine(sm, Ep);
+    RingState R;
+    round_setup<PREC>(sm, ring_buf, R);
+    run_items<PREC>(sm, sm.eng, R, blockIdx.x);
+}
+
+// ---- grid-wide round barrier of the persistent loop.  The loop kernel is
+// launched cooperatively (every CTA resident), so a CTA that waits here
+// waits only for CTAs that are running.  Waits are bounded in time; past
+// the bound the CTA raises the abort bit and every CTA leaves the loop.
+constexpr unsigned long long ROUND_WAIT_LIMIT_NS = 10ull * 1000 * 1000 * 1000;
+enum { CTL_STOP = 1, CTL_ABORT = 2 };
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// All CTAs arrive; the last one closes the round (rounds, running, stop
+// decision; count_round false for the set-up barrier) and opens the next.
+// Returns the control word (CTL_*) for every thread of every CTA.
+__device__ int grid_round_end(Engine* Ed, const Engine& E, int* ctl_smem, bool count_round) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned* cnt = (unsigned*)&Ed->sc[5];
+        unsigned* gen = (unsigned*)&Ed->sc[6];
+        volatile int* ctl = &Ed->sc[7];
+        unsigned g = ld_acquire_u32(gen);
+        unsigned old;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(cnt) : "memory");
+        int c;
+        if (old == gridDim.x - 1) {
+            *(volatile unsigned*)cnt = 0;
+            c = *ctl & CTL_ABORT;
+            if (count_round) {
+                int r = ++(*E.rounds);
+                int run = *(volatile int*)E.running;
+                E.out[0] = run;
+                E.out[1] = r;
+                if (run <= 0 || r >= *E.max_rounds) c |= CTL_STOP;
+            }
+            *ctl = c;
+            st_release_u32(gen, g + 1);
+        } else {
+            unsigned long long t0 = global_ns();
+            while (ld_acquire_u32(gen) == g) {
+                __nanosleep(128);
+                if (global_ns() - t0 > ROUND_WAIT_LIMIT_NS) {
+                    atomicOr((int*)ctl, CTL_ABORT);
+                    break;
+                }
+            }
+            c = *ctl;
+        }
+        if (c & CTL_ABORT) atomicOr(E.out + 2, 1);
+        *ctl_smem = c;
+    }
+    __syncthreads();
+    return *ctl_smem;
+}
+
+// Persistent form of the iteration: pass constants at p0 (do_init), then
+// rounds of run_items separated by the grid barrier until no fit runs or the
+// round cap is reached.  One cooperative launch replaces a graph of
+// per-round kernels.
+template <int PREC>
+__global__ void __launch_bounds__(EVAL_THREADS, 2) fit_loop_kernel(const Engine* __restrict__ Ep, int do_init) {
+    __shared__ RoundSmem sm;
+    extern __shared__ __align__(128) float ring_buf[];
+    stage_engine(sm, Ep);
+    const Engine& E = sm.eng;
+    Engine* Ed = const_cast<Engine*>(Ep);
+    RingState R;
+    round_setup<PREC>(sm, ring_buf, R);
+    // This CTA's rank among all CTAs ordered by (slot on its SM, SM id), so
+    // that work items 0, 1, 2, ... land on distinct SMs before any SM gets a
+    // second one (a fit with fewer tiles than SMs gets one SM per tile).
+    if (threadIdx.x == 0) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        sm.flag[0] = (int)smid;
+        sm.flag[1] = atomicAdd(E.sm_cnt + (smid < SM_IDS ? smid : SM_IDS - 1), 1);
+    }
+    if (grid_round_end(Ed, E, &sm.ctl, false)) return;
+    int first;
+    {
+        const int smid = sm.flag[0], slot = sm.flag[1];
+        unsigned nsm;
+        asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsm));
+        nsm = nsm < SM_IDS ? nsm : SM_IDS;
+        int part = 0;
+        for (int k = threadIdx.x; k < (int)nsm; k += blockDim.x) {
+            int c = __ldcg(E.sm_cnt + k);
+            part += min(c, slot) + ((k < smid && c > slot) ? 1 : 0);
+        }
+        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+        __syncthreads();                                  // flag[0..1] read by every thread
+        if (threadIdx.x == 0) sm.flag[2] = 0;
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) atomicAdd(&sm.flag[2], part);
+        __syncthreads();
+        first = sm.flag[2];
+    }
+    if (do_init) {
+        int nf = *E.nfits_dev;
+        for (int f = blockIdx.x; f < nf; f += gridDim.x) {
+            if (threadIdx.x < 32) {
+                const FitDesc& d = E.desc[f];
+                FitState* st = E.state + f;
+                int l = threadIdx.x;
+                if (l < 8) { sm.trf.vec[VX][l] = (l < d.n) ? st->x[l] : 0.0; sm.trf.vec[VXT][l] = sm.trf.vec[VX][l]; }
+                __syncwarp();
+                prep_pass<PREC>(d, st, sm.trf);
+            }
+            __syncthreads();
+        }
+        if (grid_round_end(Ed, E, &sm.ctl, false)) return;
+    }
+    while (true) {
+        run_items<PREC>(sm, E, R, first);
+        if (grid_round_end(Ed, E, &sm.ctl, true)) break;
+    }
+    // every CTA has read the counters (before the first round): rank 0 clears them for the next launch
+    if (first == 0)
+        for (int k = threadIdx.x; k < SM_IDS; k += blockDim.x) E.sm_cnt[k] = 0;
 }
 
 // Pass constants for the first evaluation (at p0): base = trial = p0.
@@ -561,16 +715,6 @@ __global__ void init_slots_kernel(const Engine* __restrict__ Ep, const int* __re
         prep_pass<PREC>(d, st, S);
         __syncwarp();
     }
-}
-
-__global__ void round_end_kernel(const Engine* __restrict__ Ep, cudaGraphConditionalHandle h) {
-    const Engine E = *Ep;
-    int r = ++(*E.rounds);
-    int run = *E.running;
-    E.out[0] = run;
-    E.out[1] = r;
-    unsigned keep = (run > 0 && r < *E.max_rounds) ? 1u : 0u;
-    cudaGraphSetConditional(h, keep);
 }
 
 // w = 1/sigma (FP64) for the plain path.
@@ -636,21 +780,31 @@ void* kernel_eval_round(int prec) {
 void* kernel_init_fits(int prec) {
     return prec == PREC_MIXED ? (void*)init_fits_kernel<PREC_MIXED> : (void*)init_fits_kernel<PREC_FP64>;
 }
-void* kernel_round_end() { return (void*)round_end_kernel; }
+void* kernel_fit_loop(int prec) {
+    return prec == PREC_MIXED ? (void*)fit_loop_kernel<PREC_MIXED> : (void*)fit_loop_kernel<PREC_FP64>;
+}
 void* kernel_init_slots(int prec) {
     return prec == PREC_MIXED ? (void*)init_slots_kernel<PREC_MIXED> : (void*)init_slots_kernel<PREC_FP64>;
 }
 size_t eval_dyn_smem(int prec) { return prec == PREC_MIXED ? RING_BYTES : 0; }
+// Resident CTAs per SM of the round kernels (the loop kernel's cooperative
+// grid is this times the SM count, so both kernels must fit it).
 int eval_blocks_per_sm(int prec) {
-    int b = 0;
+    int b = 0, b2 = 0;
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(eval_round_kernel<PREC_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RING_BYTES);
+        cudaFuncSetAttribute(fit_loop_kernel<PREC_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RING_BYTES);
         attr_set = true;
     }
-    if (prec == PREC_MIXED) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, eval_round_kernel<PREC_MIXED>, EVAL_THREADS, RING_BYTES);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, eval_round_kernel<PREC_FP64>, EVAL_THREADS, 0);
-    return b;
+    if (prec == PREC_MIXED) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, eval_round_kernel<PREC_MIXED>, EVAL_THREADS, RING_BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fit_loop_kernel<PREC_MIXED>, EVAL_THREADS, RING_BYTES);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, eval_round_kernel<PREC_FP64>, EVAL_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fit_loop_kernel<PREC_FP64>, EVAL_THREADS, 0);
+    }
+    return b < b2 ? b : b2;
 }
 cudaError_t launch_stage_weights(bool f64, const void* sigma, double* w, int64_t m, int blocks, cudaStream_t s) {
     if (f64) stage_weights_kernel<double><<<blocks, 256, 0, s>>>((const double*)sigma, w, m);

@@ -8,8 +8,8 @@ namespace gbfit {
 // the host engine never names a template kernel of another translation unit).
 void* kernel_eval_round(int prec);
 void* kernel_init_fits(int prec);
-void* kernel_round_end();
 void* kernel_init_slots(int prec);
+void* kernel_fit_loop(int prec);
 int eval_blocks_per_sm(int prec);
 size_t eval_dyn_smem(int prec);
 cudaError_t launch_stage_weights(bool f64, const void* sigma, double* w, int64_t m, int blocks, cudaStream_t s);

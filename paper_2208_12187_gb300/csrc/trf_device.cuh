@@ -57,6 +57,7 @@ enum TracePhase { TR_TILE = 0, TR_COMBINE, TR_LOGIC, TR_EIGEN, TR_C_FENCE, TR_ST
 
 // Shared-memory workspace of the warp that runs one fit's step.
 struct TrfSmem {
+    FitState stc;     // copy of the fit's state up to its trace (read-only view for the step)
     double tot[KMAX];
     double B[64];     // Gram at x, full symmetric 8x8
     double A[64];     // Jacobi work matrix

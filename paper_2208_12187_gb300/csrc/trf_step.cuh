@@ -311,6 +311,7 @@ __device__ int eig_fast(int n, const double* Ah, const double* Vwarm, TrfSmem& S
 }
 
 // Coleman-Li scaling at the current x, g (lane values; lanes >= n: v = dv = 0).
+// st: the fit's state (the step passes its shared-memory copy).
 __device__ __forceinline__ void cl_scaling(const FitDesc& d, const FitState* st, const TrfSmem& S, int n,
                                            double& v, double& dv, double& sx) {
     int l = threadIdx.x & 31;
@@ -404,14 +405,29 @@ __device__ void write_result(const FitDesc& d, FitState* st, FitResult* res, int
     __syncthreads();
 }
 
+// Copy the fit's state (up to its trace counters) into S.stc with all
+// threads of the CTA; L2 loads, since other CTAs wrote it in earlier rounds.
+// Issued before the final combine so that the loads overlap it; the
+// combine's closing barrier publishes the copy.
+constexpr int STATE_WORDS = (int)(offsetof(FitState, trace) / sizeof(uint4));
+static_assert(offsetof(FitState, trace) % sizeof(uint4) == 0, "FitState prefix must be whole 16-byte words");
+__device__ __forceinline__ void prefetch_state(const FitState* st, TrfSmem& S) {
+    const uint4* src = reinterpret_cast<const uint4*>(st);
+    uint4* dst = reinterpret_cast<uint4*>(&S.stc);
+    for (int k = threadIdx.x; k < STATE_WORDS; k += blockDim.x) dst[k] = __ldcg(src + k);
+}
+
 // Scalar slots of TrfSmem::sd / si shared between the phases.
 enum { SD_F = 0, SD_DELTA, SD_ALPHA, SD_GNORM };
-enum { SI_STATUS = 0, SI_NFEV, SI_NJEV, SI_FACTOR, SI_GN };
+enum { SI_STATUS = 0, SI_NFEV, SI_NJEV, SI_FACTOR, SI_GN, SI_REJECTED };
 
 // One trust-region iteration for one fit.  S.tot holds the combined sums of
-// the evaluation at st->xt that just finished.
+// the evaluation at st->xt that just finished; S.stc the state as it was
+// before this step (prefetch_state).  State is read from S.stc and written
+// to st (and to S.stc where a later phase of the same step reads it).
 template <int PREC>
 __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem& S, int* running) {
+    const FitState* cst = &S.stc;
     const int n = d.n;
     const int t = threadIdx.x, warp = t >> 5, l = t & 31;
     const int NT = n_tri(n);
@@ -420,12 +436,12 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
     // ================= phase 1 (warp 0): accept / reject, termination tests
     if (warp == 0) {
         if (l < n) {
-            S.vec[VX][l] = st->x[l];
-            S.vec[VXT][l] = st->xt[l];
-            S.vec[VG][l] = st->g[l];
+            S.vec[VX][l] = cst->x[l];
+            S.vec[VXT][l] = cst->xt[l];
+            S.vec[VG][l] = cst->g[l];
         }
-        const bool init = st->phase == PH_INIT;
-        const double* srcB = init ? S.tot : st->B;   // packed upper triangle
+        const bool init = cst->phase == PH_INIT;
+        const double* srcB = init ? S.tot : cst->B;   // packed upper triangle
         for (int e = l; e < 64; e += 32) {
             int i = e >> 3, j = e & 7;
             double b = 0.0;
@@ -435,30 +451,31 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
         __syncwarp();
         const double f2n = S.tot[NT + n];
         int status = FS_RUNNING;
-        double f = st->f, Delta = st->Delta, alpha = st->alpha;
-        int nfev = st->nfev, njev = st->njev, factor_valid = st->factor_valid;
-        bool take = false;
+        double f = cst->f, Delta = cst->Delta, alpha = cst->alpha;
+        int nfev = cst->nfev, njev = cst->njev, factor_valid = cst->factor_valid;
+        bool take = false, rejected = false;
         if (init) {
             take = true;
             f = 0.5 * f2n;
             nfev = 1; njev = 1;
             bool fin = (l >= NT + n + 1 || isfinite(S.tot[l])) && (l + 32 >= NT + n + 1 || isfinite(S.tot[l + 32]));
             fin = __all_sync(FULL, fin);
-            if (st->bad_data) status = FS_INVALID_DATA;
+            if (cst->bad_data) status = FS_INVALID_DATA;
             else if (!fin) status = FS_NUMERICAL;
         } else {
             nfev += 1;
             double f_new = 0.5 * f2n;
             double actual = (PREC == PREC_MIXED) ? -0.5 * S.tot[NT + n + 1] : f - f_new;
-            double pred = st->predicted;
+            double pred = cst->predicted;
             double gamma = (isfinite(f_new) && isfinite(actual) && pred > 0.0) ? actual * rcp64(pred) : -INFINITY;
             bool accepted;
             double Dn;
             if (gamma > 0.75) { accepted = true; Dn = 2.0 * Delta; }
             else if (gamma >= 0.25 && gamma <= 0.75) { accepted = true; Dn = Delta; }
-            else { accepted = false; Dn = 0.25 * st->s_norm; }
+            else { accepted = false; Dn = 0.25 * cst->s_norm; }
+            rejected = !accepted;
             bool ftol_ok = accepted && actual < d.ftol * f;
-            bool xtol_ok = st->step_norm < st->xtol_thr;
+            bool xtol_ok = cst->step_norm < cst->xtol_thr;
             if (accepted) { take = true; f = f_new; njev += 1; factor_valid = 0; }
             Delta = Dn;
             if (ftol_ok && xtol_ok) status = FS_FTOL_XTOL;
@@ -476,15 +493,17 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             __syncwarp();
             if (d.jac_scale && status == FS_RUNNING && l < n) {
                 double c = sqrt(S.B[l * 8 + l]);
-                if (!init) c = fmax(c, st->scale_inv[l]);
-                st->scale_inv[l] = (c == 0.0) ? 1.0 : c;
+                if (!init) c = fmax(c, cst->scale_inv[l]);
+                c = (c == 0.0) ? 1.0 : c;
+                S.stc.scale_inv[l] = c;
+                st->scale_inv[l] = c;
             }
             __syncwarp();
         }
         double gnorm = 0.0;
         if (status == FS_RUNNING) {
             double v, dv, sx;
-            cl_scaling(d, st, S, n, v, dv, sx);
+            cl_scaling(d, cst, S, n, v, dv, sx);
             if (init) {
                 double xl = (l < n) ? S.vec[VX][l] : 0.0;
                 double dd = (l < n) ? (d.bounded ? sqrt(v) : 1.0) * sx : 1.0;
@@ -502,6 +521,7 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
         if (l == 0) {
             S.sd[SD_F] = f; S.sd[SD_DELTA] = Delta; S.sd[SD_ALPHA] = alpha; S.sd[SD_GNORM] = gnorm;
             S.si[SI_STATUS] = status; S.si[SI_NFEV] = nfev; S.si[SI_NJEV] = njev; S.si[SI_FACTOR] = factor_valid;
+            S.si[SI_REJECTED] = rejected ? 1 : 0;
             st->factor_valid = factor_valid;   // the eigen cache describes the current B only
         }
     }
@@ -524,7 +544,7 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
     // ================= phase 2 (warp 0): scaled model matrix Ah = D B D + diag(C)
     if (warp == 0) {
         double v, dv, sx;
-        cl_scaling(d, st, S, n, v, dv, sx);
+        cl_scaling(d, cst, S, n, v, dv, sx);
         double g = (l < n) ? S.vec[VG][l] : 0.0;
         double dl = (l < n) ? (d.bounded ? sqrt(v) : 1.0) * sx : 0.0;
         if (l < 8) {
@@ -549,7 +569,10 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
     // equilibrated matrix), and lambda_min >= min_diag / cond must stay far
     // above the rank cutoff lambda_max 8 n eps64 (lambda_max <= n here), so
     // that the pseudo-inverse of the eigen path would drop nothing.
-    if (warp == 0) {
+    // After a rejected trial B_hat and g_hat are unchanged and Delta has
+    // shrunk below the rejected step (Algorithm 3), so the Gauss-Newton step
+    // (inside the old region or not) cannot be inside the new one: skip it.
+    if (warp == 0 && !S.si[SI_REJECTED]) {
         float sc = 1.0f, mind = 0.0f;
         bool ok = chol32(n, S.Ah, S.Lf, sc, mind);
         ok = __all_sync(FULL, ok);
@@ -568,6 +591,8 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             S.si[SI_GN] = (ok && inside) ? 1 : 0;
             if (ok && inside) trace_bump(st->trace, TR_N_GN, 1);
         }
+    } else if (warp == 0 && threadIdx.x == 0) {
+        S.si[SI_GN] = 0;
     }
     __syncthreads();
     trace_add(st, TR_GN, tclk);
@@ -576,13 +601,13 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
     if (S.si[SI_GN]) {
         // not needed
     } else if (!S.si[SI_FACTOR]) {
-        int sw = eig_fast(n, S.Ah, st->has_basis ? st->V : nullptr, S, st->trace);
+        int sw = eig_fast(n, S.Ah, cst->has_basis ? cst->V : nullptr, S, st->trace);
         if (t < 64) st->V[t] = S.V[t];
         if (t < 8) st->lam[t] = S.vec[VLAM][t];
         if (t == 0) { st->has_basis = 1; st->factor_valid = 1; st->jacobi_sweeps = sw; trace_bump(st->trace, TR_N_EIG, 1); }
     } else {
-        if (t < 64) S.V[t] = st->V[t];
-        if (t < 8) S.vec[VLAM][t] = st->lam[t];
+        if (t < 64) S.V[t] = cst->V[t];
+        if (t < 8) S.vec[VLAM][t] = cst->lam[t];
     }
     __syncthreads();
     trace_add(st, TR_EIGEN, tclk);

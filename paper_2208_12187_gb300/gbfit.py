@@ -60,7 +60,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int64), ("fits", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("graph_rounds", ctypes.c_int64), ("passes", ctypes.c_int64), ("point_passes", ctypes.c_double),
                 ("eval_ms", ctypes.c_double), ("eval_launches", ctypes.c_int64),
-                ("phase_cycles", ctypes.c_double * 24)]
+                ("phase_cycles", ctypes.c_double * 24), ("host_ms", ctypes.c_double)]
 
 PHASES = ["tile", "combine", "logic", "eigen", "comb_fence", "step", "prep", "finish", "comb_group", "comb_final",
           "eig_warm", "eig_j32", "eig_ns", "eig_rr", "j32_sweeps", "refine_passes", "gn_path", "n_gn", "n_eig",
@@ -89,6 +89,7 @@ class ResultRec(ctypes.Structure):
 
 
 _LIB = None
+_DEFAULT_OPT = None
 
 
 def load(path: Optional[str] = None) -> ctypes.CDLL:
@@ -107,8 +108,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.gbfit_last_error.restype = ctypes.c_char_p
     lib.gbfit_default_options.argtypes = [ctypes.POINTER(Options)]
     lib.gbfit_model_info.argtypes = [I, IP, IP]
-    lib.gbfit_curve_fit.argtypes = [I, P, I64, I, ctypes.POINTER(ctypes.c_int64), P, P, I, DP, DP, DP,
-                                    ctypes.POINTER(Options), DP, DP, DP, IP, IP, P]
+    # the single-fit call takes raw addresses (lowest per-call marshalling cost)
+    lib.gbfit_curve_fit.argtypes = [I, P, I64, I, P, P, P, I, P, P, P, P, P, P, P, P, P, P]
     lib.gbfit_curve_fit_batch.argtypes = [I, I, ctypes.POINTER(ctypes.c_int64), P, I, P, P, I, DP, DP, DP,
                                           ctypes.POINTER(Options), DP, DP, DP, IP, IP, P]
     lib.gbfit_evaluate.argtypes = [I, P, I64, I, ctypes.POINTER(ctypes.c_int64), P, P, I, DP, I, I, DP, P]
@@ -128,6 +129,10 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     for name in EXPORTS:
         getattr(lib, name)
     _LIB = lib
+    global _DEFAULT_OPT
+    o = Options()
+    lib.gbfit_default_options(ctypes.byref(o))
+    _DEFAULT_OPT = bytes(o)
     return lib
 
 
@@ -140,26 +145,38 @@ def _dptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+_NP_CODE = {np.dtype(np.float32): F32, np.dtype(np.float64): F64}
+_TORCH = None      # (torch.Tensor, {dtype: code}) once torch is importable
+
+
+def _torch_types():
+    global _TORCH
+    if _TORCH is None:
+        try:
+            import torch
+            _TORCH = (torch.Tensor, {torch.float32: F32, torch.float64: F64})
+        except ImportError:
+            _TORCH = (None, {})
+    return _TORCH
+
+
 def _array_info(a):
-    """(pointer, dtype code, keepalive) for a torch tensor or NumPy array."""
+    """(address, dtype code, keepalive) for a torch tensor or NumPy array."""
     if a is None:
         return None, None, None
-    try:
-        import torch
-        if isinstance(a, torch.Tensor):
-            if not a.is_contiguous():
-                a = a.contiguous()
-            code = {torch.float32: F32, torch.float64: F64}.get(a.dtype)
-            if code is None:
-                raise TypeError("data tensors must be float32 or float64")
-            return ctypes.c_void_p(a.data_ptr()), code, a
-    except ImportError:
-        pass
+    tt, tcodes = _TORCH or _torch_types()
+    if tt is not None and isinstance(a, tt):
+        if not a.is_contiguous():
+            a = a.contiguous()
+        code = tcodes.get(a.dtype)
+        if code is None:
+            raise TypeError("data tensors must be float32 or float64")
+        return a.data_ptr(), code, a
     a = np.ascontiguousarray(a)
-    code = {np.dtype(np.float32): F32, np.dtype(np.float64): F64}.get(a.dtype)
+    code = _NP_CODE.get(a.dtype)
     if code is None:
         raise TypeError("data arrays must be float32 or float64")
-    return ctypes.c_void_p(a.ctypes.data), code, a
+    return a.ctypes.data, code, a
 
 
 def _stream_ptr(stream):
@@ -175,12 +192,14 @@ def _stream_ptr(stream):
 
 
 def _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles=0):
-    o = Options()
-    load().gbfit_default_options(ctypes.byref(o))
+    load()
+    o = Options.from_buffer_copy(_DEFAULT_OPT)
     o.ftol, o.xtol, o.gtol = ftol, xtol, gtol
     o.max_nfev = int(max_nfev or 0)
     keep = None
-    if isinstance(x_scale, str):
+    if isinstance(x_scale, (int, float)) and x_scale == 1.0:
+        pass
+    elif isinstance(x_scale, str):
         if x_scale != "jac":
             raise ValueError("x_scale must be 'jac' or positive numbers")
         o.x_scale_jac = 1
@@ -188,10 +207,22 @@ def _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, 
         keep = np.ascontiguousarray(np.broadcast_to(np.asarray(x_scale, dtype=np.float64), (n,)))
         o.x_scale = _dptr(keep)
     o.absolute_sigma = int(bool(absolute_sigma))
-    o.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision] if isinstance(precision, str) else int(precision)
+    o.precision = _PREC.get(precision, precision) if isinstance(precision, str) else int(precision)
+    if isinstance(o.precision, str):
+        raise KeyError(precision)
     o.tile_points = int(tile_points)
     o.group_tiles = int(group_tiles)
     return o, keep
+
+
+_PREC = {"fp64": PREC_FP64, "mixed": PREC_MIXED}
+
+
+def _vec(v, n):
+    a = np.asarray(v, dtype=np.float64)
+    if a.shape != (n,):
+        a = np.broadcast_to(a, (n,))
+    return np.ascontiguousarray(a)
 
 
 def _bounds(n, lb, ub):
@@ -209,7 +240,7 @@ def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None
     grid_wh=(W, H) for the implicit pixel grid.  Returns dict(popt, pcov, cost,
     nfev, status).
     """
-    lib = load()
+    lib = _LIB or load()
     n = N_PARAMS[model]
     yp, dt, ykeep = _array_info(ydata)
     xp, xdt, xkeep = _array_info(xdata)
@@ -217,27 +248,28 @@ def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None
     m = int(ykeep.shape[0])
     if xp is not None and xdt != dt or sp is not None and sdt != dt:
         raise TypeError("xdata, ydata and sigma must share one dtype")
+    gw = None
     if grid_wh is not None:
         layout = X_GRID
-        gw = (ctypes.c_int64 * 2)(int(grid_wh[0]), int(grid_wh[1]))
+        gw = np.array([int(grid_wh[0]), int(grid_wh[1])], dtype=np.int64)
         xp = None
     else:
         layout = X_SOA2 if (xkeep is not None and len(xkeep.shape) == 2) else X_VEC
-        gw = None
-    p0a = np.ascontiguousarray(np.asarray(p0, dtype=np.float64))
-    lbv, ubv = _bounds(n, lb, ub)
+    p0a = _vec(p0, n)
+    lbv = None if lb is None else _vec(lb, n)
+    ubv = None if ub is None else _vec(ub, n)
     opt, okeep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles)
-    popt = np.zeros(n)
-    pcov = np.zeros(n * n)
-    cost = ctypes.c_double()
-    nfev = ctypes.c_int()
-    status = ctypes.c_int()
-    rc = lib.gbfit_curve_fit(model, xp, m, layout, gw, yp, sp, dt, _dptr(p0a),
-                             None if lbv is None else _dptr(lbv), None if ubv is None else _dptr(ubv),
-                             ctypes.byref(opt), _dptr(popt), _dptr(pcov), ctypes.byref(cost),
-                             ctypes.byref(nfev), ctypes.byref(status), _stream_ptr(stream))
-    _check(rc)
-    return dict(popt=popt, pcov=pcov.reshape(n, n), cost=cost.value, nfev=nfev.value, status=status.value)
+    out = np.zeros(n + n * n + 1)                  # popt | pcov | cost
+    ints = np.zeros(2, dtype=np.int32)             # nfev | status
+    a = out.ctypes.data
+    rc = lib.gbfit_curve_fit(model, xp, m, layout, None if gw is None else gw.ctypes.data, yp, sp, dt,
+                             p0a.ctypes.data, None if lbv is None else lbv.ctypes.data,
+                             None if ubv is None else ubv.ctypes.data, ctypes.addressof(opt), a, a + 8 * n,
+                             a + 8 * (n + n * n), ints.ctypes.data, ints.ctypes.data + 4, _stream_ptr(stream))
+    if rc != OK:
+        _check(rc)
+    return dict(popt=out[:n], pcov=out[n:n + n * n].reshape(n, n), cost=float(out[-1]), nfev=int(ints[0]),
+                status=int(ints[1]))
 
 
 def curve_fit_batch(model: int, offsets, xdata, ydata, p0, sigma=None, lb=None, ub=None,
