@@ -346,6 +346,8 @@ typedef struct gbfit_stats {
                                  tile start, 22 tile loop (of 0), 23 spare */
     double host_ms;           /* host wall time inside the run of fits (job set-up, launch,
                                  wait for the device, result copy)                    */
+    double loop_busy_ms;      /* loop kernel, summed over CTAs: time in rounds' work    */
+    double loop_wait_ms;      /* loop kernel, summed over CTAs: time at round barriers  */
 } gbfit_stats;
 
 /* Zero the counters. */

@@ -25,7 +25,7 @@ using namespace gbfit;
 
 namespace {
 
-constexpr int TILE_MIN = 2048, TILE_MAX = 16384, TILE_SPLIT = 304;
+constexpr int TILE_MIN = 2048, TILE_MAX = 16384, TILE_SPLIT = 304;   // TILE_SPLIT: grid when none is known
 
 thread_local std::string g_err;
 
@@ -77,7 +77,7 @@ struct JobLayout {
         items = o;   o += align256(ntiles * sizeof(WorkItem));
         gcnt = o;    o += align256(ngroups * sizeof(int));
         fcnt = o;    o += align256(nf * sizeof(int));
-        smcnt = o;   o += align256(SM_IDS * sizeof(int));
+        smcnt = o;   o += align256((SM_IDS + 1) * sizeof(int));
         res_hdr = o; o += 256;
         res = o;     o += align256(nf * sizeof(FitResult));
         end = o;
@@ -210,9 +210,15 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-int choose_tile(int64_t m, int user) {
+// Tile of a single fit spread over a grid of `grid` CTAs: the fewest rounds
+// k of at most TILE_MAX-point tiles per CTA, then tiles of m / (grid k)
+// points, so that every CTA gets k or k - 1 tiles.
+int choose_tile(int64_t m, int user, int grid) {
     if (user > 0) return ((user + EVAL_THREADS - 1) / EVAL_THREADS) * EVAL_THREADS;
-    int64_t t = (m + TILE_SPLIT - 1) / TILE_SPLIT;
+    const int64_t G = grid > 0 ? grid : TILE_SPLIT;
+    int64_t k = (m + G * TILE_MAX - 1) / (G * TILE_MAX);
+    if (k < 1) k = 1;
+    int64_t t = (m + G * k - 1) / (G * k);
     t = ((t + EVAL_THREADS - 1) / EVAL_THREADS) * EVAL_THREADS;
     if (t < TILE_MIN) t = TILE_MIN;
     if (t > TILE_MAX) t = TILE_MAX;
@@ -336,7 +342,7 @@ int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::
         for (int t = 0; t < hd[f].n_tiles; ++t) hi[k++] = WorkItem{(int)f, t};
     }
     CUDA_TRY(cudaMemcpyAsync(c->job, hb, L.res_hdr, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemsetAsync(c->job + L.res_hdr, 0, 4 * sizeof(int), s));   // out[]: running, rounds, abort
+    CUDA_TRY(cudaMemsetAsync(c->job + L.res_hdr, 0, 32, s));   // out[]: running, rounds, abort; busy / wait ns
     double eval_ms = 0.0;
     int64_t eval_launches = 0;
     {
@@ -365,6 +371,7 @@ int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::
     const int* outsc = (const int*)(hb + L.res_hdr);
     int running = outsc[0], rounds = outsc[1];
     if (outsc[2]) return fail(GBFIT_E_TIMEOUT, "a round barrier of the loop kernel timed out");
+    const unsigned long long* acct = (const unsigned long long*)(hb + L.res_hdr) + 2;
     hr.resize(nf);
     memcpy(hr.data(), hb + L.res, nf * sizeof(FitResult));
     if (rounds_out) *rounds_out = rounds;
@@ -377,6 +384,8 @@ int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::
         g_stats.graph_rounds += rounds;
         g_stats.eval_ms += eval_ms;
         g_stats.eval_launches += eval_launches;
+        g_stats.loop_busy_ms += acct[0] * 1e-6;
+        g_stats.loop_wait_ms += acct[1] * 1e-6;
         for (size_t f = 0; f < nf; ++f) {
             for (int k = 0; k < 24; ++k) g_stats.phase_cycles[k] += hr[f].trace[k];
             g_stats.passes += hr[f].nfev;
@@ -417,7 +426,8 @@ int stage_data(Ctx* c, const void* x, size_t xbytes, const void* y, size_t ybyte
 
 // multi: the fit runs beside others (batched or served) and takes its shape
 // from the tile table; otherwise its tiles spread over every SM.
-int fill_desc(FitDesc& d, const FitArgs& a, const gbfit_options& o, bool bounded, int64_t m, bool multi) {
+int fill_desc(FitDesc& d, const FitArgs& a, const gbfit_options& o, bool bounded, int64_t m, bool multi,
+              int grid = 0) {
     memset(&d, 0, sizeof d);
     d.model = a.model; d.n = a.n; d.layout = a.layout; d.dtype = a.dtype;
     d.prec = o.precision; d.bounded = bounded ? 1 : 0; d.jac_scale = o.x_scale_jac ? 1 : 0;
@@ -425,7 +435,7 @@ int fill_desc(FitDesc& d, const FitArgs& a, const gbfit_options& o, bool bounded
     if (multi) {
         multi_shape(a.model, o.precision, m, o.tile_points, o.group_tiles, &d.tile_points, &d.group_tiles);
     } else {
-        d.tile_points = choose_tile(m, o.tile_points);
+        d.tile_points = choose_tile(m, o.tile_points, grid);
         d.group_tiles = o.group_tiles > 0 ? o.group_tiles : GROUP_TILES;
     }
     d.n_tiles = (int)((m + d.tile_points - 1) / d.tile_points);
@@ -520,7 +530,7 @@ static int single_fit(int model_id, const void* xdata, int64_t m, int x_layout, 
     if ((rc = stage_data(c, x_layout == GBFIT_X_GRID ? nullptr : xdata, xbytes, ydata, (size_t)m * es, sigma,
                          (size_t)m * es, s, &sd))) return rc;
     std::vector<FitDesc> hd(1);
-    fill_desc(hd[0], a, o, bounded, m, false);
+    fill_desc(hd[0], a, o, bounded, m, false, c->grid_p[o.precision]);
     const void* x2 = (x_layout == GBFIT_X_SOA2) ? (const char*)sd.x + (size_t)m * es : nullptr;
     if (sigma && o.precision == GBFIT_PREC_FP64) {
         bool changed = false;
@@ -886,7 +896,11 @@ extern "C" int gbfit_evaluate_noalloc(int model_id, const void* xdata, int64_t m
     }
     for (int i = 0; i < n; ++i)
         if (!std::isfinite(p[i])) return fail(GBFIT_E_INVALID_ARG, "p[%d] is not finite", i);
-    const int tp = choose_tile(m, tile_points);
+    int nsm = 0, dev0 = 0;
+    CUDA_TRY(cudaGetDevice(&dev0));
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev0));
+    const int grid_na = nsm * std::max(1, eval_blocks_per_sm(precision));
+    const int tp = choose_tile(m, tile_points, grid_na);
     const int64_t ntiles = (m + tp - 1) / tp;
     if (ntiles > NOALLOC_MAX_TILES)
         return fail(GBFIT_E_INVALID_ARG,
@@ -941,7 +955,7 @@ extern "C" int gbfit_evaluate_noalloc(int model_id, const void* xdata, int64_t m
     o.max_nfev = 1;
     FitArgs a{model_id, n, x_layout, dtype, m, gw, xdata, nullptr, ydata, sigma, p, nullptr, nullptr};
     FitDesc d;
-    fill_desc(d, a, o, false, m, false);
+    fill_desc(d, a, o, false, m, false, grid_na);
     size_t es = dtype == GBFIT_F64 ? 8 : 4;
     d.x = x_layout == GBFIT_X_GRID ? nullptr : xdata;
     d.x2 = (x_layout == GBFIT_X_SOA2) ? (const char*)xdata + (size_t)m * es : nullptr;
@@ -1321,7 +1335,7 @@ int gbfit_server_step(gbfit_server* s, int* n_active, int* n_queued) {
         int* hsc = (int*)(s->hbuf + s->L->end + (size_t)s->max_slots * 4);
         memcpy(hsc, sc8, sizeof sc8);
         CUDA_TRY(cudaMemcpyAsync(&Ed->sc[0], hsc, sizeof sc8, cudaMemcpyHostToDevice, s->stream));
-        CUDA_TRY(cudaMemsetAsync(s->job + s->L->res_hdr, 0, 4 * sizeof(int), s->stream));
+        CUDA_TRY(cudaMemsetAsync(s->job + s->L->res_hdr, 0, 32, s->stream));
         int do_init = 0;
         void* a_loop[] = {&Ed, &do_init};
         CUDA_TRY(cudaLaunchCooperativeKernel(kernel_fit_loop(s->prec), dim3(s->grid), dim3(EVAL_THREADS), a_loop,

@@ -25,9 +25,8 @@ enum Phase { PH_INIT = 0, PH_TRIAL = 1 };
 //   [NT, NT+n)     J'^T r'
 //   NT+n           sum r'^2                        (= 2 f at the evaluated point)
 //   NT+n+1         sum dr (2 r + dr)   mixed only  (= 2 (f' - f), cancellation-free)
-//   NT+n+2         sum r^2             mixed only  (= 2 f at the base point)
 __host__ __device__ constexpr int n_tri(int n) { return n * (n + 1) / 2; }
-__host__ __device__ constexpr int n_acc(int n, int prec) { return n_tri(n) + n + (prec == PREC_MIXED ? 3 : 1); }
+__host__ __device__ constexpr int n_acc(int n, int prec) { return n_tri(n) + n + (prec == PREC_MIXED ? 2 : 1); }
 
 // Immutable description of one fit (uploaded once).
 struct FitDesc {
@@ -83,7 +82,7 @@ struct FitResult;
 // the cached graph stays valid while per-call sizes and scratch change.
 struct Engine {
     FitResult* results;    // [fits]
-    int* out;              // in the result region: [0] running, [1] rounds (copied back)
+    int* out;              // result header: [0] running, [1] rounds, [2] abort; u64 words 2-3: loop busy / wait ns
     FitDesc* desc;
     FitState* state;
     WorkItem* items;
@@ -97,7 +96,8 @@ struct Engine {
     int* rounds;           // graph bodies executed since launch
     int* max_rounds;       // cap on graph bodies (guarantees the WHILE loop ends)
     int* nfits_dev;        // number of fits of the current launch
-    int* sm_cnt;           // [SM_IDS] CTAs per SM of the loop kernel (zero between launches)
+    int* sm_cnt;           // [SM_IDS + 1] CTAs per SM of the loop kernel, then the round's next
+                           // dynamic work item (all zero between launches)
     int sc[8];             // the scalars the pointers above refer to
 };
 

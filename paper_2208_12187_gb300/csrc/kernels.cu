@@ -91,10 +91,10 @@ __device__ __forceinline__ void block_reduce(T (&acc)[K], T* red /*[8][K]*/, T& 
 template <typename T> __device__ __forceinline__ T ldg_t(const void* p, int64_t i) { return __ldg((const T*)p + i); }
 
 struct PointCoord {
-    // incremental pixel coordinates for the implicit grid
-    int64_t X, Y, W;
-    __device__ void init(int64_t i, int64_t w) { W = w; Y = i / w; X = i - Y * w; }
-    __device__ void advance(int64_t step) {
+    // incremental pixel coordinates for the implicit grid (W, H < 2^31)
+    int X, Y, W;
+    __device__ void init(int64_t i, int64_t w) { W = (int)w; Y = (int)(i / w); X = (int)(i - (int64_t)Y * w); }
+    __device__ void advance(int step) {
         X += step;
         if (X >= W) { if (W >= EVAL_THREADS) { X -= W; Y += 1; } else { Y += X / W; X = X % W; } }
     }
@@ -141,7 +141,6 @@ __device__ __forceinline__ void accum_point(const float* pfl, const double* pdl,
         for (int a = 0; a < N; ++a) acc[NT + a] = fmaf(Jw[a], rn, acc[NT + a]);
         acc[NT + N] = fmaf(rn, rn, acc[NT + N]);
         acc[NT + N + 1] = fmaf(dr, fmaf(2.0f, r, dr), acc[NT + N + 1]);
-        acc[NT + N + 2] = fmaf(r, r, acc[NT + N + 2]);
     } else {
         double h, J[N];
         M::eval_plain(pdl, X, Y, h, J);
@@ -157,6 +156,39 @@ __device__ __forceinline__ void accum_point(const float* pfl, const double* pdl,
         for (int a = 0; a < N; ++a) acc[NT + a] = fma(Jw[a], r, acc[NT + a]);
         acc[NT + N] = fma(r, r, acc[NT + N]);
     }
+}
+
+// Two points at once with packed FP32 (1D models, mixed precision).
+template <class M, int WK>
+__device__ __forceinline__ void accum_point2(const float* pfl, float2 X, float2 yv, float2 sv, bool check,
+                                             float2 (&acc)[n_acc(M::N, PREC_MIXED)], int& bad) {
+    constexpr int N = M::N;
+    constexpr int NT = n_tri(N);
+    float2 w = bc(1.0f);
+    if (WK == W_SIGMA) {
+        if (check && !(sv.x > 0.0f && isfinite(sv.x) && sv.y > 0.0f && isfinite(sv.y))) bad = 1;
+        w = make_float2(__fdividef(1.0f, sv.x), __fdividef(1.0f, sv.y));
+    }
+    if (check && !(isfinite(X.x) && isfinite(X.y) && isfinite(yv.x) && isfinite(yv.y))) bad = 1;
+    float2 hb, dh, J[N];
+    M::eval_mixed2(pfl, X, hb, dh, J);
+    float2 r = sub2(hb, yv), dr = dh;
+    if (WK == W_SIGMA) {
+        r = mul2(w, r);
+        dr = mul2(w, dr);
+#pragma unroll
+        for (int a = 0; a < N; ++a) J[a] = mul2(w, J[a]);
+    }
+    float2 rn = add2(r, dr);
+    int idx = 0;
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int b = a; b < N; ++b) { acc[idx] = fma2(J[a], J[b], acc[idx]); ++idx; }
+#pragma unroll
+    for (int a = 0; a < N; ++a) acc[NT + a] = fma2(J[a], rn, acc[NT + a]);
+    acc[NT + N] = fma2(rn, rn, acc[NT + N]);
+    acc[NT + N + 1] = fma2(dr, fma2(bc(2.0f), r, dr), acc[NT + N + 1]);
 }
 
 // Points [i0, i1) with register loads (software-pipelined one point ahead).
@@ -190,14 +222,23 @@ __device__ __forceinline__ void tile_points(const FitDesc& d, const float* pfl, 
 }
 
 // ---- bulk-copy ring (mixed precision, FP32 data): each CTA streams its
-// tile through NST shared-memory stages of CHUNK points per array with
+// tile through NST shared-memory stages of CH points per array with
 // cp.async.bulk, completion tracked by one mbarrier per stage, so that
 // about NST-1 chunks (tens of KB per SM) are in flight while the threads
 // compute from shared memory.
-constexpr int CHUNK = 1024;
 constexpr int NST = 4;
-constexpr int RING_ARRAYS = 4;                       // x, x2, y, sigma at most
-constexpr size_t RING_BYTES = size_t(NST) * RING_ARRAYS * CHUNK * sizeof(float);
+constexpr int STAGE_FLOATS = 4096;                   // 16 KB per stage, shared by the streamed arrays
+constexpr size_t RING_BYTES = size_t(NST) * STAGE_FLOATS * sizeof(float);
+// Arrays a layout streams (x, x2, y, sigma as present) and the chunk (points
+// per stage) that fills a stage with them: 4096 / 2048 / 1024 points.
+template <int LAYOUT, int WK>
+struct RingShape {
+    static constexpr int NA = (LAYOUT == X_GRID ? 0 : LAYOUT == X_SOA2 ? 2 : 1) + 1 + (WK == W_SIGMA ? 1 : 0);
+    static constexpr int CH = NA <= 1 ? 4096 : NA == 2 ? 2048 : 1024;
+    static constexpr int SX = 0, SX2 = 1;                                   // slots (when present)
+    static constexpr int SY = LAYOUT == X_GRID ? 0 : LAYOUT == X_SOA2 ? 2 : 1;
+    static constexpr int SS = SY + 1;
+};
 constexpr long long MBAR_SPIN_LIMIT = 1ll << 22;     // bounded waits (error flag past the limit)
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -223,6 +264,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
     for (long long it = 0; it < MBAR_SPIN_LIMIT; ++it)
         if (mbar_try_wait(bar, parity)) return true;
@@ -239,8 +283,9 @@ __device__ __forceinline__ int arrive_acq_rel(int* ctr) {
 }
 
 struct RingState {
-    unsigned long long* bar;     // [NST] mbarriers
-    float* buf;                  // [NST][RING_ARRAYS][CHUNK]
+    unsigned long long* bar;     // [NST] full barriers (bulk-copy completion)
+    unsigned long long* empty;   // [NST] empty barriers (one arrival per warp when a stage is consumed)
+    float* buf;                  // [NST][STAGE_FLOATS]
     unsigned seq;                // chunks consumed by this CTA so far (same in all threads)
     int* fail;                   // shared flag: a bounded wait gave up
 };
@@ -248,31 +293,42 @@ struct RingState {
 template <class M, int LAYOUT, int WK>
 __device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0, int64_t i1, bool check,
                                  float (&acc)[n_acc(M::N, PREC_MIXED)], int& bad, RingState& R) {
+    using RS = RingShape<LAYOUT, WK>;
+    constexpr int CH = RS::CH;
     const int t = threadIdx.x;
-    // arrays streamed: slot 0 x (or X row), 1 Y row, 2 y, 3 sigma
-    const float* src[RING_ARRAYS] = {LAYOUT == X_GRID ? nullptr : (const float*)d.x,
-                                     LAYOUT == X_SOA2 ? (const float*)d.x2 : nullptr, (const float*)d.y,
-                                     WK == W_SIGMA ? (const float*)d.w : nullptr};
+    // streamed arrays in slot order
+    const float* src[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (LAYOUT != X_GRID) src[RS::SX] = (const float*)d.x;
+    if (LAYOUT == X_SOA2) src[RS::SX2] = (const float*)d.x2;
+    src[RS::SY] = (const float*)d.y;
+    if (WK == W_SIGMA) src[RS::SS] = (const float*)d.w;
     // head up to 16-byte alignment of y; every streamed array must share it
-    int64_t h = (int64_t)(((16 - (reinterpret_cast<uintptr_t>(src[2] + i0) & 15)) & 15) / 4);
+    int64_t h = (int64_t)(((16 - (reinterpret_cast<uintptr_t>(src[RS::SY] + i0) & 15)) & 15) / 4);
     bool aligned = true;
-    for (int a = 0; a < RING_ARRAYS; ++a)
-        if (src[a] && (reinterpret_cast<uintptr_t>(src[a] + i0 + h) & 15)) aligned = false;
+#pragma unroll
+    for (int a = 0; a < RS::NA; ++a)
+        if (reinterpret_cast<uintptr_t>(src[a] + i0 + h) & 15) aligned = false;
     int64_t a0 = i0 + h;
-    if (!aligned || a0 >= i1) { tile_points<M, PREC_MIXED, float, LAYOUT, WK>(d, pfl, nullptr, i0, i1, check, acc, bad); return; }
-    const int nch = (int)((i1 - a0) / CHUNK);
-    const int64_t a1 = a0 + (int64_t)nch * CHUNK;
-    unsigned bytes = 0;
-    for (int a = 0; a < RING_ARRAYS; ++a) bytes += src[a] ? CHUNK * sizeof(float) : 0;
+    if (!aligned || a0 + 4 > i1) { tile_points<M, PREC_MIXED, float, LAYOUT, WK>(d, pfl, nullptr, i0, i1, check, acc, bad); return; }
+    // whole 16-byte words go through the ring (a short last chunk allowed),
+    // at most 3 trailing points through plain loads
+    const int64_t nring = ((i1 - a0) / 4) * 4;
+    const int nch = (int)((nring + CH - 1) / CH);
+    const int64_t a1 = a0 + nring;
+    auto count = [&](int c) { return (int)min((int64_t)CH, nring - (int64_t)c * CH); };
+    // issue chunk c into its stage once every warp has released the stage's
+    // previous chunk (bounded wait; a timeout marks the ring failed)
     auto issue = [&](int c) {
         unsigned g = R.seq + c;
         int s = g % NST;
         unsigned long long* bar = R.bar + s;
+        if (g >= (unsigned)NST && !mbar_wait(R.empty + s, ((g / NST) - 1) & 1)) { *R.fail = 1; return; }
+        const unsigned nb = (unsigned)count(c) * sizeof(float);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(bar, bytes);
-        for (int a = 0; a < RING_ARRAYS; ++a)
-            if (src[a]) bulk_load(R.buf + (s * RING_ARRAYS + a) * CHUNK, src[a] + a0 + (int64_t)c * CHUNK,
-                                  CHUNK * sizeof(float), bar);
+        mbar_expect_tx(bar, nb * RS::NA);
+#pragma unroll
+        for (int a = 0; a < RS::NA; ++a)
+            bulk_load(R.buf + s * STAGE_FLOATS + a * CH, src[a] + a0 + (int64_t)c * CH, nb, bar);
     };
     if (t == 0)
         for (int c = 0; c < nch && c < NST; ++c) issue(c);
@@ -280,36 +336,56 @@ __device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0,
     tile_points<M, PREC_MIXED, float, LAYOUT, WK>(d, pfl, nullptr, i0, a0, check, acc, bad);
     PointCoord pc;
     if (LAYOUT == X_GRID) pc.init(a0 + t, d.grid_w);
+    constexpr bool PK = M::PACKED && LAYOUT == X_VEC;      // two points per thread step
+    constexpr int K = n_acc(M::N, PREC_MIXED);
+    float2 acc2[PK ? K : 1];         // (the head's sums move in, so that acc[] is dead in the loop)
+#pragma unroll
+    for (int k = 0; k < (PK ? K : 1); ++k) acc2[k] = make_float2(PK ? acc[k] : 0.0f, 0.0f);
     for (int c = 0; c < nch; ++c) {
         unsigned g = R.seq + c;
         int s = g % NST;
         if (!mbar_wait(R.bar + s, (g / NST) & 1)) *R.fail = 1;
-        __syncthreads();
         if (*R.fail) break;
-        const float* B = R.buf + s * RING_ARRAYS * CHUNK;
+        const float* B = R.buf + s * STAGE_FLOATS;
+        const int cnt = count(c);
+        if constexpr (PK) {
 #pragma unroll 2
-        for (int k = t; k < CHUNK; k += EVAL_THREADS) {
+            for (int k = 2 * t; k < cnt; k += 2 * EVAL_THREADS) {
+                float2 X = *reinterpret_cast<const float2*>(B + RS::SX * CH + k);
+                float2 yv = *reinterpret_cast<const float2*>(B + RS::SY * CH + k);
+                float2 sv = (WK == W_SIGMA) ? *reinterpret_cast<const float2*>(B + RS::SS * CH + k) : bc(1.0f);
+                accum_point2<M, WK>(pfl, X, yv, sv, check, acc2, bad);
+            }
+        } else
+#pragma unroll 2
+        for (int k = t; k < cnt; k += EVAL_THREADS) {
             float X = 0.0f, Y = 0.0f;
             if (LAYOUT == X_GRID) {
                 X = float(pc.X);
                 Y = float(pc.Y);
                 pc.advance(EVAL_THREADS);
             } else {
-                X = B[0 * CHUNK + k];
-                if (LAYOUT == X_SOA2) Y = B[1 * CHUNK + k];
+                X = B[RS::SX * CH + k];
+                if (LAYOUT == X_SOA2) Y = B[RS::SX2 * CH + k];
             }
-            float yv = B[2 * CHUNK + k];
-            float sv = (WK == W_SIGMA) ? B[3 * CHUNK + k] : 1.0f;
+            float yv = B[RS::SY * CH + k];
+            float sv = (WK == W_SIGMA) ? B[RS::SS * CH + k] : 1.0f;
             accum_point<M, PREC_MIXED, WK>(pfl, nullptr, X, Y, yv, sv, check, acc, bad);
         }
-        __syncthreads();                                   // stage free for reuse
+        __syncwarp();
+        if ((t & 31) == 0) mbar_arrive(R.empty + s);      // this warp is done with the stage
         if (t == 0 && c + NST < nch) issue(c + NST);
     }
+    __syncthreads();
     if (*R.fail) {
         // give copies still in flight a bounded chance to land before leaving
         for (int c = 0; c < nch; ++c) { unsigned g = R.seq + c; mbar_wait(R.bar + (g % NST), (g / NST) & 1); }
     }
     R.seq += nch;
+    if constexpr (PK) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] = acc2[k].x + acc2[k].y;
+    }
     // tail with plain loads
     tile_points<M, PREC_MIXED, float, LAYOUT, WK>(d, pfl, nullptr, a1, i1, check, acc, bad);
 }
@@ -318,6 +394,7 @@ __device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0,
 struct RoundSmem {
     Engine eng;                        // the launch's engine record (kept out of registers)
     unsigned long long mbar[NST];
+    unsigned long long mbar_empty[NST];
     int ring_fail;
     FitDesc desc;
     long long t_mark, t_fence, t_group, t_loop;
@@ -497,12 +574,16 @@ __device__ __forceinline__ void stage_engine(RoundSmem& sm, const Engine* Ep) {
 template <int PREC>
 __device__ __forceinline__ void round_setup(RoundSmem& sm, float* ring_buf, RingState& R) {
     R.bar = sm.mbar;
+    R.empty = sm.mbar_empty;
     R.buf = ring_buf;
     R.seq = 0;
     R.fail = &sm.ring_fail;
     if (PREC == PREC_MIXED) {
         if (threadIdx.x == 0) {
-            for (int s = 0; s < NST; ++s) mbar_init(&sm.mbar[s], 1);
+            for (int s = 0; s < NST; ++s) {
+                mbar_init(&sm.mbar[s], 1);
+                mbar_init(&sm.mbar_empty[s], EVAL_THREADS / 32);
+            }
             sm.ring_fail = 0;
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
@@ -512,17 +593,33 @@ __device__ __forceinline__ void round_setup(RoundSmem& sm, float* ring_buf, Ring
     __syncthreads();
 }
 
-// One round: this CTA's share of the work items (grid-stride from `first`).
+// One round: this CTA's share of the work items.  The first item of every
+// CTA is `first` (items 0 .. grid-1 one per CTA); after that either
+// grid-stride (static) or the next unclaimed item from the round's counter
+// (dynamic: CTAs that finish early take more, so no CTA ends a round far
+// behind the others).  Which CTA processes an item does not change any sum.
 template <int PREC>
-__device__ __forceinline__ void run_items(RoundSmem& sm, const Engine& E, RingState& R, int first) {
+__device__ __forceinline__ void run_items(RoundSmem& sm, const Engine& E, RingState& R, int first,
+                                          int* next_item) {
     int n_items = *E.n_items;
-    for (int it = first; it < n_items; it += gridDim.x) {
+    for (int it = first; it < n_items;) {
         long long t_item = clock64();
         WorkItem wi = E.items[it];
         FitState* stp = E.state + wi.fit;
         if (threadIdx.x == 0) { sm.flag[0] = stp->run; sm.flag[1] = stp->phase; }
         __syncthreads();
-        if (sm.flag[0] != RS_RUNNING) { __syncthreads(); continue; }
+        if (sm.flag[0] != RS_RUNNING) {
+            __syncthreads();
+            if (next_item) {
+                if (threadIdx.x == 0) sm.flag[0] = (int)gridDim.x + atomicAdd(next_item, 1);
+                __syncthreads();
+                it = sm.flag[0];
+                __syncthreads();
+            } else {
+                it += gridDim.x;
+            }
+            continue;
+        }
         // stage desc and pass constants
         {
             const int* src = (const int*)(E.desc + wi.fit);
@@ -538,6 +635,13 @@ __device__ __forceinline__ void run_items(RoundSmem& sm, const Engine& E, RingSt
             case 2: process_item<MGauss2D, PREC>(sm, E, wi.fit, wi.tile, R, t_item); break;
             case 3: process_item<MPoly2, PREC>(sm, E, wi.fit, wi.tile, R, t_item); break;
         }
+        if (next_item) {
+            if (threadIdx.x == 0) sm.flag[0] = (int)gridDim.x + atomicAdd(next_item, 1);
+            __syncthreads();
+            it = sm.flag[0];
+        } else {
+            it += gridDim.x;
+        }
         __syncthreads();
     }
 }
@@ -549,7 +653,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) eval_round_kernel(const Engin
     stage_engine(sm, Ep);
     RingState R;
     round_setup<PREC>(sm, ring_buf, R);
-    run_items<PREC>(sm, sm.eng, R, blockIdx.x);
+    run_items<PREC>(sm, sm.eng, R, blockIdx.x, nullptr);
 }
 
 // ---- grid-wide round barrier of the persistent loop.  The loop kernel is
@@ -590,6 +694,7 @@ __device__ int grid_round_end(Engine* Ed, const Engine& E, int* ctl_smem, bool c
             *(volatile unsigned*)cnt = 0;
             c = *ctl & CTL_ABORT;
             if (count_round) {
+                E.sm_cnt[SM_IDS] = 0;                 // next round's dynamic items start over
                 int r = ++(*E.rounds);
                 int run = *(volatile int*)E.running;
                 E.out[0] = run;
@@ -673,13 +778,23 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) fit_loop_kernel(const Engine*
         }
         if (grid_round_end(Ed, E, &sm.ctl, false)) return;
     }
+    // time accounting of the loop (result header, 64-bit words 2..3):
+    // per-CTA time in rounds' work and time waiting at the barrier
+    unsigned long long* acct = reinterpret_cast<unsigned long long*>(E.out) + 2;
     while (true) {
-        run_items<PREC>(sm, E, R, first);
-        if (grid_round_end(Ed, E, &sm.ctl, true)) break;
+        unsigned long long t0 = global_ns();
+        run_items<PREC>(sm, E, R, first, E.sm_cnt + SM_IDS);
+        unsigned long long t1 = global_ns();
+        int c = grid_round_end(Ed, E, &sm.ctl, true);
+        if (threadIdx.x == 0) {
+            atomicAdd(acct, t1 - t0);
+            atomicAdd(acct + 1, global_ns() - t1);
+        }
+        if (c) break;
     }
     // every CTA has read the counters (before the first round): rank 0 clears them for the next launch
     if (first == 0)
-        for (int k = threadIdx.x; k < SM_IDS; k += blockDim.x) E.sm_cnt[k] = 0;
+        for (int k = threadIdx.x; k <= SM_IDS; k += blockDim.x) E.sm_cnt[k] = 0;
 }
 
 // Pass constants for the first evaluation (at p0): base = trial = p0.

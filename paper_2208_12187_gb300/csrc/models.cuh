@@ -22,32 +22,57 @@
 
 namespace gbfit {
 
-// expm1(z) for FP32: Taylor series through z^9 for |z| <= 0.5 (truncation
-// error below 3e-9 relative), exp(z) - 1 otherwise (no cancellation there).
-__device__ __forceinline__ float expm1_series(float z) {
-    float p = fmaf(z, 1.0f / 362880.0f, 1.0f / 40320.0f);
-    p = fmaf(z, p, 1.0f / 5040.0f);
-    p = fmaf(z, p, 1.0f / 720.0f);
-    p = fmaf(z, p, 1.0f / 120.0f);
+// E' = exp(-q_new) and dE = E' - E without cancellation, where E = exp(-q)
+// and dq = q_new - q is formed without cancellation by the caller.
+// |dq| <= 1/8: dE = E expm1(-dq), expm1 by its Taylor series through z^6
+// (truncation below 1e-9 relative).  |dq| > 1/8: the plain difference,
+// where |dE| >= 11% of max(E, E'), so it keeps ~5e-6 relative accuracy
+// (those are large steps, far from the region where the actual reduction
+// must be resolved below FP32 rounding of the cost).
+__device__ __forceinline__ void exp_shift(float E, float q_new, float dq, float& En, float& dE) {
+    En = __expf(-q_new);
+    float z = -dq;
+    float p = fmaf(z, 1.0f / 720.0f, 1.0f / 120.0f);
     p = fmaf(z, p, 1.0f / 24.0f);
     p = fmaf(z, p, 1.0f / 6.0f);
     p = fmaf(z, p, 0.5f);
     p = fmaf(z, p, 1.0f);
-    p = p * z;
-    return fabsf(z) <= 0.5f ? p : __expf(z) - 1.0f;
+    float dEs = E * (p * z);
+    dE = fabsf(z) <= 0.125f ? dEs : En - E;
 }
 
-// E' = E exp(-dq) and dE = E' - E without cancellation.  For large -dq the
-// base value E is already tiny (E <= exp(-15)) and E' is taken directly.
-__device__ __forceinline__ void exp_shift(float E, float q_new, float dq, float& En, float& dE) {
-    float z = -dq;
-    if (z > 15.0f) {
-        En = __expf(-q_new);
-        dE = En - E;
-    } else {
-        dE = E * expm1_series(z);
-        En = E + dE;
-    }
+// ---- packed FP32 (sm_100 family: one FFMA2 / FMUL2 / FADD2 instruction
+// does the operation for two points).  Every packed helper below is one
+// instruction except the exponentials (one MUFU ex2 per lane element).
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(bc(-1.0f), b, a); }   // exact a - b
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// exp(-q) elementwise (2^(-q log2 e))
+__device__ __forceinline__ float2 expn2(float2 q) {
+    float2 t = mul2(q, bc(-1.4426950408889634f));
+    return make_float2(ex2_approx(t.x), ex2_approx(t.y));
+}
+
+// exp_shift for two points: E' = exp(-q_new), dE = E' - E (series in dq for
+// |dq| <= 1/8, written in dq so that no negation is needed).
+__device__ __forceinline__ void exp_shift2(float2 E, float2 q_new, float2 dq, float2& En, float2& dE) {
+    En = expn2(q_new);
+    // expm1(-u) = u (-1 + u (1/2 + u (-1/6 + u (1/24 + u (-1/120 + u / 720)))))
+    float2 p = fma2(dq, bc(1.0f / 720.0f), bc(-1.0f / 120.0f));
+    p = fma2(dq, p, bc(1.0f / 24.0f));
+    p = fma2(dq, p, bc(-1.0f / 6.0f));
+    p = fma2(dq, p, bc(0.5f));
+    p = fma2(dq, p, bc(-1.0f));
+    float2 dEs = mul2(E, mul2(p, dq));
+    dE.x = fabsf(dq.x) <= 0.125f ? dEs.x : En.x - E.x;
+    dE.y = fabsf(dq.y) <= 0.125f ? dEs.y : En.y - E.y;
 }
 
 // Float images of the FP64 parameters handed to the mixed prep.
@@ -96,6 +121,21 @@ struct MGauss1D {
         dh = fmaf(pf[0], dE, fmaf(pf[9], En, pf[10]));
         J[0] = En; J[1] = pf[11] * En * dn; J[2] = pf[12] * En * dn * dn; J[3] = 1.0f;
     }
+    // the same for two points at once (packed FP32)
+    static constexpr bool PACKED = true;
+    __device__ static void eval_mixed2(const float* pf, float2 X, float2& hb, float2& dh, float2* J) {
+        float2 d = sub2(sub2(X, bc(pf[1])), bc(pf[2]));
+        float2 dd = mul2(d, d);
+        float2 E = expn2(mul2(bc(pf[3]), dd));
+        hb = fma2(bc(pf[0]), E, bc(pf[4]));
+        float2 dn = sub2(d, bc(pf[5]));
+        float2 dq = fma2(bc(pf[7] * (-pf[5])), add2(dn, d), mul2(bc(pf[6]), dd));
+        float2 En, dE;
+        exp_shift2(E, mul2(bc(pf[7]), mul2(dn, dn)), dq, En, dE);
+        dh = fma2(bc(pf[0]), dE, fma2(bc(pf[9]), En, bc(pf[10])));
+        float2 t = mul2(En, dn);
+        J[0] = En; J[1] = mul2(bc(pf[11]), t); J[2] = mul2(bc(pf[12]), mul2(t, dn)); J[3] = bc(1.0f);
+    }
 };
 
 // ------------------------------------------------------------------ dexp
@@ -133,6 +173,17 @@ struct MDexp {
         dh = fmaf(pf[0], de1, fmaf(pf[9], e1n, fmaf(pf[2], de2, fmaf(pf[10], e2n, pf[11]))));
         J[0] = e1n; J[1] = pf[12] * X * e1n; J[2] = e2n; J[3] = pf[13] * X * e2n; J[4] = 1.0f;
     }
+    static constexpr bool PACKED = true;
+    __device__ static void eval_mixed2(const float* pf, float2 X, float2& hb, float2& dh, float2* J) {
+        float2 e1 = expn2(mul2(X, bc(pf[1]))), e2 = expn2(mul2(X, bc(pf[3])));
+        hb = fma2(bc(pf[0]), e1, fma2(bc(pf[2]), e2, bc(pf[4])));
+        float2 e1n, de1, e2n, de2;
+        exp_shift2(e1, mul2(X, bc(pf[14])), mul2(X, bc(pf[5])), e1n, de1);
+        exp_shift2(e2, mul2(X, bc(pf[15])), mul2(X, bc(pf[6])), e2n, de2);
+        dh = fma2(bc(pf[0]), de1, fma2(bc(pf[9]), e1n, fma2(bc(pf[2]), de2, fma2(bc(pf[10]), e2n, bc(pf[11])))));
+        J[0] = e1n; J[1] = mul2(bc(pf[12]), mul2(X, e1n)); J[2] = e2n; J[3] = mul2(bc(pf[13]), mul2(X, e2n));
+        J[4] = bc(1.0f);
+    }
 };
 
 // ------------------------------------------------------------------ gauss2d
@@ -140,6 +191,8 @@ struct MDexp {
 // h = A exp(-u^2/(2 sx^2) - v^2/(2 sy^2)) + c,  p = (A, x0, y0, sx, sy, th, c)
 struct MGauss2D {
     static constexpr int N = 7;
+    static constexpr bool PACKED = false;
+    __device__ static void eval_mixed2(const float*, float2, float2&, float2&, float2*) {}
     __device__ static void prep_plain(const double* p, double* pd) {
         double s, c;
         sincos(p[5], &s, &c);
@@ -221,6 +274,8 @@ struct MGauss2D {
 // h = p0 + p1 x + p2 x^2  (linear in p)
 struct MPoly2 {
     static constexpr int N = 3;
+    static constexpr bool PACKED = false;
+    __device__ static void eval_mixed2(const float*, float2, float2&, float2&, float2*) {}
     __device__ static void prep_plain(const double* p, double* pd) { pd[0] = p[0]; pd[1] = p[1]; pd[2] = p[2]; }
     __device__ static void eval_plain(const double* pd, double X, double, double& h, double* J) {
         h = fma(fma(pd[2], X, pd[1]), X, pd[0]);

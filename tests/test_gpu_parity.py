@@ -199,13 +199,18 @@ def test_mixed_fit_matches_oracle(name, make, _):
 
 def test_mixed_degenerate_dexp_identifiable_part():
     """t1 ~ t2: only a1 + a2 and the curve are determined; the split is not.
-    Mixed and oracle agree on cost and on the fitted curve, not on a1, a2."""
+    Mixed and oracle agree on the fitted curve, not on a1, a2.  In the flat
+    valley the xtol / ftol tests stop each side wherever its steps become
+    small, while the cost still creeps down, so the two stopping costs agree
+    only to ~1e-5 relative; the mixed one must not be the worse one beyond
+    1e-6."""
     pr = synth.dexp(20_000, seed=5, dtype=np.float64)
     assert abs(pr.truth[1] / pr.truth[3] - 1) < 0.1          # a near-degenerate draw
     pr32 = pr.astype(np.float32)
     ref = trf.curve_fit_problem(pr32, **TOL)
     out = gpu_fit(pr, "mixed", dtype=torch.float32, **TOL)
-    assert out["cost"] == pytest.approx(ref["cost"], rel=1e-6)
+    assert out["cost"] == pytest.approx(ref["cost"], rel=1e-5)
+    assert out["cost"] <= ref["cost"] * (1 + 1e-6)
     from oracle import models
     X = pr.coords()
     hg = models.value_and_jac(pr.model, X, out["popt"])[0]
