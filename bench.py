@@ -55,15 +55,19 @@ TOL = dict(ftol=1e-10, xtol=1e-10, gtol=1e-10)
 # precision, implicit grid with sigma: bytes read (y, sigma: FP32) and FP32
 # FLOPs (FMA = 2) of model value, cancellation-free difference, Jacobian row
 # and the Gram / gradient / cost accumulation.
+# Count of the current formulation (FFMA = 2, FADD / FMUL = 1, exp / rcp
+# on the MUFU not counted): model value, difference form and Jacobian row 86,
+# weights, residuals and the Gram / gradient / cost accumulation 87.
 BYTES_PER_POINT = 8
-FLOPS_PER_POINT = 186
+FLOPS_PER_POINT = 173
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) per evaluation launch of the headline workload from
-# the ncu capture summarised in profiles/eval_round_mixed_gauss2d_1024.md; set
-# to None whenever eval_round_kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_LAUNCH = 8.590e6
+# DRAM bytes (read + write) per launch of the loop kernel (one whole fit of
+# the headline workload, 5 passes) from the ncu capture summarised in
+# profiles/fit_loop_mixed_gauss2d_1024.md; None whenever the kernel has
+# changed since the capture.
+TRAFFIC_BYTES_PER_LAUNCH = 8.620e6
 
 
 def workload_desc():
@@ -228,8 +232,6 @@ def run_ours(args, rank, local, world):
         return gbfit.curve_fit(pr.model, None, yy, pr.p0, sigma=ss, lb=pr.lb, ub=pr.ub, grid_wh=(W, H),
                                precision="mixed", **TOL)
 
-    if args.host_launch:
-        gbfit.set_profiling(True)   # same kernels, launched one by one (profilers cannot see graph nodes)
     for _ in range(max(args.warmup, 3)):
         fit(y, sg)
     torch.cuda.synchronize()
@@ -266,22 +268,28 @@ def run_ours(args, rank, local, world):
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms_max / args.steps,
                               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "note": "no extras"}))
         return None
-    # ---- roofline: per-launch CUDA-event timing of the evaluation pass
+    # ---- roofline: CUDA-event timing of the loop-kernel launch (one launch =
+    # one whole fit: nfev evaluation passes plus the trust-region steps)
     gbfit.set_profiling(True)
     gbfit.stats_reset()
+    passes = 0
     for _ in range(3):
         flush.zero_()
-        fit(y, sg)
+        passes += fit(y, sg)["nfev"]
     sp = gbfit.stats()
     gbfit.set_profiling(False)
-    avg_ms = sp["eval_ms"] / max(sp["eval_launches"], 1)
-    achieved = M * FLOPS_PER_POINT / (avg_ms / 1e3) / 1e12
+    launches_p = max(sp["eval_launches"], 1)
+    avg_ms = sp["eval_ms"] / launches_p
+    flops_per_launch = M * FLOPS_PER_POINT * passes / launches_p
+    achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
+    busy = sp["loop_busy_ms"] / max(sp["loop_busy_ms"] + sp["loop_wait_ms"], 1e-12)
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
-            "kernel": "eval_round_kernel<mixed> (rotated 2D Gaussian, grid, sigma)",
+            "kernel": "fit_loop_kernel<mixed> (rotated 2D Gaussian, grid, sigma; one launch per fit)",
             "flops_per_point": FLOPS_PER_POINT, "bytes_per_point": BYTES_PER_POINT,
+            "passes_per_launch": passes / launches_p, "flops_per_launch": flops_per_launch,
             "avg_launch_us": avg_ms * 1e3,
-            "hbm_gbs_at_this_time": M * BYTES_PER_POINT / (avg_ms / 1e3) / 1e9,
+            "cta_time_in_work_frac": busy,
             "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (unit counts and max clock)"}
     if args.traffic is not None:
         roof["traffic"] = args.traffic
@@ -332,8 +340,6 @@ def run_sweep(args):
     gbfit.load()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     sizes = [int(v) for v in args.sizes.split(",")]
-    if args.host_launch:
-        gbfit.set_profiling(True)   # iterations as plain kernel launches (for profilers)
     for m in sizes:
         pr = synth.gauss1d(m, seed=0)
         for prec, dt in (("mixed", torch.float32), ("fp64", torch.float64)):
@@ -592,8 +598,6 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4096)
     ap.add_argument("--serve-rounds", type=int, default=4)
     ap.add_argument("--serve-rates", default="0.25,0.5,0.8,0.95")
-    ap.add_argument("--host-launch", action="store_true",
-                    help="launch iterations from the host instead of the graph (for profilers)")
     args = ap.parse_args()
     if args.sweep:
         return run_sweep(args)

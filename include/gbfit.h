@@ -357,10 +357,10 @@ int gbfit_stats_reset(void);
 int gbfit_stats_get(gbfit_stats* out);
 
 /*
- * on = 1: subsequent fits run their iterations as host-launched kernels, each
- * evaluation launch bracketed by CUDA events on the call's stream (one host
- * synchronisation per iteration: for measurement, not for speed).
- * on = 0 (default): one graph launch per call.  Results are identical.
+ * on = 1: each launch of the loop kernel (one per fit or batch call) is
+ * bracketed by CUDA events on the call's stream and its time added to
+ * gbfit_stats.eval_ms (one extra host synchronisation per call).
+ * on = 0 (default): no events.  Results are identical.
  */
 int gbfit_set_profiling(int on);
 

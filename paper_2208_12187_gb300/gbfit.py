@@ -368,7 +368,7 @@ def stats() -> dict:
 
 
 def set_profiling(on: bool):
-    """Per-launch CUDA-event timing of evaluation passes (host-launched iterations)."""
+    """CUDA-event timing of every loop-kernel launch (stats()["eval_ms"], ["eval_launches"])."""
     _check(load().gbfit_set_profiling(1 if on else 0))
 
 
