@@ -88,7 +88,6 @@ struct Ctx {
     int device = -1, sms = 0, grid_p[2] = {0, 0};
     std::mutex mu;
     char* job = nullptr; size_t cap_job = 0;   // Engine header + per-fit records
-    float* tile_part = nullptr; size_t cap_tp = 0;
     double* tile_part_d = nullptr; size_t cap_tpd = 0;
     double* group_part = nullptr; size_t cap_gp = 0;
     double* wbuf = nullptr; size_t cap_w = 0;
@@ -118,7 +117,7 @@ struct Ctx {
         E.group_cnt = (int*)(job + L.gcnt);
         E.fit_cnt = (int*)(job + L.fcnt);
         E.sm_cnt = (int*)(job + L.smcnt);
-        E.tile_part = tile_part; E.tile_part_d = tile_part_d; E.group_part = group_part;
+        E.tile_part_d = tile_part_d; E.group_part = group_part;
         E.n_items = &ed->sc[0]; E.running = &ed->sc[1]; E.rounds = &ed->sc[2];
         E.max_rounds = &ed->sc[3]; E.nfits_dev = &ed->sc[4];
         return E;
@@ -165,7 +164,6 @@ int ensure(Ctx* c, const JobLayout& L, size_t ntiles, size_t ngroups) {
     bool job_changed = false, scratch_changed = false;
     int rc;
     if ((rc = grow_dev(c->job, c->cap_job, L.end, job_changed))) return rc;
-    if ((rc = grow_dev(c->tile_part, c->cap_tp, ntiles * KMAX, scratch_changed))) return rc;
     if ((rc = grow_dev(c->tile_part_d, c->cap_tpd, ntiles * KMAX, scratch_changed))) return rc;
     if ((rc = grow_dev(c->group_part, c->cap_gp, ngroups * KMAX, scratch_changed))) return rc;
     if (job_changed) c->drop_graphs();
@@ -859,8 +857,7 @@ struct NoAllocLayout {
     static constexpr size_t fcnt = gcnt + ((NOALLOC_MAX_GROUPS * sizeof(int) + 255) / 256) * 256;
     static constexpr size_t res_hdr = fcnt + 256;                          // end of the uploaded image
     static constexpr size_t res = res_hdr + 256;
-    static constexpr size_t tp = res + ((sizeof(FitResult) + 255) / 256) * 256;
-    static constexpr size_t tpd = tp + ((size_t(NOALLOC_MAX_TILES) * KMAX * sizeof(float) + 255) / 256) * 256;
+    static constexpr size_t tpd = res + ((sizeof(FitResult) + 255) / 256) * 256;   // end of the result region
     static constexpr size_t gp = tpd + ((size_t(NOALLOC_MAX_TILES) * KMAX * sizeof(double) + 255) / 256) * 256;
     static constexpr size_t end = gp + ((size_t(NOALLOC_MAX_GROUPS) * KMAX * sizeof(double) + 255) / 256) * 256;
 };
@@ -869,7 +866,7 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = NoAllocLayout::end;             // abou
 std::mutex g_noalloc_mu;
 char* g_noalloc_dev[64] = {};                                            // device address, per device
 alignas(256) char g_noalloc_host[NoAllocLayout::res_hdr];                // upload image (static, not heap)
-alignas(256) char g_noalloc_result[NoAllocLayout::tp - NoAllocLayout::res_hdr];
+alignas(256) char g_noalloc_result[NoAllocLayout::tpd - NoAllocLayout::res_hdr];
 }  // namespace
 
 // The scratch array.  In host code this name is only a host-side stand-in
@@ -942,7 +939,6 @@ extern "C" int gbfit_evaluate_noalloc(int model_id, const void* xdata, int64_t m
     E.items = (WorkItem*)(base + LY::items);
     E.group_cnt = (int*)(base + LY::gcnt);
     E.fit_cnt = (int*)(base + LY::fcnt);
-    E.tile_part = (float*)(base + LY::tp);
     E.tile_part_d = (double*)(base + LY::tpd);
     E.group_part = (double*)(base + LY::gp);
     E.n_items = &Ed->sc[0]; E.running = &Ed->sc[1]; E.rounds = &Ed->sc[2];
@@ -1058,7 +1054,6 @@ struct gbfit_server {
     char* pool = nullptr;
     RangeAlloc pool_alloc, tile_alloc, group_alloc;
     size_t max_tiles = 0, max_groups = 0;
-    float* tile_part = nullptr;
     double* tile_part_d = nullptr;
     double* group_part = nullptr;
     char* job = nullptr;
@@ -1118,8 +1113,7 @@ int gbfit_server_create(const gbfit_server_config* cfg_in, gbfit_server** out) {
     cap = 0;
     if (grow_dev(s->job, cap, s->L->end, ch)) return bail(GBFIT_E_OOM);
     cap = 0;
-    if (s->prec == PREC_MIXED) { if (grow_dev(s->tile_part, cap, s->max_tiles * KMAX, ch)) return bail(GBFIT_E_OOM); }
-    else { if (grow_dev(s->tile_part_d, cap, s->max_tiles * KMAX, ch)) return bail(GBFIT_E_OOM); }
+    if (grow_dev(s->tile_part_d, cap, s->max_tiles * KMAX, ch)) return bail(GBFIT_E_OOM);
     cap = 0;
     if (grow_dev(s->group_part, cap, s->max_groups * KMAX, ch)) return bail(GBFIT_E_OOM);
     cap = 0;
@@ -1147,7 +1141,7 @@ int gbfit_server_create(const gbfit_server_config* cfg_in, gbfit_server** out) {
     E.group_cnt = (int*)(job + s->L->gcnt);
     E.fit_cnt = (int*)(job + s->L->fcnt);
     E.sm_cnt = (int*)(job + s->L->smcnt);
-    E.tile_part = s->tile_part; E.tile_part_d = s->tile_part_d; E.group_part = s->group_part;
+    E.tile_part_d = s->tile_part_d; E.group_part = s->group_part;
     E.n_items = &Ed->sc[0]; E.running = &Ed->sc[1]; E.rounds = &Ed->sc[2];
     E.max_rounds = &Ed->sc[3]; E.nfits_dev = &Ed->sc[4];
     E.sc[3] = 1 << 30;
@@ -1371,7 +1365,6 @@ int gbfit_server_destroy(gbfit_server* s) {
     if (s->stream) { cudaStreamSynchronize(s->stream); cudaStreamDestroy(s->stream); }
     if (s->pool) cudaFree(s->pool);
     if (s->job) cudaFree(s->job);
-    if (s->tile_part) cudaFree(s->tile_part);
     if (s->tile_part_d) cudaFree(s->tile_part_d);
     if (s->group_part) cudaFree(s->group_part);
     if (s->d_list) cudaFree(s->d_list);

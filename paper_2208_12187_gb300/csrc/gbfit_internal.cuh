@@ -87,8 +87,8 @@ struct Engine {
     FitState* state;
     WorkItem* items;
     int* n_items;
-    float* tile_part;      // [tiles][KMAX] mixed tile sums (FP32)
-    double* tile_part_d;   // [tiles][KMAX] plain tile sums (FP64)
+    double* tile_part_d;   // [tiles][KMAX] tile sums (FP64; mixed tiles are summed in FP32 and
+                           // widened by their own CTA, so that the combine only adds)
     double* group_part;    // [groups][KMAX]
     int* group_cnt;        // [groups]
     int* fit_cnt;          // [fits]

@@ -509,8 +509,7 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
     if (threadIdx.x == 0) sm.t_mark = clock64();
     int64_t row = d.tile_base + tile;
     if (threadIdx.x < K) {
-        if (PREC == PREC_MIXED) E.tile_part[row * KMAX + threadIdx.x] = float(tsum);
-        else E.tile_part_d[row * KMAX + threadIdx.x] = double(tsum);
+        E.tile_part_d[row * KMAX + threadIdx.x] = double(tsum);
     }
     // ---- last arriver of the group combines the group
     __syncthreads();
@@ -526,10 +525,7 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
     if (d.n_groups == 1) prefetch_state(stp, sm.trf);      // this CTA runs the step
     if (threadIdx.x == 0) sm.t_fence = clock64();
     double* gout = E.group_part + (d.group_base + group) * KMAX;
-    if (PREC == PREC_MIXED)
-        combine_rows<float>(E.tile_part + (d.tile_base + g0) * KMAX, gsize, K, sm.comb, sm.trf.tot);
-    else
-        combine_rows<double>(E.tile_part_d + (d.tile_base + g0) * KMAX, gsize, K, sm.comb, sm.trf.tot);
+    combine_rows<double>(E.tile_part_d + (d.tile_base + g0) * KMAX, gsize, K, sm.comb, sm.trf.tot);
     if (threadIdx.x == 0) {
         E.group_cnt[d.group_base + group] = 0;
         sm.t_group = clock64();

@@ -73,7 +73,7 @@ struct TrfSmem {
     float Af2[64];
     float Rf[64];     // FP32 accumulated rotations
     float Rf2[64];
-    float Lf[64];     // FP32 Cholesky factor (fast path)
+    float Lf[64];     // FP32 inverse of the equilibrated matrix (fast path)
     float csf[8];
     float pfs[PF];
     MixedParams mp;

@@ -134,71 +134,73 @@ __device__ int jacobi32(int n, float* A, float* A2, float* R, float* R2, int max
     return sweeps;
 }
 
-// ---- Gauss-Newton fast path: FP32 Cholesky, FP64 iterative refinement.
-// Lower Cholesky factor of M = sc * Ah (sc = 1 / max diagonal) in FP32 into
-// L (float 8x8 smem, lower triangle; the diagonal holds 1/L_kk).  Warp 0.
-// Returns false when a pivot is not positive.  min_diag: smallest diagonal
-// entry of M.
-__device__ bool chol32(int n, const double* Ah, float* L, float& sc, float& min_diag) {
+// ---- Gauss-Newton fast path: FP32 inverse, FP64 iterative refinement.
+// M = sc * Ah (sc = 1 / max diagonal).  Mi <- M^-1 in FP32 by Gauss-Jordan
+// elimination without pivoting, in place (float 8x8 smem; rows and columns
+// >= n stay those of the identity).  The pivots are those of M's LDL^T
+// factorisation, so M is positive definite exactly when all are positive;
+// returns false otherwise.  min_diag: smallest diagonal entry of M.  One
+// warp; each lane owns two entries, n rank-one steps.
+__device__ bool inv32(int n, const double* Ah, float* Mi, float& sc, float& min_diag) {
     const int l = threadIdx.x & 31;
     double dmax = gmax8((l < n) ? Ah[l * 8 + l] : 0.0);
     if (!(dmax > 0.0)) return false;
     sc = float(rcp64(dmax));
-    for (int e = l; e < 64; e += 32) {
-        int i = e >> 3, j = e & 7;
-        L[e] = (i < n && j <= i) ? float(Ah[e]) * sc : 0.0f;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        int e = l + 32 * u, i = e >> 3, j = e & 7;
+        Mi[e] = (i < n && j < n) ? float(Ah[e]) * sc : (i == j ? 1.0f : 0.0f);
     }
     __syncwarp();
     bool ok = true;
     min_diag = 1.0f;
-    for (int k = 0; k < n; ++k) min_diag = fminf(min_diag, L[k * 8 + k]);
+    for (int k = 0; k < n; ++k) min_diag = fminf(min_diag, Mi[k * 9]);
     for (int k = 0; k < n; ++k) {
-        float akk = L[k * 8 + k];
-        ok = ok && akk > 0.0f;
-        float rd = rsqrtf(akk > 0.0f ? akk : 1.0f);         // 1 / L_kk
-        __syncwarp();
-        if (l > k && l < n) L[l * 8 + k] *= rd;               // column k
-        if (l == k) L[k * 8 + k] = rd;
-        __syncwarp();
-        for (int e = l; e < 64; e += 32) {                    // trailing update
-            int i = e >> 3, j = e & 7;
-            if (j > k && i >= j && i < n) L[e] = fmaf(-L[i * 8 + k], L[j * 8 + k], L[e]);
+        float piv = Mi[k * 9];
+        ok = ok && piv > 0.0f;
+        float r = __frcp_rn(piv > 0.0f ? piv : 1.0f);
+        float nv[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            int e = l + 32 * u, i = e >> 3, j = e & 7;
+            float aik = Mi[i * 8 + k], akj = Mi[k * 8 + j], aij = Mi[e];
+            nv[u] = (i == k) ? ((j == k) ? r : akj * r) : ((j == k) ? -aik * r : fmaf(-aik * r, akj, aij));
         }
+        __syncwarp();
+        Mi[l] = nv[0];
+        Mi[l + 32] = nv[1];
         __syncwarp();
     }
     return ok;
 }
 
-// z = (L L^T)^-1 b in FP32 (lane values; L from chol32 with inverse diagonal).
-__device__ __forceinline__ float cholsolve32(int n, const float* L, float b) {
+// y = Mi v in FP32 (lane values; lane j holds v_j, lane i receives y_i).
+__device__ __forceinline__ float apply32(int n, const float* Mi, float v) {
     const int l = threadIdx.x & 31;
-    for (int k = 0; k < n; ++k) {                             // L y = b
-        float yk = __shfl_sync(FULL, b, k) * L[k * 8 + k];
-        if (l == k) b = yk;
-        else if (l > k && l < n) b = fmaf(-L[l * 8 + k], yk, b);
-    }
-    for (int k = n - 1; k >= 0; --k) {                        // L^T z = y
-        float zk = __shfl_sync(FULL, b, k) * L[k * 8 + k];
-        if (l == k) b = zk;
-        else if (l < k) b = fmaf(-L[k * 8 + l], zk, b);
-    }
-    return (l < n) ? b : 0.0f;
+    const int i = l >> 2, j = l & 3;
+    float v0 = __shfl_sync(FULL, v, j), v1 = __shfl_sync(FULL, v, j + 4);
+    float acc = fmaf(Mi[i * 8 + j], v0, Mi[i * 8 + j + 4] * v1);
+    acc += __shfl_xor_sync(FULL, acc, 1);
+    acc += __shfl_xor_sync(FULL, acc, 2);
+    float r = __shfl_sync(FULL, acc, (l & 7) << 2);
+    return l < n ? r : 0.0f;
 }
 
-// Ah p = rhs to FP64 accuracy: FP32 Cholesky solve (M = sc Ah, so
+// Ah p = rhs to FP64 accuracy: FP32 solve with M^-1 (M = sc Ah, so
 // p = M^-1 (sc rhs)), then two rounds of FP64 residual + FP32 correction.
 // d1, d2: norms of the two corrections (FP32); their ratio estimates
-// eps32 * cond of the equilibrated matrix.  tmp: an 8-double smem vector.
-__device__ double solve_refined(int n, const double* Ah, const float* L, float sc, double rhs, double* tmp,
+// eps32 * cond of the equilibrated matrix.  tmp: an 8-double smem vector
+// of the calling warp.
+__device__ double solve_refined(int n, const double* Ah, const float* Mi, float sc, double rhs, double* tmp,
                                 float& d1, float& d2) {
     const int l = threadIdx.x & 31;
-    double p = double(cholsolve32(n, L, float(rhs) * sc));
+    double p = double(apply32(n, Mi, float(rhs) * sc));
     float dn[2];
     for (int it = 0; it < 2; ++it) {
         if (l < 8) tmp[l] = (l < n) ? p : 0.0;
         __syncwarp();
         double r = rhs - matvec8(Ah, tmp, n);
-        float dz = cholsolve32(n, L, float(r) * sc);
+        float dz = apply32(n, Mi, float(r) * sc);
         p += double(dz);
         float q = dz * dz;
         for (int o = 4; o; o >>= 1) q += __shfl_xor_sync(FULL, q, o);
@@ -207,6 +209,16 @@ __device__ double solve_refined(int n, const double* Ah, const float* L, float s
     d1 = dn[0];
     d2 = dn[1];
     return (l < n) ? p : 0.0;
+}
+
+// The refined solve is trusted (as an FP64-accurate solve with a
+// non-singular matrix) when the refinement contracts (ratio ~ eps32 cond of
+// the equilibrated matrix) and min_diag / cond stays far above the rank
+// cutoff 8 n eps64 of the pseudo-inverse (lambda_max <= n after
+// equilibration), so that the pseudo-inverse would drop nothing.
+__device__ __forceinline__ bool refined_ok(float d1, float d2, float min_diag) {
+    float cond = fmaxf(1.0f, __fdividef(d2, fmaxf(d1, 1e-37f) * 6e-8f));
+    return (d2 <= 1e-3f * d1 || d2 == 0.0f) && __fdividef(min_diag, cond) > 1e-11f;
 }
 
 // FP64-accurate eigen-decomposition Ah = V diag(lam) V^T (Appendix B: Ah =
@@ -370,6 +382,10 @@ __device__ void prep_pass(const FitDesc& d, FitState* st, TrfSmem& S) {
     __syncwarp();
 }
 
+// Scalar slots of TrfSmem::sd / si shared between the phases.
+enum { SD_F = 0, SD_DELTA, SD_ALPHA, SD_GNORM, SD_SC, SD_MIND };
+enum { SI_STATUS = 0, SI_NFEV, SI_NJEV, SI_FACTOR, SI_GN, SI_REJECTED, SI_PCOV };
+
 // Result record with pcov (R13) from an FP64-accurate eigen-decomposition of
 // the unscaled Gram at the solution.  All CTA threads call.
 __device__ void write_result(const FitDesc& d, FitState* st, FitResult* res, int status, TrfSmem& S) {
@@ -384,6 +400,33 @@ __device__ void write_result(const FitDesc& d, FitState* st, FitResult* res, int
         return;
     }
     __syncthreads();
+    // Well-conditioned Gram: its inverse, one refined solve per column, one
+    // column per warp (equal to the pseudo-inverse when nothing is cut).
+    if (t < 32) {
+        float sc = 1.0f, mind = 0.0f;
+        bool ok = __all_sync(FULL, inv32(n, S.B, S.Lf, sc, mind));
+        if (t == 0) { S.si[SI_PCOV] = ok ? 1 : 0; S.sd[SD_SC] = sc; S.sd[SD_MIND] = mind; }
+    }
+    __syncthreads();
+    if (S.si[SI_PCOV]) {
+        const int w = t >> 5, l = t & 31;
+        if (w < n) {
+            float d1, d2;
+            double col = solve_refined(n, S.B, S.Lf, float(S.sd[SD_SC]), (l == w) ? 1.0 : 0.0, S.W + 8 * w, d1, d2);
+            if (l < n) S.H[l * 8 + w] = col;
+            if (l == 0 && !refined_ok(d1, d2, float(S.sd[SD_MIND]))) S.si[SI_PCOV] = 0;
+        }
+        __syncthreads();
+        if (S.si[SI_PCOV]) {
+            double scale = d.absolute_sigma ? 1.0 : 2.0 * st->f / double(d.m - n);
+            if (t < 64) {
+                int i = t >> 3, j = t & 7;
+                if (i < n && j < n) res->pcov[i * n + j] = 0.5 * (S.H[i * 8 + j] + S.H[j * 8 + i]) * scale;
+            }
+            __syncthreads();
+            return;
+        }
+    }
     eig_fast(n, S.B, nullptr, S);
     if (t < 32) {
         int l = t;
@@ -417,9 +460,6 @@ __device__ __forceinline__ void prefetch_state(const FitState* st, TrfSmem& S) {
     for (int k = threadIdx.x; k < STATE_WORDS; k += blockDim.x) dst[k] = __ldcg(src + k);
 }
 
-// Scalar slots of TrfSmem::sd / si shared between the phases.
-enum { SD_F = 0, SD_DELTA, SD_ALPHA, SD_GNORM };
-enum { SI_STATUS = 0, SI_NFEV, SI_NJEV, SI_FACTOR, SI_GN, SI_REJECTED };
 
 // One trust-region iteration for one fit.  S.tot holds the combined sums of
 // the evaluation at st->xt that just finished; S.stc the state as it was
@@ -574,15 +614,14 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
     // (inside the old region or not) cannot be inside the new one: skip it.
     if (warp == 0 && !S.si[SI_REJECTED]) {
         float sc = 1.0f, mind = 0.0f;
-        bool ok = chol32(n, S.Ah, S.Lf, sc, mind);
+        bool ok = inv32(n, S.Ah, S.Lf, sc, mind);
         ok = __all_sync(FULL, ok);
         bool inside = false;
         if (ok) {
             double gh = (l < n) ? S.vec[VGH][l] : 0.0;
             float d1, d2;
             double pt = solve_refined(n, S.Ah, S.Lf, sc, -gh, S.vec[VTMP], d1, d2);
-            float cond = fmaxf(1.0f, __fdividef(d2, fmaxf(d1, 1e-37f) * 6e-8f));
-            ok = (d2 <= 1e-3f * d1 || d2 == 0.0f) && __fdividef(mind, cond) > 1e-11f;
+            ok = refined_ok(d1, d2, mind);
             double Delta = S.sd[SD_DELTA];
             inside = gsum8(pt * pt) <= Delta * Delta;
             if (l < 8) S.vec[VSTR][l] = pt;
