@@ -96,7 +96,7 @@ struct PointCoord {
     __device__ void init(int64_t i, int64_t w) { W = (int)w; Y = (int)(i / w); X = (int)(i - (int64_t)Y * w); }
     __device__ void advance(int step) {
         X += step;
-        if (X >= W) { if (W >= EVAL_THREADS) { X -= W; Y += 1; } else { Y += X / W; X = X % W; } }
+        if (X >= W) { if (W >= step) { X -= W; Y += 1; } else { Y += X / W; X = X % W; } }
     }
 };
 
@@ -158,10 +158,12 @@ __device__ __forceinline__ void accum_point(const float* pfl, const double* pdl,
     }
 }
 
-// Two points at once with packed FP32 (1D models, mixed precision).
-template <class M, int WK>
-__device__ __forceinline__ void accum_point2(const float* pfl, float2 X, float2 yv, float2 sv, bool check,
-                                             float2 (&acc)[n_acc(M::N, PREC_MIXED)], int& bad) {
+// Two points at once with packed FP32 (mixed precision): model, residual
+// and weights packed; accumulators packed (ACC = float2, two partial sums
+// per slot) or scalar (ACC = float, both points added to one sum).
+template <class M, int WK, typename ACC>
+__device__ __forceinline__ void accum_point2(const float* pfl, float2 X, float2 Y, float2 yv, float2 sv, bool check,
+                                             ACC (&acc)[n_acc(M::N, PREC_MIXED)], int& bad) {
     constexpr int N = M::N;
     constexpr int NT = n_tri(N);
     float2 w = bc(1.0f);
@@ -169,9 +171,10 @@ __device__ __forceinline__ void accum_point2(const float* pfl, float2 X, float2 
         if (check && !(sv.x > 0.0f && isfinite(sv.x) && sv.y > 0.0f && isfinite(sv.y))) bad = 1;
         w = make_float2(__fdividef(1.0f, sv.x), __fdividef(1.0f, sv.y));
     }
-    if (check && !(isfinite(X.x) && isfinite(X.y) && isfinite(yv.x) && isfinite(yv.y))) bad = 1;
+    if (check && !(isfinite(X.x) && isfinite(X.y) && isfinite(Y.x) && isfinite(Y.y) && isfinite(yv.x) &&
+                   isfinite(yv.y))) bad = 1;
     float2 hb, dh, J[N];
-    M::eval_mixed2(pfl, X, hb, dh, J);
+    M::eval_mixed2(pfl, X, Y, hb, dh, J);
     float2 r = sub2(hb, yv), dr = dh;
     if (WK == W_SIGMA) {
         r = mul2(w, r);
@@ -180,15 +183,31 @@ __device__ __forceinline__ void accum_point2(const float* pfl, float2 X, float2 
         for (int a = 0; a < N; ++a) J[a] = mul2(w, J[a]);
     }
     float2 rn = add2(r, dr);
-    int idx = 0;
+    float2 dc = mul2(dr, fma2(bc(2.0f), r, dr));
+    if constexpr (std::is_same<ACC, float2>::value) {
+        int idx = 0;
 #pragma unroll
-    for (int a = 0; a < N; ++a)
+        for (int a = 0; a < N; ++a)
 #pragma unroll
-        for (int b = a; b < N; ++b) { acc[idx] = fma2(J[a], J[b], acc[idx]); ++idx; }
+            for (int b = a; b < N; ++b) { acc[idx] = fma2(J[a], J[b], acc[idx]); ++idx; }
 #pragma unroll
-    for (int a = 0; a < N; ++a) acc[NT + a] = fma2(J[a], rn, acc[NT + a]);
-    acc[NT + N] = fma2(rn, rn, acc[NT + N]);
-    acc[NT + N + 1] = fma2(dr, fma2(bc(2.0f), r, dr), acc[NT + N + 1]);
+        for (int a = 0; a < N; ++a) acc[NT + a] = fma2(J[a], rn, acc[NT + a]);
+        acc[NT + N] = fma2(rn, rn, acc[NT + N]);
+        acc[NT + N + 1] = add2(dc, acc[NT + N + 1]);
+    } else {
+        int idx = 0;
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int b = a; b < N; ++b) {
+                acc[idx] = fmaf(J[a].y, J[b].y, fmaf(J[a].x, J[b].x, acc[idx]));
+                ++idx;
+            }
+#pragma unroll
+        for (int a = 0; a < N; ++a) acc[NT + a] = fmaf(J[a].y, rn.y, fmaf(J[a].x, rn.x, acc[NT + a]));
+        acc[NT + N] = fmaf(rn.y, rn.y, fmaf(rn.x, rn.x, acc[NT + N]));
+        acc[NT + N + 1] += dc.x + dc.y;
+    }
 }
 
 // Points [i0, i1) with register loads (software-pipelined one point ahead).
@@ -335,8 +354,11 @@ __device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0,
     // head points with plain loads while the first chunks stream in
     tile_points<M, PREC_MIXED, float, LAYOUT, WK>(d, pfl, nullptr, i0, a0, check, acc, bad);
     PointCoord pc;
-    if (LAYOUT == X_GRID) pc.init(a0 + t, d.grid_w);
-    constexpr bool PK = M::PACKED && LAYOUT == X_VEC;      // two points per thread step
+    if (LAYOUT == X_GRID) pc.init(a0 + (M::PACK == 2 ? 2 * t : t), d.grid_w);
+    // two points per thread step: 1D models on explicit x (packed sums),
+    // the 2D model on the grid or explicit coordinates (scalar sums)
+    constexpr bool PK = M::PACK == 1 && LAYOUT == X_VEC;
+    constexpr bool PK2 = M::PACK == 2 && LAYOUT != X_VEC;
     constexpr int K = n_acc(M::N, PREC_MIXED);
     float2 acc2[PK ? K : 1];         // (the head's sums move in, so that acc[] is dead in the loop)
 #pragma unroll
@@ -354,7 +376,26 @@ __device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0,
                 float2 X = *reinterpret_cast<const float2*>(B + RS::SX * CH + k);
                 float2 yv = *reinterpret_cast<const float2*>(B + RS::SY * CH + k);
                 float2 sv = (WK == W_SIGMA) ? *reinterpret_cast<const float2*>(B + RS::SS * CH + k) : bc(1.0f);
-                accum_point2<M, WK>(pfl, X, yv, sv, check, acc2, bad);
+                accum_point2<M, WK, float2>(pfl, X, bc(0.0f), yv, sv, check, acc2, bad);
+            }
+        } else if constexpr (PK2) {
+            for (int k = 2 * t; k < cnt; k += 2 * EVAL_THREADS) {
+                float2 X, Y;
+                if (LAYOUT == X_GRID) {
+                    // pixels k, k + 1 of the chunk: (X, Y) and its right neighbour (next row at the edge)
+                    X.x = float(pc.X);
+                    Y.x = float(pc.Y);
+                    bool wrap = pc.X + 1 >= pc.W;
+                    X.y = wrap ? 0.0f : float(pc.X + 1);
+                    Y.y = wrap ? float(pc.Y + 1) : float(pc.Y);
+                    pc.advance(2 * EVAL_THREADS);
+                } else {
+                    X = *reinterpret_cast<const float2*>(B + RS::SX * CH + k);
+                    Y = *reinterpret_cast<const float2*>(B + RS::SX2 * CH + k);
+                }
+                float2 yv = *reinterpret_cast<const float2*>(B + RS::SY * CH + k);
+                float2 sv = (WK == W_SIGMA) ? *reinterpret_cast<const float2*>(B + RS::SS * CH + k) : bc(1.0f);
+                accum_point2<M, WK, float>(pfl, X, Y, yv, sv, check, acc, bad);
             }
         } else
 #pragma unroll 2

@@ -121,9 +121,10 @@ struct MGauss1D {
         dh = fmaf(pf[0], dE, fmaf(pf[9], En, pf[10]));
         J[0] = En; J[1] = pf[11] * En * dn; J[2] = pf[12] * En * dn * dn; J[3] = 1.0f;
     }
-    // the same for two points at once (packed FP32)
-    static constexpr bool PACKED = true;
-    __device__ static void eval_mixed2(const float* pf, float2 X, float2& hb, float2& dh, float2* J) {
+    // the same for two points at once (packed FP32); PACK 1: packed
+    // accumulators too (few slots), 2: scalar accumulators (many slots)
+    static constexpr int PACK = 1;
+    __device__ static void eval_mixed2(const float* pf, float2 X, float2, float2& hb, float2& dh, float2* J) {
         float2 d = sub2(sub2(X, bc(pf[1])), bc(pf[2]));
         float2 dd = mul2(d, d);
         float2 E = expn2(mul2(bc(pf[3]), dd));
@@ -173,8 +174,8 @@ struct MDexp {
         dh = fmaf(pf[0], de1, fmaf(pf[9], e1n, fmaf(pf[2], de2, fmaf(pf[10], e2n, pf[11]))));
         J[0] = e1n; J[1] = pf[12] * X * e1n; J[2] = e2n; J[3] = pf[13] * X * e2n; J[4] = 1.0f;
     }
-    static constexpr bool PACKED = true;
-    __device__ static void eval_mixed2(const float* pf, float2 X, float2& hb, float2& dh, float2* J) {
+    static constexpr int PACK = 1;
+    __device__ static void eval_mixed2(const float* pf, float2 X, float2, float2& hb, float2& dh, float2* J) {
         float2 e1 = expn2(mul2(X, bc(pf[1]))), e2 = expn2(mul2(X, bc(pf[3])));
         hb = fma2(bc(pf[0]), e1, fma2(bc(pf[2]), e2, bc(pf[4])));
         float2 e1n, de1, e2n, de2;
@@ -191,8 +192,7 @@ struct MDexp {
 // h = A exp(-u^2/(2 sx^2) - v^2/(2 sy^2)) + c,  p = (A, x0, y0, sx, sy, th, c)
 struct MGauss2D {
     static constexpr int N = 7;
-    static constexpr bool PACKED = false;
-    __device__ static void eval_mixed2(const float*, float2, float2&, float2&, float2*) {}
+    static constexpr int PACK = 2;
     __device__ static void prep_plain(const double* p, double* pd) {
         double s, c;
         sincos(p[5], &s, &c);
@@ -268,14 +268,41 @@ struct MGauss2D {
         J[5] = Q * 2.0f * un * vn * (pf[15] - pf[14]);
         J[6] = 1.0f;
     }
+    __device__ static void eval_mixed2(const float* pf, float2 X, float2 Y, float2& hb, float2& dh, float2* J) {
+        float2 dx = sub2(sub2(X, bc(pf[1])), bc(pf[2]));
+        float2 dy = sub2(sub2(Y, bc(pf[3])), bc(pf[4]));
+        float2 u = fma2(dx, bc(pf[5]), mul2(dy, bc(pf[6])));
+        float2 v = fma2(dy, bc(pf[5]), mul2(dx, bc(-pf[6])));
+        float2 q = fma2(mul2(bc(pf[7]), u), u, mul2(mul2(bc(pf[8]), v), v));
+        float2 E = expn2(q);
+        hb = fma2(bc(pf[0]), E, bc(pf[9]));
+        float2 du = fma2(dx, bc(pf[10]), fma2(dy, bc(pf[11]), bc(pf[12])));
+        float2 dv = fma2(dy, bc(pf[10]), fma2(dx, bc(-pf[11]), bc(pf[13])));
+        float2 un = add2(u, du), vn = add2(v, dv);
+        float2 dq = fma2(mul2(bc(pf[14]), du), add2(un, u),
+                         fma2(mul2(bc(pf[16]), u), u, fma2(mul2(bc(pf[15]), dv), add2(vn, v), mul2(mul2(bc(pf[17]), v), v))));
+        float2 qn = fma2(mul2(bc(pf[14]), un), un, mul2(mul2(bc(pf[15]), vn), vn));
+        float2 En, dE;
+        exp_shift2(E, qn, dq, En, dE);
+        dh = fma2(bc(pf[0]), dE, fma2(bc(pf[19]), En, bc(pf[20])));
+        float2 Q = mul2(bc(pf[18]), En);
+        float2 au = mul2(bc(2.0f * pf[14]), un), bv = mul2(bc(2.0f * pf[15]), vn);
+        J[0] = En;
+        J[1] = mul2(Q, fma2(au, bc(pf[21]), mul2(bv, bc(-pf[22]))));
+        J[2] = mul2(Q, fma2(au, bc(pf[22]), mul2(bv, bc(pf[21]))));
+        J[3] = mul2(mul2(mul2(Q, bc(pf[23])), un), un);
+        J[4] = mul2(mul2(mul2(Q, bc(pf[24])), vn), vn);
+        J[5] = mul2(mul2(mul2(Q, bc(2.0f * (pf[15] - pf[14]))), un), vn);
+        J[6] = bc(1.0f);
+    }
 };
 
 // ------------------------------------------------------------------ poly2
 // h = p0 + p1 x + p2 x^2  (linear in p)
 struct MPoly2 {
     static constexpr int N = 3;
-    static constexpr bool PACKED = false;
-    __device__ static void eval_mixed2(const float*, float2, float2&, float2&, float2*) {}
+    static constexpr int PACK = 0;
+    __device__ static void eval_mixed2(const float*, float2, float2, float2&, float2&, float2*) {}
     __device__ static void prep_plain(const double* p, double* pd) { pd[0] = p[0]; pd[1] = p[1]; pd[2] = p[2]; }
     __device__ static void eval_plain(const double* pd, double X, double, double& h, double* J) {
         h = fma(fma(pd[2], X, pd[1]), X, pd[0]);
