@@ -432,8 +432,12 @@ def run_batch(args):
     plain_fps = S / (time.perf_counter() - t0)
     # popt error of the batched mixed fits: against the FP64 oracle (sample) and the plain FP64 GPU path
     K = min(args.oracle_sample, bt.nfits)
-    e_or = np.array([relerr_vec(out["popt"][k], trf.curve_fit_problem(bt.fit(k).astype(np.float64), **TOL)["popt"])
-                     for k in range(K)])
+    refs = [trf.curve_fit_problem(bt.fit(k).astype(np.float64), **TOL) for k in range(K)]
+    e_or = np.array([relerr_vec(out["popt"][k], refs[k]["popt"]) for k in range(K)])
+    # the same difference in units of each parameter's standard error (oracle pcov):
+    # numerical error against the statistical uncertainty of the fit
+    e_se = np.array([float(np.max(np.abs(out["popt"][k] - refs[k]["popt"]) /
+                                  np.sqrt(np.maximum(np.abs(np.diag(refs[k]["pcov"])), 1e-300)))) for k in range(K)])
     e_pl = np.array([relerr_vec(out["popt"][k], plain[k]) for k in range(S)])
     err = lambda e: {"max": float(e.max()), "p50": float(np.median(e)), "frac_le_1e-6": float(np.mean(e <= 1e-6))}
     print(json.dumps({"mode": "batch", "model": "dexp", "nfits": bt.nfits, "total_points": int(bt.offsets[-1]),
@@ -442,6 +446,8 @@ def run_batch(args):
                       "plain_fp64_one_at_a_time": {"fits_per_s": plain_fps, "sample": S},
                       "batched_over_plain_fits_per_s": res["fits_per_s"] / plain_fps,
                       "popt_rel_err_vs_oracle": {**err(e_or), "sample": K},
+                      "popt_err_in_standard_errors_vs_oracle": {"max": float(e_se.max()), "p50": float(np.median(e_se)),
+                                                                "frac_le_1e-3": float(np.mean(e_se <= 1e-3))},
                       "popt_rel_err_vs_plain_fp64_gpu": {**err(e_pl), "sample": S}}))
 
 

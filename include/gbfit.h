@@ -9,9 +9,9 @@
  * (Appendix B).  Everything after argument checking runs on one GPU: model,
  * residual and Jacobian rows are formed in registers and reduced to J^T J,
  * J^T r and the cost without writing J to memory; the n x n step, ratio,
- * radius update and termination run on the device; the iteration loop is a
- * CUDA graph with a device-set WHILE condition, so a fit makes no host round
- * trip per iteration.
+ * radius update and termination run on the device; every iteration of a
+ * call runs inside one persistent (cooperative) kernel launch, so a fit
+ * makes no host round trip per iteration.
  *
  * Conventions shared by every entry point
  *   - Return value: GBFIT_OK (0) or a negative GBFIT_E_* code; the message of
@@ -26,7 +26,7 @@
  *     enqueues its work on that stream and returns after the results have
  *     been copied back (one stream synchronisation per call).
  *   - Calls on one device are serialised by an internal lock (the device
- *     workspace and cached graphs are shared).
+ *     workspace and the cached launch are shared).
  *   - Fit non-convergence is not an error: it is reported in fit_status.
  */
 #ifndef GBFIT_H
@@ -137,10 +137,11 @@ int gbfit_curve_fit(int model_id,
 /*
  * Many independent fits of one model over concatenated data (paper Appendix A's
  * fixed-size padding replaced by segment offsets: no point of one fit touches
- * another).  All fits iterate together: each graph round evaluates every
- * running fit once, in shared launches, and a fit that has finished takes no
- * further work.  A fit's reduction tiling depends only on its own m, so its
- * result is bit-identical alone and in any batch.
+ * another).  All fits iterate together in one launch: each round evaluates
+ * every running fit once, and a fit that has finished takes no further work.
+ * A fit's reduction shape comes from the tile table (gbfit_tune_shape) and
+ * depends only on its own m, so its result is bit-identical alone (with the
+ * same shape) and in any batch.
  *   nfits      number of fits (>= 1)
  *   offsets    host int64 [nfits + 1], offsets[0] = 0, strictly increasing by >= n
  *   xdata      [total] (GBFIT_X_VEC) or [2][total] (GBFIT_X_SOA2)
@@ -325,7 +326,7 @@ int gbfit_evaluate_noalloc(int model_id,
 typedef struct gbfit_stats {
     int64_t calls;            /* gbfit_curve_fit / _batch / _evaluate calls            */
     int64_t fits;             /* fits completed                                        */
-    int64_t kernel_launches;  /* kernels the library executed (graph nodes included)   */
+    int64_t kernel_launches;  /* kernels the library launched                           */
     int64_t graph_rounds;     /* rounds of the persistent loop kernel (one evaluation of
                                  every running fit each)                              */
     int64_t passes;           /* data passes = sum over fits of nfev                   */

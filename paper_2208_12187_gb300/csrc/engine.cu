@@ -301,7 +301,7 @@ gbfit_options defaults() {
 
 // Run nfits fits whose descriptors (data pointers already on the device) are
 // in hd[]; writes per-fit results into hr[].  One host-to-device copy of the
-// job buffer, one graph launch, one device-to-host copy of the results.
+// job buffer, one loop-kernel launch, one device-to-host copy of the results.
 int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::vector<double>>& p0s,
              std::vector<FitResult>& hr, cudaStream_t s, int* rounds_out) {
     const auto t_host0 = std::chrono::steady_clock::now();
