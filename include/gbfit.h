@@ -300,9 +300,9 @@ int gbfit_server_destroy(gbfit_server* s);
  *   - xdata, ydata and sigma must be device pointers (no staging copy);
  *   - the pass's scratch (tile and group partial sums, arrival counters, the
  *     one-fit job record) lives in a fixed file-scope device array of about
- *     1.2 MB that every GPU loading the library keeps until the process exits;
- *     at most 2048 reduction tiles fit, i.e. m <= 33,554,432 points at the
- *     largest default tile (16384 points); larger requests fail with
+ *     1 MB that every GPU loading the library keeps until the process exits;
+ *     at most 2048 reduction tiles fit, i.e. m <= 134,217,728 points at the
+ *     largest default tile (65536 points); larger requests fail with
  *     GBFIT_E_INVALID_ARG and a message giving the limit;
  *   - the first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call

@@ -25,7 +25,7 @@ using namespace gbfit;
 
 namespace {
 
-constexpr int TILE_MIN = 2048, TILE_MAX = 16384, TILE_SPLIT = 304;   // TILE_SPLIT: grid when none is known
+constexpr int TILE_MIN = 2048, TILE_MAX = 65536, TILE_SPLIT = 304;   // TILE_SPLIT: grid when none is known
 
 thread_local std::string g_err;
 
@@ -861,7 +861,7 @@ struct NoAllocLayout {
     static constexpr size_t gp = tpd + ((size_t(NOALLOC_MAX_TILES) * KMAX * sizeof(double) + 255) / 256) * 256;
     static constexpr size_t end = gp + ((size_t(NOALLOC_MAX_GROUPS) * KMAX * sizeof(double) + 255) / 256) * 256;
 };
-constexpr size_t NOALLOC_SCRATCH_BYTES = NoAllocLayout::end;             // about 1.2 MB
+constexpr size_t NOALLOC_SCRATCH_BYTES = NoAllocLayout::end;             // about 0.9 MB
 
 std::mutex g_noalloc_mu;
 char* g_noalloc_dev[64] = {};                                            // device address, per device
@@ -903,7 +903,7 @@ extern "C" int gbfit_evaluate_noalloc(int model_id, const void* xdata, int64_t m
         return fail(GBFIT_E_INVALID_ARG,
                     "m = %lld needs %lld reduction tiles of %d points; the allocation-free entry point holds at "
                     "most %d tiles (m <= %lld points at the largest default tile)",
-                    (long long)m, (long long)ntiles, tp, NOALLOC_MAX_TILES, (long long)NOALLOC_MAX_TILES * 16384);
+                    (long long)m, (long long)ntiles, tp, NOALLOC_MAX_TILES, (long long)NOALLOC_MAX_TILES * TILE_MAX);
     if (!is_device_ptr(ydata) || (xdata && x_layout != GBFIT_X_GRID && !is_device_ptr(xdata)) ||
         (sigma && !is_device_ptr(sigma)))
         return fail(GBFIT_E_INVALID_ARG, "the allocation-free entry point needs device-resident data arrays");

@@ -443,6 +443,7 @@ struct RoundSmem {
     double pd[PD];
     int flag[4];
     int ctl;
+    int desc_fit;                      // fit whose descriptor is in desc (-1: none yet)
     union {
         float redf[8 * KMAX];
         double redd[8 * KMAX];
@@ -615,6 +616,7 @@ __device__ __forceinline__ void round_setup(RoundSmem& sm, float* ring_buf, Ring
     R.buf = ring_buf;
     R.seq = 0;
     R.fail = &sm.ring_fail;
+    if (threadIdx.x == 0) sm.desc_fit = -1;
     if (PREC == PREC_MIXED) {
         if (threadIdx.x == 0) {
             for (int s = 0; s < NST; ++s) {
@@ -643,8 +645,19 @@ __device__ __forceinline__ void run_items(RoundSmem& sm, const Engine& E, RingSt
         long long t_item = clock64();
         WorkItem wi = E.items[it];
         FitState* stp = E.state + wi.fit;
-        if (threadIdx.x == 0) { sm.flag[0] = stp->run; sm.flag[1] = stp->phase; }
+        // one round trip for the item's state words, pass constants and (when
+        // this CTA's previous item was another fit) descriptor; state from
+        // L2, since other CTAs rewrite it between rounds
+        if (threadIdx.x == 0) { sm.flag[0] = __ldcg(&stp->run); sm.flag[1] = __ldcg(&stp->phase); }
+        if (PREC == PREC_MIXED) { if (threadIdx.x < PF) sm.pf[threadIdx.x] = __ldcg(stp->pf + threadIdx.x); }
+        else { if (threadIdx.x < PD) sm.pd[threadIdx.x] = __ldcg(stp->pd + threadIdx.x); }
+        if (wi.fit != sm.desc_fit) {
+            const int* src = (const int*)(E.desc + wi.fit);
+            int* dst = (int*)&sm.desc;
+            for (int k = threadIdx.x; k < (int)(sizeof(FitDesc) / 4); k += EVAL_THREADS) dst[k] = src[k];
+        }
         __syncthreads();
+        if (threadIdx.x == 0) sm.desc_fit = wi.fit;
         if (sm.flag[0] != RS_RUNNING) {
             __syncthreads();
             if (next_item) {
@@ -657,15 +670,6 @@ __device__ __forceinline__ void run_items(RoundSmem& sm, const Engine& E, RingSt
             }
             continue;
         }
-        // stage desc and pass constants
-        {
-            const int* src = (const int*)(E.desc + wi.fit);
-            int* dst = (int*)&sm.desc;
-            for (int k = threadIdx.x; k < (int)(sizeof(FitDesc) / 4); k += EVAL_THREADS) dst[k] = src[k];
-            if (PREC == PREC_MIXED) { if (threadIdx.x < PF) sm.pf[threadIdx.x] = stp->pf[threadIdx.x]; }
-            else { if (threadIdx.x < PD) sm.pd[threadIdx.x] = stp->pd[threadIdx.x]; }
-        }
-        __syncthreads();
         switch (sm.desc.model) {
             case 0: process_item<MGauss1D, PREC>(sm, E, wi.fit, wi.tile, R, t_item); break;
             case 1: process_item<MDexp, PREC>(sm, E, wi.fit, wi.tile, R, t_item); break;

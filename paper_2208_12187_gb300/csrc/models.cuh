@@ -242,6 +242,41 @@ struct MGauss2D {
         pf[21] = ct; pf[22] = st;
         pf[23] = 2.0f * kat / sxt; pf[24] = 2.0f * kbt / syt;
     }
+    // prep_mixed on a whole warp: the four angles' sin/cos and the four
+    // widths' 1/(2 w^2) (and 2 k / w) in lanes 0-3 at once, the rest on
+    // lane 0.  tmp: 16 floats of shared memory.
+    __device__ static void prep_mixed_warp(const MixedParams& P, float* pf, float* tmp) {
+        const int l = threadIdx.x & 31;
+        const int q = l & 3;
+        const float th = P.x[5], dth = P.dx[5];
+        float ang = q == 0 ? th : q == 1 ? P.xt[5] : q == 2 ? 0.5f * dth : th + 0.5f * dth;
+        float sn, cs;
+        sincosf(ang, &sn, &cs);
+        float w = q == 0 ? P.x[3] : q == 1 ? P.x[4] : q == 2 ? P.xt[3] : P.xt[4];
+        float kk = 0.5f / (w * w);
+        float rk = 2.0f * kk / w;
+        if (l < 4) { tmp[l] = sn; tmp[4 + l] = cs; tmp[8 + l] = kk; tmp[12 + l] = rk; }
+        __syncwarp();
+        if (l == 0) {
+            float s = tmp[0], c = tmp[4], st = tmp[1], ct = tmp[5], sh = tmp[2];
+            float dc = -2.0f * tmp[3] * sh, ds = 2.0f * tmp[7] * sh;
+            float sx = P.x[3], sy = P.x[4], sxt = P.xt[3], syt = P.xt[4];
+            float ka = tmp[8], kb = tmp[9], kat = tmp[10], kbt = tmp[11];
+            float dx0 = P.dx[1], dy0 = P.dx[2];
+            pf[0] = P.x[0]; pf[1] = P.x[1]; pf[2] = P.xlo[1]; pf[3] = P.x[2]; pf[4] = P.xlo[2];
+            pf[5] = c; pf[6] = s; pf[7] = ka; pf[8] = kb; pf[9] = P.x[6];
+            pf[10] = dc; pf[11] = ds;
+            pf[12] = -dx0 * ct - dy0 * st;
+            pf[13] = dx0 * st - dy0 * ct;
+            pf[14] = kat; pf[15] = kbt;
+            pf[16] = -P.dx[3] * (sxt + sx) * 2.0f * ka * kat;
+            pf[17] = -P.dx[4] * (syt + sy) * 2.0f * kb * kbt;
+            pf[18] = P.xt[0]; pf[19] = P.dx[0]; pf[20] = P.dx[6];
+            pf[21] = ct; pf[22] = st;
+            pf[23] = tmp[14]; pf[24] = tmp[15];
+        }
+        __syncwarp();
+    }
     __device__ static void eval_mixed(const float* pf, float X, float Y, float& hb, float& dh, float* J) {
         float dx = (X - pf[1]) - pf[2];
         float dy = (Y - pf[3]) - pf[4];

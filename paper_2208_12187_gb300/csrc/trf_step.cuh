@@ -355,12 +355,14 @@ __device__ void prep_pass(const FitDesc& d, FitState* st, TrfSmem& S) {
             S.mp.dx[l] = float(xt - x);
         }
         __syncwarp();
-        if (l == 0) {
-            for (int k = 0; k < PF; ++k) S.pfs[k] = 0.0f;
+        S.pfs[l] = 0.0f;
+        __syncwarp();
+        if (d.model == 2) {
+            MGauss2D::prep_mixed_warp(S.mp, S.pfs, S.Af);
+        } else if (l == 0) {
             switch (d.model) {
                 case 0: MGauss1D::prep_mixed(S.mp, S.pfs); break;
                 case 1: MDexp::prep_mixed(S.mp, S.pfs); break;
-                case 2: MGauss2D::prep_mixed(S.mp, S.pfs); break;
                 case 3: MPoly2::prep_mixed(S.mp, S.pfs); break;
             }
         }
