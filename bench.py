@@ -63,6 +63,7 @@ FLOPS_PER_POINT = 173
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 L2_FLUSH_BYTES = 256 << 20
+HBM_PEAK_GBS = 6785.9          # MEASURED_PEAKS.json: copy bandwidth of the GB300s
 # DRAM bytes (read + write) per launch of the loop kernel (one whole fit of
 # the headline workload, 5 passes) from the ncu capture summarised in
 # profiles/fit_loop_mixed_gauss2d_1024.md; None whenever the kernel has
@@ -162,17 +163,31 @@ def allreduce(values, op, world):
 
 
 # ------------------------------------------------------------------ CPU oracle timing
-def oracle_rate(pr, budget_s: float = 12.0, max_fits: int = 8):
+def oracle_rate(pr, budget_s: float = 12.0, max_fits: int = 8, want_result: bool = False):
     """Time whole oracle fits of the workload until the budget is spent."""
     from oracle import trf
-    t_total, pts, fits = 0.0, 0.0, 0
+    t_total, pts, fits, out = 0.0, 0.0, 0, None
     while fits < max_fits and (t_total < budget_s or fits == 0):
         t0 = time.perf_counter()
         out = trf.curve_fit_problem(pr, **TOL)
         t_total += time.perf_counter() - t0
         pts += pr.m * out["nfev"]
         fits += 1
+    if want_result:
+        return pts / t_total, fits, t_total, out
     return pts / t_total, fits, t_total
+
+
+def oracle_rate_one_core(budget_s: float = 8.0):
+    """The same oracle timing with one BLAS / OpenMP thread, in a child
+    process (thread counts are fixed when numpy loads)."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-rate-only", str(budget_s)],
+                             env=env, capture_output=True, text=True, timeout=budget_s * 10 + 60)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:          # reported, never fatal for the bench line
+        return {"error": str(e)[:200]}
 
 
 def blas_threads():
@@ -325,11 +340,50 @@ def run_ours(args, rank, local, world):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    # ---- the same workload: explicit coordinates (SoA) and the plain FP64 path
+    res["config_layouts"] = layouts_and_fp64(args, pr, y, sg, flush, dev)
     if rank == 0 and not args.no_cpu_baseline:
-        rate, fits, secs = oracle_rate(pr)
+        rate, fits, secs, ref = oracle_rate(pr, want_result=True)
+        one = oracle_rate_one_core()
         res["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-                               "sample": f"{fits} whole FP64 oracle fits of the same workload ({secs:.1f} s)"}
+                               "sample": f"{fits} whole FP64 oracle fits of the same workload ({secs:.1f} s)",
+                               "one_core": one}
+        rel = lambda a: float(np.max(np.abs(np.asarray(a) - ref["popt"]) / np.maximum(np.abs(ref["popt"]), 1.0)))
+        res["popt_rel_err_vs_oracle"] = {"mixed_grid": rel(out["popt"]),
+                                         "plain_fp64_grid": rel(res["config_layouts"]["plain_fp64_popt"])}
+        res["config_layouts"].pop("plain_fp64_popt")
+    else:
+        res["config_layouts"].pop("plain_fp64_popt")
     return res
+
+
+def layouts_and_fp64(args, pr, y, sg, flush, dev):
+    """Headline workload through explicit pixel coordinates (x, y rows FP32)
+    and through the plain FP64 path (grid), a few timed fits each."""
+    import torch
+    from paper_2208_12187_gb300 import gbfit, synth
+    Xc = torch.as_tensor(pr.coords().astype(np.float32)).to(dev)            # [2, m]
+    out = {}
+    for name, kw in (("mixed_explicit_soa2", dict(xdata=Xc, grid_wh=None, precision="mixed")),
+                     ("plain_fp64_grid", dict(xdata=None, grid_wh=(W, H), precision="fp64"))):
+        f = lambda: gbfit.curve_fit(pr.model, kw["xdata"], y, pr.p0, sigma=sg, lb=pr.lb, ub=pr.ub,
+                                    grid_wh=kw["grid_wh"], precision=kw["precision"], **TOL)
+        f()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms, pts, r = 0.0, 0.0, None
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0.record()
+            r = f()
+            e1.record()
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            pts += M * r["nfev"]
+        out[name] = {"value": pts / (ms / 1e3), "unit": UNIT, "ms_per_fit": ms / 3, "nfev": r["nfev"]}
+        if name == "plain_fp64_grid":
+            out["plain_fp64_popt"] = r["popt"]
+    return out
 
 
 def run_sweep(args):
@@ -367,11 +421,16 @@ def run_sweep(args):
             st = gbfit.stats()
             it = max(st["passes"], 1)
             cyc = st["phase_cycles"]
+            bpp = 8 if prec == "mixed" else 16
+            busy_ms = st["loop_busy_ms"] / max(st["loop_ctas"], 1)        # average CTA, per fit
             tile_share = cyc["tile"] / max(sum(v for k, v in cyc.items() if not k.startswith(("n_", "spare", "j32", "refine", "eig_", "comb_", "gn"))), 1)
             print(json.dumps({"mode": "sweep", "model": "gauss1d", "m": m, "precision": prec, "nfev": nf,
                               "fit_ms": ms / steps, "point_iters_per_s": pts / (ms / 1e3),
                               "bytes_per_point": 8 if prec == "mixed" else 16,
-                              "hbm_gbs_equiv": pts * (8 if prec == "mixed" else 16) / (ms / 1e3) / 1e9,
+                              "hbm_gbs_equiv": pts * bpp / (ms / 1e3) / 1e9,
+                              "hbm_frac_of_fit_time": pts * bpp / (ms / 1e3) / 1e9 / HBM_PEAK_GBS,
+                              "pass_gbs": m * nf * bpp / (busy_ms / 1e3) / 1e9,
+                              "pass_hbm_frac": m * nf * bpp / (busy_ms / 1e3) / 1e9 / HBM_PEAK_GBS,
                               "own_tile_cycles_per_iter": cyc["tile"] / it,
                               "step_cycles_per_iter": (cyc["logic"] + cyc["eigen"] + cyc["gn_path"] + cyc["step"] + cyc["prep"] + cyc["finish"]) / it,
                               "combine_cycles_per_iter": cyc["combine"] / it}))
@@ -433,19 +492,35 @@ def run_batch(args):
     # popt error of the batched mixed fits: against the FP64 oracle (sample) and the plain FP64 GPU path
     K = min(args.oracle_sample, bt.nfits)
     refs = [trf.curve_fit_problem(bt.fit(k).astype(np.float64), **TOL) for k in range(K)]
-    e_or = np.array([relerr_vec(out["popt"][k], refs[k]["popt"]) for k in range(K)])
+    # the double exponential is symmetric under (a1, t1) <-> (a2, t2): compare
+    # with t1 <= t2 on both sides
+    canon = lambda p: np.asarray(p)[[2, 3, 0, 1, 4]] if p[1] > p[3] else np.asarray(p)
+    e_or = np.array([relerr_vec(canon(out["popt"][k]), canon(refs[k]["popt"])) for k in range(K)])
+    # ill-conditioned: some parameter not determined to 10 % (oracle standard error)
+    ill = np.array([bool(np.max(np.sqrt(np.abs(np.diag(r["pcov"]))) / np.maximum(np.abs(r["popt"]), 1e-300)) > 0.1)
+                    for r in refs])
+    # where popt differs by more than 1e-6: cost of the GPU's stopping point
+    # relative to the oracle's (<= 0: the GPU stopped at an equal or lower cost)
+    big = np.where(e_or > 1e-6)[0]
+    dcost = np.array([(out["cost"][k] - refs[k]["cost"]) / refs[k]["cost"] for k in big])
     # the same difference in units of each parameter's standard error (oracle pcov):
     # numerical error against the statistical uncertainty of the fit
     e_se = np.array([float(np.max(np.abs(out["popt"][k] - refs[k]["popt"]) /
                                   np.sqrt(np.maximum(np.abs(np.diag(refs[k]["pcov"])), 1e-300)))) for k in range(K)])
-    e_pl = np.array([relerr_vec(out["popt"][k], plain[k]) for k in range(S)])
+    e_pl = np.array([relerr_vec(canon(out["popt"][k]), canon(plain[k])) for k in range(S)])
     err = lambda e: {"max": float(e.max()), "p50": float(np.median(e)), "frac_le_1e-6": float(np.mean(e <= 1e-6))}
     print(json.dumps({"mode": "batch", "model": "dexp", "nfits": bt.nfits, "total_points": int(bt.offsets[-1]),
                       "m": "log-uniform [200, 200000]", "data": "synthetic fp32", "generate_s": gen_s,
                       "autotune_s": tune_s, "tuned_shapes_log2m_to_tile_group": shapes, "mixed_batched": res,
                       "plain_fp64_one_at_a_time": {"fits_per_s": plain_fps, "sample": S},
                       "batched_over_plain_fits_per_s": res["fits_per_s"] / plain_fps,
-                      "popt_rel_err_vs_oracle": {**err(e_or), "sample": K},
+                      "popt_rel_err_vs_oracle": {**err(e_or), "sample": K,
+                                                 "ill_conditioned_flagged": int(ill.sum()),
+                                                 "well_conditioned": err(e_or[~ill]) if (~ill).any() else None,
+                                                 "where_above_1e-6_cost_rel_diff": {
+                                                     "n": int(big.size),
+                                                     "max": float(dcost.max()) if big.size else None,
+                                                     "frac_le_1e-9": float(np.mean(dcost <= 1e-9)) if big.size else None}},
                       "popt_err_in_standard_errors_vs_oracle": {"max": float(e_se.max()), "p50": float(np.median(e_se)),
                                                                 "frac_le_1e-3": float(np.mean(e_se <= 1e-3))},
                       "popt_rel_err_vs_plain_fp64_gpu": {**err(e_pl), "sample": S}}))
@@ -603,8 +678,13 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
     ap.add_argument("--serve-slots", type=int, default=4096)
     ap.add_argument("--serve-rounds", type=int, default=4)
-    ap.add_argument("--serve-rates", default="0.25,0.5,0.8,0.95")
+    ap.add_argument("--serve-rates", default="0.1,0.25,0.5,0.8,1.0,1.2")
+    ap.add_argument("--oracle-rate-only", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_rate_only is not None:
+        rate, fits, secs = oracle_rate(make_problem(0), budget_s=args.oracle_rate_only, max_fits=4)
+        print(json.dumps({"value": rate, "unit": UNIT, "cores": 1, "sample": f"{fits} fits ({secs:.1f} s)"}))
+        return
     if args.sweep:
         return run_sweep(args)
     if args.batch:

@@ -349,6 +349,8 @@ typedef struct gbfit_stats {
                                  wait for the device, result copy)                    */
     double loop_busy_ms;      /* loop kernel, summed over CTAs: time in rounds' work    */
     double loop_wait_ms;      /* loop kernel, summed over CTAs: time at round barriers  */
+    int64_t loop_ctas;        /* CTAs summed over loop-kernel launches (busy / ctas = the
+                                 average CTA's time in work per launch)               */
 } gbfit_stats;
 
 /* Zero the counters. */

@@ -384,6 +384,7 @@ int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::
         g_stats.eval_launches += eval_launches;
         g_stats.loop_busy_ms += acct[0] * 1e-6;
         g_stats.loop_wait_ms += acct[1] * 1e-6;
+        g_stats.loop_ctas += c->grid_p[prec];
         for (size_t f = 0; f < nf; ++f) {
             for (int k = 0; k < 24; ++k) g_stats.phase_cycles[k] += hr[f].trace[k];
             g_stats.passes += hr[f].nfev;

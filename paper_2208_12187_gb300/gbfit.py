@@ -61,7 +61,7 @@ class Stats(ctypes.Structure):
                 ("graph_rounds", ctypes.c_int64), ("passes", ctypes.c_int64), ("point_passes", ctypes.c_double),
                 ("eval_ms", ctypes.c_double), ("eval_launches", ctypes.c_int64),
                 ("phase_cycles", ctypes.c_double * 24), ("host_ms", ctypes.c_double),
-                ("loop_busy_ms", ctypes.c_double), ("loop_wait_ms", ctypes.c_double)]
+                ("loop_busy_ms", ctypes.c_double), ("loop_wait_ms", ctypes.c_double), ("loop_ctas", ctypes.c_int64)]
 
 PHASES = ["tile", "combine", "logic", "eigen", "comb_fence", "step", "prep", "finish", "comb_group", "comb_final",
           "eig_warm", "eig_j32", "eig_ns", "eig_rr", "j32_sweeps", "refine_passes", "gn_path", "n_gn", "n_eig",

@@ -263,7 +263,9 @@ class ServeStream:
         are i.i.d., so any prefix is a valid draw of the same recipe);
       * gauss2d: a W x W pixel grid, W taken from a sqrt(2) ladder between
         sqrt(m_lo) and sqrt(m_hi), the rung nearest sqrt(m) in log scale
-        (so 2D sizes are discrete, within a factor 2^(1/4) of the draw).
+        (so 2D sizes are discrete, within a factor 2^(1/4) of the draw);
+        widths sx, sy = W U(0.05, 0.15), centre uniform in the central half,
+        A = 980, c = 20, theta = 0.4 (the 1024^2 recipe otherwise).
     Arrival times are drawn separately (`arrivals`).
     """
 
@@ -284,7 +286,10 @@ class ServeStream:
         self.ladder = sorted({int(round(w_lo * 2.0 ** (i / 2.0))) for i in range(k + 1)} | {int(math.floor(w_hi))})
         for v in range(n_data):
             for W in self.ladder:
-                self.data[(MODEL_GAUSS2D, v, W)] = gauss2d_grid(W, seed=3000 + 97 * v + W, dtype=dtype)
+                r2 = np.random.default_rng(3000 + 97 * v + W)
+                truth = [980.0, W * r2.uniform(0.25, 0.75), W * r2.uniform(0.25, 0.75),
+                         W * r2.uniform(0.05, 0.15), W * r2.uniform(0.05, 0.15), 0.4, 20.0]
+                self.data[(MODEL_GAUSS2D, v, W)] = gauss2d_grid(W, seed=3000 + 97 * v + W, truth=truth, dtype=dtype)
         for k2 in range(n_requests):
             if self.models[k2] == MODEL_GAUSS2D:
                 lw = 0.5 * math.log(float(self.m[k2]))

@@ -286,6 +286,34 @@ def test_autotune_installs_valid_shapes_and_fits_still_match():
     assert np.array_equal(gbfit.tune_get()["tile_points"], saved["tile_points"])
 
 
+def test_sigma_none_equals_sigma_ones():
+    """Config 0 passes sigma = None and sigma = ones: Eqs. easy_jac / easy_res
+    with S = I leave J and r unchanged, so the fits must agree exactly."""
+    pr = synth.gauss1d(10_000, seed=0)
+    ones = np.ones(pr.m)
+    for prec, dt in (("fp64", torch.float64), ("mixed", torch.float32)):
+        a = gbfit.curve_fit(pr.model, dev(pr.x, dt), dev(pr.y, dt), pr.p0, precision=prec, **TOL)
+        b = gbfit.curve_fit(pr.model, dev(pr.x, dt), dev(pr.y, dt), pr.p0, sigma=dev(ones, dt), precision=prec,
+                            **TOL)
+        assert relerr(a["popt"], b["popt"]) <= 1e-12
+        assert a["nfev"] == b["nfev"]
+        np.testing.assert_allclose(a["pcov"], b["pcov"], rtol=1e-10)
+
+
+def test_explicit_coordinates_equal_implicit_grid():
+    """Config 1's two layouts: pixel coordinates passed as x, y rows give the
+    fit of the implicit grid (mixed: within the mixed tolerance of each other
+    and of the oracle)."""
+    pr = synth.gauss2d_grid(256, seed=8, dtype=np.float32)
+    ref = trf.curve_fit_problem(pr.astype(np.float64), **TOL)
+    g = gpu_fit(pr, "mixed", dtype=torch.float32, **TOL)
+    Xc = pr.coords().astype(np.float32)
+    e = gbfit.curve_fit(pr.model, dev(Xc), dev(pr.y, torch.float32), pr.p0, sigma=dev(pr.sigma, torch.float32),
+                        lb=pr.lb, ub=pr.ub, precision="mixed", **TOL)
+    assert relerr(g["popt"], ref["popt"]) <= 1e-6
+    assert relerr(e["popt"], ref["popt"]) <= 1e-6
+
+
 # ------------------------------------------------------------------ edge cases
 def test_minimum_size_fit_m_equals_n():
     rng = np.random.default_rng(0)
