@@ -175,13 +175,61 @@ def test_x_scale_jac_matches_oracle():
     assert relerr(out["popt"], ref["popt"]) <= 1e-8
 
 
+def test_x_scale_vector_and_absolute_sigma_match_oracle():
+    """R7 with a numeric x_scale (D = 1/x_scale) and R13 with absolute_sigma."""
+    pr = synth.gauss1d(5000, seed=4, with_sigma=True)
+    pr.sigma = np.random.default_rng(4).uniform(0.05, 0.2, pr.m)
+    xs = np.array([2.0, 0.5, 0.25, 1.0])
+    ref = trf.curve_fit_problem(pr, x_scale=xs, absolute_sigma=True, **TOL)
+    out = gpu_fit(pr, "fp64", x_scale=xs, absolute_sigma=True, **TOL)
+    assert out["nfev"] == ref["nfev"]
+    assert relerr(out["popt"], ref["popt"]) <= 1e-8
+    np.testing.assert_allclose(out["pcov"], ref["pcov"], rtol=1e-6, atol=1e-12 * np.max(np.abs(ref["pcov"])))
+
+
+def test_batch_soa2_sigma_and_1d_sigma_match_oracle():
+    """Batched fits through explicit 2D coordinates with sigma (mixed) and 1D
+    fits with sigma (plain FP64): each fit against the oracle."""
+    fits = [synth.gauss2d_grid(48 + 8 * k, seed=20 + k, dtype=np.float32, layout=synth.LAYOUT_SOA2) for k in range(5)]
+    off = np.concatenate([[0], np.cumsum([f.m for f in fits])])
+    X = np.concatenate([f.x for f in fits], axis=1).astype(np.float32)
+    Y = np.concatenate([f.y for f in fits]).astype(np.float32)
+    S = np.concatenate([f.sigma for f in fits]).astype(np.float32)
+    P0 = np.stack([f.p0 for f in fits])
+    out = gbfit.curve_fit_batch(gbfit.MODEL_GAUSS2D, off, dev(X), dev(Y), P0, sigma=dev(S), lb=fits[0].lb,
+                                ub=fits[0].ub, precision="mixed", **TOL)
+    for k, f in enumerate(fits):
+        ref = trf.curve_fit_problem(f.astype(np.float64), **TOL)
+        assert relerr(out["popt"][k], ref["popt"]) <= 1e-6, k
+    fits = [synth.gauss1d(3000 + 1111 * k, seed=30 + k, with_sigma=True) for k in range(4)]
+    for f in fits:
+        f.sigma = np.random.default_rng(f.m).uniform(0.05, 0.3, f.m)
+    off = np.concatenate([[0], np.cumsum([f.m for f in fits])])
+    out = gbfit.curve_fit_batch(gbfit.MODEL_GAUSS1D, off, dev(np.concatenate([f.x for f in fits])),
+                                dev(np.concatenate([f.y for f in fits])), np.stack([f.p0 for f in fits]),
+                                sigma=dev(np.concatenate([f.sigma for f in fits])), precision="fp64", **TOL)
+    for k, f in enumerate(fits):
+        ref = trf.curve_fit_problem(f, **TOL)
+        assert out["nfev"][k] == ref["nfev"]
+        assert relerr(out["popt"][k], ref["popt"]) <= 1e-8, k
+
+
 # ------------------------------------------------------------------ whole fits, mixed precision
 MIXED_FITS = [
     ("gauss1d_m1e4", lambda: synth.gauss1d(10_000, seed=0), None),
     ("dexp", lambda: synth.dexp(20_000, seed=5, truth=[4.0, 0.8, 6.0, 9.0, 0.5], dtype=np.float64), None),
     ("gauss2d_256_grid", lambda: synth.gauss2d_grid(256, seed=1, dtype=np.float64), None),
     ("gauss2d_soa", lambda: synth.gauss2d_grid(128, seed=3, dtype=np.float64, layout=synth.LAYOUT_SOA2), None),
+    ("gauss1d_sigma", lambda: with_sigma(synth.gauss1d(30_000, seed=6), 6), None),
+    ("dexp_sigma", lambda: with_sigma(synth.dexp(20_000, seed=5, truth=[4.0, 0.8, 6.0, 9.0, 0.5],
+                                                 dtype=np.float64), 7), None),
 ]
+
+
+def with_sigma(pr, seed):
+    """The same problem with per-point uncertainties U(0.05, 0.3) (App. C weighting)."""
+    import dataclasses
+    return dataclasses.replace(pr, sigma=np.random.default_rng(seed).uniform(0.05, 0.3, pr.m))
 
 
 @pytest.mark.parametrize("name,make,_", MIXED_FITS)
