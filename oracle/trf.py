@@ -28,6 +28,10 @@ follows.  Where the paper is silent or garbled the reading taken is one of:
   R12 r = h - y (Eq. residual).
   R13 pcov = V diag(1/s^2) V^T of the unscaled J at the solution (R10 cutoff),
       times 2 f / (m - n) unless absolute_sigma.
+  R14 Robust losses (named in Section 5, not stated): cost 1/2 C^2 sum rho(z),
+      z = (r/C)^2; the method runs on rows rescaled to the loss's gradient and
+      Gauss-Newton Hessian (see reduce.robust_rows); pcov from the rescaled J
+      and the robust cost.
 
 Outline of one fit (Algorithm 1, Section 2):
   x <- x0, Delta <- Delta0                                   R6
@@ -349,7 +353,8 @@ def covariance(J, cost, m, n, absolute_sigma):
 
 
 def curve_fit(model, X, y, sigma=None, p0=None, lb=None, ub=None, ftol=1e-8, xtol=1e-8,
-              gtol=1e-8, max_nfev=None, x_scale=1.0, absolute_sigma=False, record=False):
+              gtol=1e-8, max_nfev=None, x_scale=1.0, absolute_sigma=False, record=False,
+              loss="linear", f_scale=1.0):
     """Fit model `model` to (X, y) with per-point sigma by the TRF method.
 
     Returns a dict: popt, pcov, cost, nfev, njev, status and (if record) the
@@ -383,7 +388,11 @@ def curve_fit(model, X, y, sigma=None, p0=None, lb=None, ub=None, ftol=1e-8, xto
     w = _reduce.weights(sigma, m)
     jac_scale = isinstance(x_scale, str) and x_scale == "jac"
 
-    f, g, _, r, J = _reduce.evaluate(model, X, y, w, x)
+    if loss not in _reduce.LOSSES:
+        raise ValueError(f"unknown loss {loss!r}")
+    if not f_scale > 0:
+        raise ValueError("f_scale must be > 0")
+    f, g, _, r, J = _reduce.evaluate(model, X, y, w, x, loss, f_scale)
     nfev, njev = 1, 1
     hist = []
     out = dict(nfev=nfev, njev=njev)
@@ -428,7 +437,7 @@ def curve_fit(model, X, y, sigma=None, p0=None, lb=None, ub=None, ftol=1e-8, xto
         x_new = x + step
         if bounded:
             x_new = make_strictly_feasible(x_new, lb, ub)
-        f_new, g_new, _, r_new, J_new = _reduce.evaluate(model, X, y, w, x_new)
+        f_new, g_new, _, r_new, J_new = _reduce.evaluate(model, X, y, w, x_new, loss, f_scale)
         nfev += 1
         actual = f - f_new
         s_norm = float(np.linalg.norm(s_h))
