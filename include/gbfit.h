@@ -85,6 +85,18 @@ extern "C" {
                                 cancellation-free difference form), tile sums promoted to
                                 FP64; combine, n x n solve, ratio and tests in FP64            */
 
+/* ---- robust losses (the paper's Section 5 names "various loss functions"
+ * without stating them; the library's reading): the cost becomes
+ * f = 1/2 C^2 sum rho(z_i), z_i = (r_i / C)^2 with C = f_scale, and the method
+ * runs on rows rescaled to the loss's gradient and Gauss-Newton Hessian
+ * (J_i * sqrt(s_i), r_i * rho'(z_i) / sqrt(s_i), s_i = rho' + 2 z rho'').
+ * pcov then comes from the rescaled Jacobian and the robust cost. ---- */
+#define GBFIT_LOSS_LINEAR   0  /* rho = z                                  */
+#define GBFIT_LOSS_SOFT_L1  1  /* rho = 2 (sqrt(1 + z) - 1)                */
+#define GBFIT_LOSS_HUBER    2  /* rho = z (z <= 1), 2 sqrt(z) - 1 beyond   */
+#define GBFIT_LOSS_CAUCHY   3  /* rho = ln(1 + z)                          */
+#define GBFIT_LOSS_ARCTAN   4  /* rho = arctan(z)                          */
+
 typedef struct gbfit_options {
     double ftol, xtol, gtol;   /* termination tolerances (defaults 1e-8)                         */
     int max_nfev;              /* <= 0: 100 * n                                                  */
@@ -94,7 +106,9 @@ typedef struct gbfit_options {
     int precision;             /* GBFIT_PREC_*                                                   */
     int tile_points;           /* points per reduction tile; 0 = library choice                  */
     int group_tiles;           /* tiles per first-level combine group; 0 = library choice        */
-    int reserved[3];
+    int loss;                  /* GBFIT_LOSS_* (default linear)                                  */
+    int reserved[1];
+    double f_scale;            /* robust loss scale C > 0; 0 reads as 1                          */
 } gbfit_options;
 
 /* Library version (GBFIT_VERSION). */
@@ -262,6 +276,8 @@ typedef struct gbfit_request {
     double ftol, xtol, gtol;
     int max_nfev;
     uint64_t tag;                        /* returned with the result                            */
+    int loss;                            /* GBFIT_LOSS_* (0 = linear)                           */
+    double f_scale;                      /* robust loss scale; 0 reads as 1                     */
 } gbfit_request;
 
 typedef struct gbfit_result_rec {

@@ -288,6 +288,8 @@ int check_opts(const gbfit_options* o, int n) {
             if (!(o->x_scale[i] > 0) || !std::isfinite(o->x_scale[i])) return fail(GBFIT_E_INVALID_ARG, "x_scale[%d] must be > 0", i);
     if (o->tile_points < 0 || o->tile_points > (1 << 24)) return fail(GBFIT_E_INVALID_ARG, "tile_points out of range");
     if (o->group_tiles < 0 || o->group_tiles > 1024) return fail(GBFIT_E_INVALID_ARG, "group_tiles out of range");
+    if (o->loss < GBFIT_LOSS_LINEAR || o->loss > GBFIT_LOSS_ARCTAN) return fail(GBFIT_E_INVALID_ARG, "unknown loss %d", o->loss);
+    if (!(o->f_scale >= 0) || !std::isfinite(o->f_scale)) return fail(GBFIT_E_INVALID_ARG, "f_scale must be > 0");
     return GBFIT_OK;
 }
 
@@ -296,6 +298,7 @@ gbfit_options defaults() {
     memset(&o, 0, sizeof o);
     o.ftol = o.xtol = o.gtol = 1e-8;
     o.precision = GBFIT_PREC_MIXED;
+    o.f_scale = 1.0;
     return o;
 }
 
@@ -447,6 +450,8 @@ int fill_desc(FitDesc& d, const FitArgs& a, const gbfit_options& o, bool bounded
     }
     d.ftol = o.ftol; d.xtol = o.xtol; d.gtol = o.gtol;
     d.absolute_sigma = o.absolute_sigma;
+    d.loss = o.loss;
+    d.f_scale = o.f_scale > 0 ? o.f_scale : 1.0;
     return GBFIT_OK;
 }
 
@@ -1169,6 +1174,8 @@ int gbfit_server_submit(gbfit_server* s, const gbfit_request* r, uint64_t* ticke
               r->p0, r->has_bounds ? r->lb : nullptr, r->has_bounds ? r->ub : nullptr};
     bool bounded;
     if ((rc = check_params(a, &bounded))) return rc;
+    if (r->loss < GBFIT_LOSS_LINEAR || r->loss > GBFIT_LOSS_ARCTAN) return fail(GBFIT_E_INVALID_ARG, "unknown loss %d", r->loss);
+    if (!(r->f_scale >= 0) || !std::isfinite(r->f_scale)) return fail(GBFIT_E_INVALID_ARG, "f_scale must be > 0");
     size_t need = req_data_bytes(*r);
     int tp, gt;
     multi_shape(r->model_id, s->prec, r->m, 0, 0, &tp, &gt);
@@ -1247,6 +1254,8 @@ int gbfit_server_step(gbfit_server* s, int* n_active, int* n_queued) {
         o.xtol = r.xtol > 0 ? r.xtol : 1e-8;
         o.gtol = r.gtol > 0 ? r.gtol : 1e-8;
         o.max_nfev = r.max_nfev;
+        o.loss = r.loss;
+        o.f_scale = r.f_scale;
         FitArgs a{r.model_id, n, r.x_layout, r.dtype, r.m, r.grid_w, nullptr, nullptr, nullptr, nullptr,
                   r.p0, r.has_bounds ? r.lb : nullptr, r.has_bounds ? r.ub : nullptr};
         bool bounded = false;

@@ -19,6 +19,9 @@ enum DType { F32 = 0, F64 = 1 };
 enum WKind { W_NONE = 0, W_ARRAY = 1, W_SIGMA = 2 };
 enum RunState { RS_RUNNING = 0, RS_DONE = 1 };
 enum Phase { PH_INIT = 0, PH_TRIAL = 1 };
+enum Loss { LOSS_LINEAR = 0, LOSS_SOFT_L1, LOSS_HUBER, LOSS_CAUCHY, LOSS_ARCTAN };
+// pass-constant slots holding the robust loss's C^2 and 1/C^2
+constexpr int PF_C2 = PF - 1, PF_IC2 = PF - 2, PD_C2 = PD - 1, PD_IC2 = PD - 2;
 
 // Accumulator slot layout for a model with n parameters (NT = n(n+1)/2):
 //   [0, NT)        packed upper triangle of J'^T J' at the evaluated point
@@ -44,6 +47,8 @@ struct FitDesc {
     double lb[NMAX], ub[NMAX], xscale[NMAX];
     double ftol, xtol, gtol;
     int absolute_sigma, group_tiles;
+    int loss, pad2;
+    double f_scale;        // robust loss scale C (1 for the linear loss)
 };
 
 // Mutable per-fit state, kept on the device across iterations.

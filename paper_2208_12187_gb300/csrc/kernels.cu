@@ -1,877 +1,19 @@
-// Device kernels of libgbfit.
-//
-//   eval_round_kernel<PREC>  one trust-region iteration for every running fit:
-//       each CTA takes (fit, tile) work items, evaluates model, residual and
-//       Jacobian row per point in registers, reduces J^T J, J^T r and cost
-//       sums over its tile (never writing J), and writes one tile partial.
-//       The last CTA of a group of tiles combines the group (FP64, fixed
-//       order); the last group of a fit combines the fit and runs the
-//       trust-region step for it (trf_step), which prepares the next
-//       evaluation point.  No CTA waits for another: the hand-off is an
-//       atomic arrival counter (last arriver continues).
-//   fit_loop_kernel<PREC>  the same rounds in one cooperative launch,
-//       separated by a grid-wide barrier (bounded waits), until no fit runs
-//       or the round cap is reached.
+// Device kernels of libgbfit that do not depend on the precision mode, and
+// the host-side handles that pick a precision's instantiation.
 //   stage_weights_kernel  w = 1/sigma in FP64 for the plain path.
 //   tr_subproblem_kernel  one subproblem solve (test entry point).
+//   synth_fill_kernel     the autotuner's calibration data.
 #include <cstdint>
-#include <type_traits>
 #include <cuda_runtime.h>
 #include "gbfit_internal.cuh"
 #include "models.cuh"
 #include "trf_device.cuh"
 #include "trf_step.cuh"
+#include "kernels.cuh"
 
 namespace gbfit {
 
 __constant__ double c_synth_truth[4][NMAX];   // autotuner calibration parameters per model
-
-// ------------------------------------------------------------------ warp/block reduction
-// Reduce-scatter across the warp: after 5 halvings lane l holds the warp sum
-// of ceil(K/32) slots.  Costs about K shuffles instead of 5 K.
-template <int K, typename T>
-struct WarpRS {
-    static constexpr int H1 = (K + 1) / 2, H2 = (H1 + 1) / 2, H3 = (H2 + 1) / 2, H4 = (H3 + 1) / 2,
-                         H5 = (H4 + 1) / 2;
-    template <int C, int H>
-    __device__ __forceinline__ static void level(T (&v)[K], int lane, int off) {
-        bool up = lane & off;
-#pragma unroll
-        for (int i = 0; i < H; ++i) {
-            T a = v[i];
-            T b = (i + H < C) ? v[i + H] : T(0);
-            T send = up ? a : b;
-            T keep = up ? b : a;
-            v[i] = keep + __shfl_xor_sync(FULL, send, off);
-        }
-    }
-    // original slot held in v[i] by `lane` after all levels, or -1 for padding:
-    // unwind the halvings, checking the index against each level's count.
-    __device__ __forceinline__ static int slot(int lane, int i) {
-        int k = i + ((lane & 1) ? H5 : 0);
-        if (k >= H4) return -1;
-        k += (lane & 2) ? H4 : 0;
-        if (k >= H3) return -1;
-        k += (lane & 4) ? H3 : 0;
-        if (k >= H2) return -1;
-        k += (lane & 8) ? H2 : 0;
-        if (k >= H1) return -1;
-        k += (lane & 16) ? H1 : 0;
-        return k < K ? k : -1;
-    }
-    __device__ __forceinline__ static void run(T (&v)[K], int lane) {
-        level<K, H1>(v, lane, 16);
-        level<H1, H2>(v, lane, 8);
-        level<H2, H3>(v, lane, 4);
-        level<H3, H4>(v, lane, 2);
-        level<H4, H5>(v, lane, 1);
-    }
-};
-
-// Block sum of acc[K] over EVAL_THREADS threads; thread k < K gets slot k in out.
-template <int K, typename T>
-__device__ __forceinline__ void block_reduce(T (&acc)[K], T* red /*[8][K]*/, T& out) {
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpRS<K, T>::run(acc, lane);
-#pragma unroll
-    for (int i = 0; i < WarpRS<K, T>::H5; ++i) {
-        int s = WarpRS<K, T>::slot(lane, i);
-        if (s >= 0) red[warp * K + s] = acc[i];
-    }
-    __syncthreads();
-    if (threadIdx.x < K) {
-        T sum = red[threadIdx.x];
-#pragma unroll
-        for (int w = 1; w < EVAL_THREADS / 32; ++w) sum += red[w * K + threadIdx.x];
-        out = sum;
-    }
-}
-
-// ------------------------------------------------------------------ point loops
-template <typename T> __device__ __forceinline__ T ldg_t(const void* p, int64_t i) { return __ldg((const T*)p + i); }
-
-struct PointCoord {
-    // incremental pixel coordinates for the implicit grid (W, H < 2^31)
-    int X, Y, W;
-    __device__ void init(int64_t i, int64_t w) { W = (int)w; Y = (int)(i / w); X = (int)(i - (int64_t)Y * w); }
-    __device__ void advance(int step) {
-        X += step;
-        if (X >= W) { if (W >= step) { X -= W; Y += 1; } else { Y += X / W; X = X % W; } }
-    }
-};
-
-template <int PREC> struct AccT { using T = double; };
-template <> struct AccT<PREC_MIXED> { using T = float; };
-
-// One point: model value, residual and Jacobian row in registers, added to
-// the Gram / gradient / cost accumulators (slot layout in gbfit_internal.cuh).
-template <class M, int PREC, int WK>
-__device__ __forceinline__ void accum_point(const float* pfl, const double* pdl, typename AccT<PREC>::T X,
-                                            typename AccT<PREC>::T Y, typename AccT<PREC>::T yv,
-                                            typename AccT<PREC>::T sv, bool check,
-                                            typename AccT<PREC>::T (&acc)[n_acc(M::N, PREC)], int& bad) {
-    using AT = typename AccT<PREC>::T;
-    constexpr int N = M::N;
-    constexpr int NT = n_tri(N);
-    AT w = AT(1);
-    if (WK == W_ARRAY) w = sv;
-    if (WK == W_SIGMA) {
-        if (check && !(sv > AT(0) && isfinite(sv))) bad = 1;
-        if (PREC == PREC_MIXED) w = __fdividef(1.0f, float(sv)); else w = AT(1) / sv;
-    }
-    if (check) {
-        if (!isfinite(X) || !isfinite(Y) || !isfinite(yv)) bad = 1;
-        if (WK == W_ARRAY && !(w > AT(0) && isfinite(w))) bad = 1;
-    }
-    AT Jw[N];
-    if constexpr (PREC == PREC_MIXED) {
-        float hb, dh, J[N];
-        M::eval_mixed(pfl, X, Y, hb, dh, J);
-        float r = w * (hb - yv);
-        float dr = w * dh;
-        float rn = r + dr;
-#pragma unroll
-        for (int a = 0; a < N; ++a) Jw[a] = w * J[a];
-        int idx = 0;
-#pragma unroll
-        for (int a = 0; a < N; ++a)
-#pragma unroll
-            for (int b = a; b < N; ++b) { acc[idx] = fmaf(Jw[a], Jw[b], acc[idx]); ++idx; }
-#pragma unroll
-        for (int a = 0; a < N; ++a) acc[NT + a] = fmaf(Jw[a], rn, acc[NT + a]);
-        acc[NT + N] = fmaf(rn, rn, acc[NT + N]);
-        acc[NT + N + 1] = fmaf(dr, fmaf(2.0f, r, dr), acc[NT + N + 1]);
-    } else {
-        double h, J[N];
-        M::eval_plain(pdl, X, Y, h, J);
-        double r = w * (h - yv);
-#pragma unroll
-        for (int a = 0; a < N; ++a) Jw[a] = w * J[a];
-        int idx = 0;
-#pragma unroll
-        for (int a = 0; a < N; ++a)
-#pragma unroll
-            for (int b = a; b < N; ++b) { acc[idx] = fma(Jw[a], Jw[b], acc[idx]); ++idx; }
-#pragma unroll
-        for (int a = 0; a < N; ++a) acc[NT + a] = fma(Jw[a], r, acc[NT + a]);
-        acc[NT + N] = fma(r, r, acc[NT + N]);
-    }
-}
-
-// Two points at once with packed FP32 (mixed precision): model, residual
-// and weights packed; accumulators packed (ACC = float2, two partial sums
-// per slot) or scalar (ACC = float, both points added to one sum).
-template <class M, int WK, typename ACC>
-__device__ __forceinline__ void accum_point2(const float* pfl, float2 X, float2 Y, float2 yv, float2 sv, bool check,
-                                             ACC (&acc)[n_acc(M::N, PREC_MIXED)], int& bad) {
-    constexpr int N = M::N;
-    constexpr int NT = n_tri(N);
-    float2 w = bc(1.0f);
-    if (WK == W_SIGMA) {
-        if (check && !(sv.x > 0.0f && isfinite(sv.x) && sv.y > 0.0f && isfinite(sv.y))) bad = 1;
-        w = make_float2(__fdividef(1.0f, sv.x), __fdividef(1.0f, sv.y));
-    }
-    if (check && !(isfinite(X.x) && isfinite(X.y) && isfinite(Y.x) && isfinite(Y.y) && isfinite(yv.x) &&
-                   isfinite(yv.y))) bad = 1;
-    float2 hb, dh, J[N];
-    M::eval_mixed2(pfl, X, Y, hb, dh, J);
-    float2 r = sub2(hb, yv), dr = dh;
-    if (WK == W_SIGMA) {
-        r = mul2(w, r);
-        dr = mul2(w, dr);
-#pragma unroll
-        for (int a = 0; a < N; ++a) J[a] = mul2(w, J[a]);
-    }
-    float2 rn = add2(r, dr);
-    float2 dc = mul2(dr, fma2(bc(2.0f), r, dr));
-    if constexpr (std::is_same<ACC, float2>::value) {
-        int idx = 0;
-#pragma unroll
-        for (int a = 0; a < N; ++a)
-#pragma unroll
-            for (int b = a; b < N; ++b) { acc[idx] = fma2(J[a], J[b], acc[idx]); ++idx; }
-#pragma unroll
-        for (int a = 0; a < N; ++a) acc[NT + a] = fma2(J[a], rn, acc[NT + a]);
-        acc[NT + N] = fma2(rn, rn, acc[NT + N]);
-        acc[NT + N + 1] = add2(dc, acc[NT + N + 1]);
-    } else {
-        int idx = 0;
-#pragma unroll
-        for (int a = 0; a < N; ++a)
-#pragma unroll
-            for (int b = a; b < N; ++b) {
-                acc[idx] = fmaf(J[a].y, J[b].y, fmaf(J[a].x, J[b].x, acc[idx]));
-                ++idx;
-            }
-#pragma unroll
-        for (int a = 0; a < N; ++a) acc[NT + a] = fmaf(J[a].y, rn.y, fmaf(J[a].x, rn.x, acc[NT + a]));
-        acc[NT + N] = fmaf(rn.y, rn.y, fmaf(rn.x, rn.x, acc[NT + N]));
-        acc[NT + N + 1] += dc.x + dc.y;
-    }
-}
-
-// Points [i0, i1) with register loads (software-pipelined one point ahead).
-template <class M, int PREC, typename DT, int LAYOUT, int WK>
-__device__ __forceinline__ void tile_points(const FitDesc& d, const float* pfl, const double* pdl,
-                                            int64_t i0, int64_t i1, bool check,
-                                            typename AccT<PREC>::T (&acc)[n_acc(M::N, PREC)], int& bad) {
-    using AT = typename AccT<PREC>::T;
-    PointCoord pc;
-    int64_t i = i0 + threadIdx.x;
-    if (LAYOUT == X_GRID) pc.init(i, d.grid_w);
-    AT nX = AT(0), nY = AT(0), ny = AT(0), ns = AT(1);
-    auto load = [&](int64_t j, AT& X, AT& Y, AT& yv, AT& sv) {
-        if (LAYOUT == X_GRID) {
-            X = AT(pc.X); Y = AT(pc.Y);
-            pc.advance(EVAL_THREADS);
-        } else {
-            X = AT(ldg_t<DT>(d.x, j));
-            if (LAYOUT == X_SOA2) Y = AT(ldg_t<DT>(d.x2, j));
-        }
-        yv = AT(ldg_t<DT>(d.y, j));
-        if (WK == W_ARRAY) sv = AT(ldg_t<double>(d.w, j));      // staged FP64 weights
-        if (WK == W_SIGMA) sv = AT(ldg_t<DT>(d.w, j));
-    };
-    if (i < i1) load(i, nX, nY, ny, ns);
-    for (; i < i1; i += EVAL_THREADS) {
-        AT X = nX, Y = nY, yv = ny, sv = ns;
-        if (i + EVAL_THREADS < i1) load(i + EVAL_THREADS, nX, nY, ny, ns);
-        accum_point<M, PREC, WK>(pfl, pdl, X, Y, yv, sv, check, acc, bad);
-    }
-}
-
-// ---- bulk-copy ring (mixed precision, FP32 data): each CTA streams its
-// tile through NST shared-memory stages of CH points per array with
-// cp.async.bulk, completion tracked by one mbarrier per stage, so that
-// about NST-1 chunks (tens of KB per SM) are in flight while the threads
-// compute from shared memory.
-constexpr int NST = 4;
-constexpr int STAGE_FLOATS = 4096;                   // 16 KB per stage, shared by the streamed arrays
-constexpr size_t RING_BYTES = size_t(NST) * STAGE_FLOATS * sizeof(float);
-// Arrays a layout streams (x, x2, y, sigma as present) and the chunk (points
-// per stage) that fills a stage with them: 4096 / 2048 / 1024 points.
-template <int LAYOUT, int WK>
-struct RingShape {
-    static constexpr int NA = (LAYOUT == X_GRID ? 0 : LAYOUT == X_SOA2 ? 2 : 1) + 1 + (WK == W_SIGMA ? 1 : 0);
-    static constexpr int CH = NA <= 1 ? 4096 : NA == 2 ? 2048 : 1024;
-    static constexpr int SX = 0, SX2 = 1;                                   // slots (when present)
-    static constexpr int SY = LAYOUT == X_GRID ? 0 : LAYOUT == X_SOA2 ? 2 : 1;
-    static constexpr int SS = SY + 1;
-};
-constexpr long long MBAR_SPIN_LIMIT = 1ll << 22;     // bounded waits (error flag past the limit)
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    for (long long it = 0; it < MBAR_SPIN_LIMIT; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-// Arrival on a combine counter: one gpu-scope acq_rel atomic by one thread
-// after a CTA barrier releases the CTA's partial-sum stores (cumulativity
-// through the barrier) and, for the last arriver, acquires everyone else's.
-__device__ __forceinline__ int arrive_acq_rel(int* ctr) {
-    int old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(ctr) : "memory");
-    return old;
-}
-
-struct RingState {
-    unsigned long long* bar;     // [NST] full barriers (bulk-copy completion)
-    unsigned long long* empty;   // [NST] empty barriers (one arrival per warp when a stage is consumed)
-    float* buf;                  // [NST][STAGE_FLOATS]
-    unsigned seq;                // chunks consumed by this CTA so far (same in all threads)
-    int* fail;                   // shared flag: a bounded wait gave up
-};
-
-template <class M, int LAYOUT, int WK>
-__device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0, int64_t i1, bool check,
-                                 float (&acc)[n_acc(M::N, PREC_MIXED)], int& bad, RingState& R) {
-    using RS = RingShape<LAYOUT, WK>;
-    constexpr int CH = RS::CH;
-    const int t = threadIdx.x;
-    // streamed arrays in slot order
-    const float* src[4] = {nullptr, nullptr, nullptr, nullptr};
-    if (LAYOUT != X_GRID) src[RS::SX] = (const float*)d.x;
-    if (LAYOUT == X_SOA2) src[RS::SX2] = (const float*)d.x2;
-    src[RS::SY] = (const float*)d.y;
-    if (WK == W_SIGMA) src[RS::SS] = (const float*)d.w;
-    // head up to 16-byte alignment of y; every streamed array must share it
-    int64_t h = (int64_t)(((16 - (reinterpret_cast<uintptr_t>(src[RS::SY] + i0) & 15)) & 15) / 4);
-    bool aligned = true;
-#pragma unroll
-    for (int a = 0; a < RS::NA; ++a)
-        if (reinterpret_cast<uintptr_t>(src[a] + i0 + h) & 15) aligned = false;
-    int64_t a0 = i0 + h;
-    if (!aligned || a0 + 4 > i1) { tile_points<M, PREC_MIXED, float, LAYOUT, WK>(d, pfl, nullptr, i0, i1, check, acc, bad); return; }
-    // whole 16-byte words go through the ring (a short last chunk allowed),
-    // at most 3 trailing points through plain loads
-    const int64_t nring = ((i1 - a0) / 4) * 4;
-    const int nch = (int)((nring + CH - 1) / CH);
-    const int64_t a1 = a0 + nring;
-    auto count = [&](int c) { return (int)min((int64_t)CH, nring - (int64_t)c * CH); };
-    // issue chunk c into its stage once every warp has released the stage's
-    // previous chunk (bounded wait; a timeout marks the ring failed)
-    auto issue = [&](int c) {
-        unsigned g = R.seq + c;
-        int s = g % NST;
-        unsigned long long* bar = R.bar + s;
-        if (g >= (unsigned)NST && !mbar_wait(R.empty + s, ((g / NST) - 1) & 1)) { *R.fail = 1; return; }
-        const unsigned nb = (unsigned)count(c) * sizeof(float);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(bar, nb * RS::NA);
-#pragma unroll
-        for (int a = 0; a < RS::NA; ++a)
-            bulk_load(R.buf + s * STAGE_FLOATS + a * CH, src[a] + a0 + (int64_t)c * CH, nb, bar);
-    };
-    if (t == 0)
-        for (int c = 0; c < nch && c < NST; ++c) issue(c);
-    // head points with plain loads while the first chunks stream in
-    tile_points<M, PREC_MIXED, float, LAYOUT, WK>(d, pfl, nullptr, i0, a0, check, acc, bad);
-    PointCoord pc;
-    if (LAYOUT == X_GRID) pc.init(a0 + (M::PACK == 2 ? 2 * t : t), d.grid_w);
-    // two points per thread step: 1D models on explicit x (packed sums),
-    // the 2D model on the grid or explicit coordinates (scalar sums)
-    constexpr bool PK = M::PACK == 1 && LAYOUT == X_VEC;
-    constexpr bool PK2 = M::PACK == 2 && LAYOUT != X_VEC;
-    constexpr int K = n_acc(M::N, PREC_MIXED);
-    float2 acc2[PK ? K : 1];         // (the head's sums move in, so that acc[] is dead in the loop)
-#pragma unroll
-    for (int k = 0; k < (PK ? K : 1); ++k) acc2[k] = make_float2(PK ? acc[k] : 0.0f, 0.0f);
-    for (int c = 0; c < nch; ++c) {
-        unsigned g = R.seq + c;
-        int s = g % NST;
-        if (!mbar_wait(R.bar + s, (g / NST) & 1)) *R.fail = 1;
-        if (*R.fail) break;
-        const float* B = R.buf + s * STAGE_FLOATS;
-        const int cnt = count(c);
-        if constexpr (PK) {
-#pragma unroll 2
-            for (int k = 2 * t; k < cnt; k += 2 * EVAL_THREADS) {
-                float2 X = *reinterpret_cast<const float2*>(B + RS::SX * CH + k);
-                float2 yv = *reinterpret_cast<const float2*>(B + RS::SY * CH + k);
-                float2 sv = (WK == W_SIGMA) ? *reinterpret_cast<const float2*>(B + RS::SS * CH + k) : bc(1.0f);
-                accum_point2<M, WK, float2>(pfl, X, bc(0.0f), yv, sv, check, acc2, bad);
-            }
-        } else if constexpr (PK2) {
-            for (int k = 2 * t; k < cnt; k += 2 * EVAL_THREADS) {
-                float2 X, Y;
-                if (LAYOUT == X_GRID) {
-                    // pixels k, k + 1 of the chunk: (X, Y) and its right neighbour (next row at the edge)
-                    X.x = float(pc.X);
-                    Y.x = float(pc.Y);
-                    bool wrap = pc.X + 1 >= pc.W;
-                    X.y = wrap ? 0.0f : float(pc.X + 1);
-                    Y.y = wrap ? float(pc.Y + 1) : float(pc.Y);
-                    pc.advance(2 * EVAL_THREADS);
-                } else {
-                    X = *reinterpret_cast<const float2*>(B + RS::SX * CH + k);
-                    Y = *reinterpret_cast<const float2*>(B + RS::SX2 * CH + k);
-                }
-                float2 yv = *reinterpret_cast<const float2*>(B + RS::SY * CH + k);
-                float2 sv = (WK == W_SIGMA) ? *reinterpret_cast<const float2*>(B + RS::SS * CH + k) : bc(1.0f);
-                accum_point2<M, WK, float>(pfl, X, Y, yv, sv, check, acc, bad);
-            }
-        } else
-#pragma unroll 2
-        for (int k = t; k < cnt; k += EVAL_THREADS) {
-            float X = 0.0f, Y = 0.0f;
-            if (LAYOUT == X_GRID) {
-                X = float(pc.X);
-                Y = float(pc.Y);
-                pc.advance(EVAL_THREADS);
-            } else {
-                X = B[RS::SX * CH + k];
-                if (LAYOUT == X_SOA2) Y = B[RS::SX2 * CH + k];
-            }
-            float yv = B[RS::SY * CH + k];
-            float sv = (WK == W_SIGMA) ? B[RS::SS * CH + k] : 1.0f;
-            accum_point<M, PREC_MIXED, WK>(pfl, nullptr, X, Y, yv, sv, check, acc, bad);
-        }
-        __syncwarp();
-        if ((t & 31) == 0) mbar_arrive(R.empty + s);      // this warp is done with the stage
-        if (t == 0 && c + NST < nch) issue(c + NST);
-    }
-    __syncthreads();
-    if (*R.fail) {
-        // give copies still in flight a bounded chance to land before leaving
-        for (int c = 0; c < nch; ++c) { unsigned g = R.seq + c; mbar_wait(R.bar + (g % NST), (g / NST) & 1); }
-    }
-    R.seq += nch;
-    if constexpr (PK) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] = acc2[k].x + acc2[k].y;
-    }
-    // tail with plain loads
-    tile_points<M, PREC_MIXED, float, LAYOUT, WK>(d, pfl, nullptr, a1, i1, check, acc, bad);
-}
-
-// ------------------------------------------------------------------ shared memory of the round kernel
-struct RoundSmem {
-    Engine eng;                        // the launch's engine record (kept out of registers)
-    unsigned long long mbar[NST];
-    unsigned long long mbar_empty[NST];
-    int ring_fail;
-    FitDesc desc;
-    long long t_mark, t_fence, t_group, t_loop;
-    float pf[PF];
-    double pd[PD];
-    int flag[4];
-    int ctl;
-    int desc_fit;                      // fit whose descriptor is in desc (-1: none yet)
-    union {
-        float redf[8 * KMAX];
-        double redd[8 * KMAX];
-        double comb[EVAL_THREADS];
-    };
-    TrfSmem trf;
-};
-
-// Sum rows [0, nrows) of a [rows][KMAX] array into out[0..K) in a fixed order
-// using all threads: thread t handles slot t % K over rows = part (mod P).
-// Loads go out in batches of 8 rows per thread before any add, so that one
-// L2 round trip covers a batch (rows were written by other CTAs: __ldcg).
-template <typename T>
-__device__ void combine_rows(const T* rows, int nrows, int K, double* scratch, double* out) {
-    constexpr int BATCH = 8;
-    int P = EVAL_THREADS / K;
-    int t = threadIdx.x;
-    int k = t % K, part = t / K;
-    double s = 0.0;
-    if (part < P)
-        for (int r0 = part; r0 < nrows; r0 += BATCH * P) {
-            T v[BATCH];
-#pragma unroll
-            for (int u = 0; u < BATCH; ++u) {
-                int r = r0 + u * P;
-                v[u] = r < nrows ? __ldcg(rows + (int64_t)r * KMAX + k) : T(0);
-            }
-#pragma unroll
-            for (int u = 0; u < BATCH; ++u) s += double(v[u]);
-        }
-    scratch[t] = s;
-    __syncthreads();
-    if (t < K) {
-        double tot = 0.0;
-        for (int p = 0; p < P; ++p) tot += scratch[p * K + t];
-        out[t] = tot;
-    }
-    __syncthreads();
-}
-
-// ------------------------------------------------------------------ the round kernel
-template <class M, int PREC>
-__device__ void eval_tile_dispatch(const RoundSmem& sm, int64_t i0, int64_t i1, bool check, int& bad,
-                                   typename AccT<PREC>::T (&acc)[n_acc(M::N, PREC)], RingState& R) {
-    using AT = typename AccT<PREC>::T;
-    const FitDesc& d = sm.desc;
-#pragma unroll
-    for (int k = 0; k < n_acc(M::N, PREC); ++k) acc[k] = AT(0);
-    float pfl[PF];
-    double pdl[PD];
-    if (PREC == PREC_MIXED) {
-#pragma unroll
-        for (int k = 0; k < PF; ++k) pfl[k] = sm.pf[k];
-    } else {
-#pragma unroll
-        for (int k = 0; k < PD; ++k) pdl[k] = sm.pd[k];
-    }
-    const bool f64 = d.dtype == F64;
-    // mixed precision on FP32 data streams through the bulk-copy ring
-#define GB_CASE(LAY, WKV)                                                                              \
-    if constexpr (PREC == PREC_MIXED && WKV != W_ARRAY) {                                              \
-        if (!f64) tile_points_ring<M, LAY, WKV>(d, pfl, i0, i1, check, acc, bad, R);                   \
-        else tile_points<M, PREC, double, LAY, WKV>(d, pfl, pdl, i0, i1, check, acc, bad);             \
-    } else {                                                                                           \
-        if (f64) tile_points<M, PREC, double, LAY, WKV>(d, pfl, pdl, i0, i1, check, acc, bad);         \
-        else tile_points<M, PREC, float, LAY, WKV>(d, pfl, pdl, i0, i1, check, acc, bad);              \
-    }
-    int wk = d.wkind;
-    if (M::N == 7) {
-        if (d.layout == X_GRID) {
-            if (wk == W_NONE) { GB_CASE(X_GRID, W_NONE) } else if (wk == W_ARRAY) { GB_CASE(X_GRID, W_ARRAY) } else { GB_CASE(X_GRID, W_SIGMA) }
-        } else {
-            if (wk == W_NONE) { GB_CASE(X_SOA2, W_NONE) } else if (wk == W_ARRAY) { GB_CASE(X_SOA2, W_ARRAY) } else { GB_CASE(X_SOA2, W_SIGMA) }
-        }
-    } else {
-        if (wk == W_NONE) { GB_CASE(X_VEC, W_NONE) } else if (wk == W_ARRAY) { GB_CASE(X_VEC, W_ARRAY) } else { GB_CASE(X_VEC, W_SIGMA) }
-    }
-#undef GB_CASE
-}
-
-template <class M, int PREC>
-__device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, RingState& R, long long t_item) {
-    using AT = typename AccT<PREC>::T;
-    constexpr int N = M::N;
-    constexpr int K = n_acc(N, PREC);
-    const FitDesc& d = sm.desc;
-    FitState* stp = E.state + fit;
-    int64_t i0 = (int64_t)tile * d.tile_points;
-    int64_t i1 = i0 + d.tile_points;
-    if (i1 > d.m) i1 = d.m;
-    bool check = sm.flag[1] == PH_INIT;
-    long long t_tile = clock64();
-    int bad = 0;
-    AT acc[K];
-    eval_tile_dispatch<M, PREC>(sm, i0, i1, check, bad, acc, R);
-    if (threadIdx.x == 0) sm.t_loop = clock64();
-    if (sm.ring_fail && threadIdx.x == 0) atomicOr(&stp->bad_data, 2);   // a bounded wait gave up
-    if (check) {
-        int any = __syncthreads_or(bad);
-        if (any && threadIdx.x == 0) atomicOr(&stp->bad_data, 1);
-    }
-    AT* red = (PREC == PREC_MIXED) ? (AT*)sm.redf : (AT*)sm.redd;
-    AT tsum;
-    block_reduce<K, AT>(acc, red, tsum);
-    if (threadIdx.x == 0) sm.t_mark = clock64();
-    int64_t row = d.tile_base + tile;
-    if (threadIdx.x < K) {
-        E.tile_part_d[row * KMAX + threadIdx.x] = double(tsum);
-    }
-    // ---- last arriver of the group combines the group
-    __syncthreads();
-    int group = tile / d.group_tiles;
-    int g0 = group * d.group_tiles;
-    int gsize = min(d.group_tiles, d.n_tiles - g0);
-    if (threadIdx.x == 0) {
-        int old = arrive_acq_rel(&E.group_cnt[d.group_base + group]);
-        sm.flag[2] = (old == gsize - 1);
-    }
-    __syncthreads();
-    if (!sm.flag[2]) return;
-    if (d.n_groups == 1) prefetch_state(stp, sm.trf);      // this CTA runs the step
-    if (threadIdx.x == 0) sm.t_fence = clock64();
-    double* gout = E.group_part + (d.group_base + group) * KMAX;
-    combine_rows<double>(E.tile_part_d + (d.tile_base + g0) * KMAX, gsize, K, sm.comb, sm.trf.tot);
-    if (threadIdx.x == 0) {
-        E.group_cnt[d.group_base + group] = 0;
-        sm.t_group = clock64();
-    }
-    if (d.n_groups > 1) {
-        // second level: the last group of the fit combines the group sums
-        if (threadIdx.x < K) gout[threadIdx.x] = sm.trf.tot[threadIdx.x];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int old = arrive_acq_rel(&E.fit_cnt[fit]);
-            sm.flag[3] = (old == d.n_groups - 1);
-        }
-        __syncthreads();
-        if (!sm.flag[3]) return;
-        prefetch_state(stp, sm.trf);
-        combine_rows<double>(E.group_part + d.group_base * KMAX, d.n_groups, K, sm.comb, sm.trf.tot);
-    }
-    if (threadIdx.x == 0) {
-        E.fit_cnt[fit] = 0;
-        long long now = clock64();
-        trace_bump(stp->trace, TR_COMBINE, (unsigned long long)(now - sm.t_mark));
-        trace_bump(stp->trace, TR_C_FENCE, (unsigned long long)(sm.t_fence - sm.t_mark));
-        trace_bump(stp->trace, TR_C_GROUP, (unsigned long long)(sm.t_group - sm.t_fence));
-        trace_bump(stp->trace, TR_C_FINAL, (unsigned long long)(now - sm.t_group));
-        trace_bump(stp->trace, TR_TILE, (unsigned long long)(sm.t_mark - t_tile));
-        trace_bump(stp->trace, TR_PRE_TILE, (unsigned long long)(t_tile - t_item));
-        trace_bump(stp->trace, TR_TILE_LOOP, (unsigned long long)(sm.t_loop - t_tile));
-    }
-    __syncthreads();
-    trf_step<PREC>(d, stp, E.results + fit, sm.trf, E.running);
-    __syncthreads();
-}
-
-// Copy the engine record into shared memory (round_setup's barrier publishes it).
-__device__ __forceinline__ void stage_engine(RoundSmem& sm, const Engine* Ep) {
-    const int* src = (const int*)Ep;
-    int* dst = (int*)&sm.eng;
-    for (int k = threadIdx.x; k < (int)(sizeof(Engine) / 4); k += blockDim.x) dst[k] = src[k];
-}
-
-// Ring barriers and flags at the start of a round kernel.
-template <int PREC>
-__device__ __forceinline__ void round_setup(RoundSmem& sm, float* ring_buf, RingState& R) {
-    R.bar = sm.mbar;
-    R.empty = sm.mbar_empty;
-    R.buf = ring_buf;
-    R.seq = 0;
-    R.fail = &sm.ring_fail;
-    if (threadIdx.x == 0) sm.desc_fit = -1;
-    if (PREC == PREC_MIXED) {
-        if (threadIdx.x == 0) {
-            for (int s = 0; s < NST; ++s) {
-                mbar_init(&sm.mbar[s], 1);
-                mbar_init(&sm.mbar_empty[s], EVAL_THREADS / 32);
-            }
-            sm.ring_fail = 0;
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-    } else if (threadIdx.x == 0) {
-        sm.ring_fail = 0;
-    }
-    __syncthreads();
-}
-
-// One round: this CTA's share of the work items.  The first item of every
-// CTA is `first` (items 0 .. grid-1 one per CTA); after that either
-// grid-stride (static) or the next unclaimed item from the round's counter
-// (dynamic: CTAs that finish early take more, so no CTA ends a round far
-// behind the others).  Which CTA processes an item does not change any sum.
-template <int PREC>
-__device__ __forceinline__ void run_items(RoundSmem& sm, const Engine& E, RingState& R, int first,
-                                          int* next_item) {
-    int n_items = *E.n_items;
-    for (int it = first; it < n_items;) {
-        long long t_item = clock64();
-        WorkItem wi = E.items[it];
-        FitState* stp = E.state + wi.fit;
-        // one round trip for the item's state words, pass constants and (when
-        // this CTA's previous item was another fit) descriptor; state from
-        // L2, since other CTAs rewrite it between rounds
-        if (threadIdx.x == 0) { sm.flag[0] = __ldcg(&stp->run); sm.flag[1] = __ldcg(&stp->phase); }
-        if (PREC == PREC_MIXED) { if (threadIdx.x < PF) sm.pf[threadIdx.x] = __ldcg(stp->pf + threadIdx.x); }
-        else { if (threadIdx.x < PD) sm.pd[threadIdx.x] = __ldcg(stp->pd + threadIdx.x); }
-        if (wi.fit != sm.desc_fit) {
-            const int* src = (const int*)(E.desc + wi.fit);
-            int* dst = (int*)&sm.desc;
-            for (int k = threadIdx.x; k < (int)(sizeof(FitDesc) / 4); k += EVAL_THREADS) dst[k] = src[k];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) sm.desc_fit = wi.fit;
-        if (sm.flag[0] != RS_RUNNING) {
-            __syncthreads();
-            if (next_item) {
-                if (threadIdx.x == 0) sm.flag[0] = (int)gridDim.x + atomicAdd(next_item, 1);
-                __syncthreads();
-                it = sm.flag[0];
-                __syncthreads();
-            } else {
-                it += gridDim.x;
-            }
-            continue;
-        }
-        switch (sm.desc.model) {
-            case 0: process_item<MGauss1D, PREC>(sm, E, wi.fit, wi.tile, R, t_item); break;
-            case 1: process_item<MDexp, PREC>(sm, E, wi.fit, wi.tile, R, t_item); break;
-            case 2: process_item<MGauss2D, PREC>(sm, E, wi.fit, wi.tile, R, t_item); break;
-            case 3: process_item<MPoly2, PREC>(sm, E, wi.fit, wi.tile, R, t_item); break;
-        }
-        if (next_item) {
-            if (threadIdx.x == 0) sm.flag[0] = (int)gridDim.x + atomicAdd(next_item, 1);
-            __syncthreads();
-            it = sm.flag[0];
-        } else {
-            it += gridDim.x;
-        }
-        __syncthreads();
-    }
-}
-
-template <int PREC>
-__global__ void __launch_bounds__(EVAL_THREADS, 2) eval_round_kernel(const Engine* __restrict__ Ep) {
-    __shared__ RoundSmem sm;
-    extern __shared__ __align__(128) float ring_buf[];
-    stage_engine(sm, Ep);
-    RingState R;
-    round_setup<PREC>(sm, ring_buf, R);
-    run_items<PREC>(sm, sm.eng, R, blockIdx.x, nullptr);
-}
-
-// ---- grid-wide round barrier of the persistent loop.  The loop kernel is
-// launched cooperatively (every CTA resident), so a CTA that waits here
-// waits only for CTAs that are running.  Waits are bounded in time; past
-// the bound the CTA raises the abort bit and every CTA leaves the loop.
-constexpr unsigned long long ROUND_WAIT_LIMIT_NS = 10ull * 1000 * 1000 * 1000;
-enum { CTL_STOP = 1, CTL_ABORT = 2 };
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// All CTAs arrive; the last one closes the round (rounds, running, stop
-// decision; count_round false for the set-up barrier) and opens the next.
-// Returns the control word (CTL_*) for every thread of every CTA.
-__device__ int grid_round_end(Engine* Ed, const Engine& E, int* ctl_smem, bool count_round) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned* cnt = (unsigned*)&Ed->sc[5];
-        unsigned* gen = (unsigned*)&Ed->sc[6];
-        volatile int* ctl = &Ed->sc[7];
-        unsigned g = ld_acquire_u32(gen);
-        unsigned old;
-        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(cnt) : "memory");
-        int c;
-        if (old == gridDim.x - 1) {
-            *(volatile unsigned*)cnt = 0;
-            c = *ctl & CTL_ABORT;
-            if (count_round) {
-                E.sm_cnt[SM_IDS] = 0;                 // next round's dynamic items start over
-                int r = ++(*E.rounds);
-                int run = *(volatile int*)E.running;
-                E.out[0] = run;
-                E.out[1] = r;
-                if (run <= 0 || r >= *E.max_rounds) c |= CTL_STOP;
-            }
-            *ctl = c;
-            st_release_u32(gen, g + 1);
-        } else {
-            unsigned long long t0 = global_ns();
-            while (ld_acquire_u32(gen) == g) {
-                __nanosleep(128);
-                if (global_ns() - t0 > ROUND_WAIT_LIMIT_NS) {
-                    atomicOr((int*)ctl, CTL_ABORT);
-                    break;
-                }
-            }
-            c = *ctl;
-        }
-        if (c & CTL_ABORT) atomicOr(E.out + 2, 1);
-        *ctl_smem = c;
-    }
-    __syncthreads();
-    return *ctl_smem;
-}
-
-// Persistent form of the iteration: pass constants at p0 (do_init), then
-// rounds of run_items separated by the grid barrier until no fit runs or the
-// round cap is reached.  One cooperative launch replaces a graph of
-// per-round kernels.
-template <int PREC>
-__global__ void __launch_bounds__(EVAL_THREADS, 2) fit_loop_kernel(const Engine* __restrict__ Ep, int do_init) {
-    __shared__ RoundSmem sm;
-    extern __shared__ __align__(128) float ring_buf[];
-    stage_engine(sm, Ep);
-    const Engine& E = sm.eng;
-    Engine* Ed = const_cast<Engine*>(Ep);
-    RingState R;
-    round_setup<PREC>(sm, ring_buf, R);
-    // This CTA's rank among all CTAs ordered by (slot on its SM, SM id), so
-    // that work items 0, 1, 2, ... land on distinct SMs before any SM gets a
-    // second one (a fit with fewer tiles than SMs gets one SM per tile).
-    if (threadIdx.x == 0) {
-        unsigned smid;
-        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-        sm.flag[0] = (int)smid;
-        sm.flag[1] = atomicAdd(E.sm_cnt + (smid < SM_IDS ? smid : SM_IDS - 1), 1);
-    }
-    if (grid_round_end(Ed, E, &sm.ctl, false)) return;
-    int first;
-    {
-        const int smid = sm.flag[0], slot = sm.flag[1];
-        unsigned nsm;
-        asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsm));
-        nsm = nsm < SM_IDS ? nsm : SM_IDS;
-        int part = 0;
-        for (int k = threadIdx.x; k < (int)nsm; k += blockDim.x) {
-            int c = __ldcg(E.sm_cnt + k);
-            part += min(c, slot) + ((k < smid && c > slot) ? 1 : 0);
-        }
-        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
-        __syncthreads();                                  // flag[0..1] read by every thread
-        if (threadIdx.x == 0) sm.flag[2] = 0;
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) atomicAdd(&sm.flag[2], part);
-        __syncthreads();
-        first = sm.flag[2];
-    }
-    if (do_init) {
-        int nf = *E.nfits_dev;
-        for (int f = blockIdx.x; f < nf; f += gridDim.x) {
-            if (threadIdx.x < 32) {
-                const FitDesc& d = E.desc[f];
-                FitState* st = E.state + f;
-                int l = threadIdx.x;
-                if (l < 8) { sm.trf.vec[VX][l] = (l < d.n) ? st->x[l] : 0.0; sm.trf.vec[VXT][l] = sm.trf.vec[VX][l]; }
-                __syncwarp();
-                prep_pass<PREC>(d, st, sm.trf);
-            }
-            __syncthreads();
-        }
-        if (grid_round_end(Ed, E, &sm.ctl, false)) return;
-    }
-    // time accounting of the loop (result header, 64-bit words 2..3):
-    // per-CTA time in rounds' work and time waiting at the barrier
-    unsigned long long* acct = reinterpret_cast<unsigned long long*>(E.out) + 2;
-    while (true) {
-        unsigned long long t0 = global_ns();
-        run_items<PREC>(sm, E, R, first, E.sm_cnt + SM_IDS);
-        unsigned long long t1 = global_ns();
-        int c = grid_round_end(Ed, E, &sm.ctl, true);
-        if (threadIdx.x == 0) {
-            atomicAdd(acct, t1 - t0);
-            atomicAdd(acct + 1, global_ns() - t1);
-        }
-        if (c) break;
-    }
-    // every CTA has read the counters (before the first round): rank 0 clears them for the next launch
-    if (first == 0)
-        for (int k = threadIdx.x; k <= SM_IDS; k += blockDim.x) E.sm_cnt[k] = 0;
-}
-
-// Pass constants for the first evaluation (at p0): base = trial = p0.
-template <int PREC>
-__global__ void init_fits_kernel(const Engine* __restrict__ Ep) {
-    __shared__ TrfSmem S;
-    const Engine E = *Ep;
-    int nf = E.nfits_dev ? *E.nfits_dev : 0;
-    for (int f = blockIdx.x; f < nf; f += gridDim.x) {
-        const FitDesc& d = E.desc[f];
-        FitState* st = E.state + f;
-        int l = threadIdx.x;
-        if (l < 8) { S.vec[VX][l] = (l < d.n) ? st->x[l] : 0.0; S.vec[VXT][l] = S.vec[VX][l]; }
-        __syncwarp();
-        prep_pass<PREC>(d, st, S);
-        __syncwarp();
-    }
-}
-
-// Pass constants at p0 for the listed fits only (serving: newly admitted
-// fits join while others are mid-fit).
-template <int PREC>
-__global__ void init_slots_kernel(const Engine* __restrict__ Ep, const int* __restrict__ slots, int count) {
-    __shared__ TrfSmem S;
-    const Engine E = *Ep;
-    for (int k = blockIdx.x; k < count; k += gridDim.x) {
-        int f = slots[k];
-        const FitDesc& d = E.desc[f];
-        FitState* st = E.state + f;
-        int l = threadIdx.x;
-        if (l < 8) { S.vec[VX][l] = (l < d.n) ? st->x[l] : 0.0; S.vec[VXT][l] = S.vec[VX][l]; }
-        __syncwarp();
-        prep_pass<PREC>(d, st, S);
-        __syncwarp();
-    }
-}
 
 // w = 1/sigma (FP64) for the plain path.
 template <typename DT>
@@ -930,38 +72,12 @@ __global__ void tr_subproblem_kernel(int n, const double* B, const double* g, do
 }
 
 // ------------------------------------------------------------------ host-side handles
-void* kernel_eval_round(int prec) {
-    return prec == PREC_MIXED ? (void*)eval_round_kernel<PREC_MIXED> : (void*)eval_round_kernel<PREC_FP64>;
-}
-void* kernel_init_fits(int prec) {
-    return prec == PREC_MIXED ? (void*)init_fits_kernel<PREC_MIXED> : (void*)init_fits_kernel<PREC_FP64>;
-}
-void* kernel_fit_loop(int prec) {
-    return prec == PREC_MIXED ? (void*)fit_loop_kernel<PREC_MIXED> : (void*)fit_loop_kernel<PREC_FP64>;
-}
-void* kernel_init_slots(int prec) {
-    return prec == PREC_MIXED ? (void*)init_slots_kernel<PREC_MIXED> : (void*)init_slots_kernel<PREC_FP64>;
-}
-size_t eval_dyn_smem(int prec) { return prec == PREC_MIXED ? RING_BYTES : 0; }
-// Resident CTAs per SM of the round kernels (the loop kernel's cooperative
-// grid is this times the SM count, so both kernels must fit it).
-int eval_blocks_per_sm(int prec) {
-    int b = 0, b2 = 0;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(eval_round_kernel<PREC_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RING_BYTES);
-        cudaFuncSetAttribute(fit_loop_kernel<PREC_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RING_BYTES);
-        attr_set = true;
-    }
-    if (prec == PREC_MIXED) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, eval_round_kernel<PREC_MIXED>, EVAL_THREADS, RING_BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fit_loop_kernel<PREC_MIXED>, EVAL_THREADS, RING_BYTES);
-    } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, eval_round_kernel<PREC_FP64>, EVAL_THREADS, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fit_loop_kernel<PREC_FP64>, EVAL_THREADS, 0);
-    }
-    return b < b2 ? b : b2;
-}
+void* kernel_eval_round(int prec) { return prec == PREC_MIXED ? kernel_eval_round_mixed() : kernel_eval_round_fp64(); }
+void* kernel_init_fits(int prec) { return prec == PREC_MIXED ? kernel_init_fits_mixed() : kernel_init_fits_fp64(); }
+void* kernel_fit_loop(int prec) { return prec == PREC_MIXED ? kernel_fit_loop_mixed() : kernel_fit_loop_fp64(); }
+void* kernel_init_slots(int prec) { return prec == PREC_MIXED ? kernel_init_slots_mixed() : kernel_init_slots_fp64(); }
+size_t eval_dyn_smem(int prec) { return prec == PREC_MIXED ? eval_dyn_smem_mixed() : eval_dyn_smem_fp64(); }
+int eval_blocks_per_sm(int prec) { return prec == PREC_MIXED ? eval_blocks_per_sm_mixed() : eval_blocks_per_sm_fp64(); }
 cudaError_t launch_stage_weights(bool f64, const void* sigma, double* w, int64_t m, int blocks, cudaStream_t s) {
     if (f64) stage_weights_kernel<double><<<blocks, 256, 0, s>>>((const double*)sigma, w, m);
     else stage_weights_kernel<float><<<blocks, 256, 0, s>>>((const float*)sigma, w, m);

@@ -4,8 +4,20 @@
 #include "trf_device.cuh"
 
 namespace gbfit {
-// Host-side handles to the kernels of kernels.cu (kept non-template so that
+// Host-side handles to the kernels of kernels*.cu (kept non-template so that
 // the host engine never names a template kernel of another translation unit).
+void* kernel_eval_round_mixed();
+void* kernel_eval_round_fp64();
+void* kernel_init_fits_mixed();
+void* kernel_init_fits_fp64();
+void* kernel_fit_loop_mixed();
+void* kernel_fit_loop_fp64();
+void* kernel_init_slots_mixed();
+void* kernel_init_slots_fp64();
+int eval_blocks_per_sm_mixed();
+int eval_blocks_per_sm_fp64();
+size_t eval_dyn_smem_mixed();
+size_t eval_dyn_smem_fp64();
 void* kernel_eval_round(int prec);
 void* kernel_init_fits(int prec);
 void* kernel_init_slots(int prec);

@@ -1,0 +1,30 @@
+// The plain FP64 instantiation of the round kernels (one translation unit
+// per precision, so that the two compile in parallel).
+#include "round_kernels.cuh"
+#include "kernels.cuh"
+
+namespace gbfit {
+
+void* kernel_eval_round_fp64() { return (void*)eval_round_kernel<PREC_FP64>; }
+void* kernel_init_fits_fp64() { return (void*)init_fits_kernel<PREC_FP64>; }
+void* kernel_fit_loop_fp64() { return (void*)fit_loop_kernel<PREC_FP64>; }
+void* kernel_init_slots_fp64() { return (void*)init_slots_kernel<PREC_FP64>; }
+
+// Resident CTAs per SM of the round kernels (the loop kernel's cooperative
+// grid is this times the SM count, so both kernels must fit it).
+int eval_blocks_per_sm_fp64() {
+    const int dyn = (int)(0);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(eval_round_kernel<PREC_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        cudaFuncSetAttribute(fit_loop_kernel<PREC_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        attr_set = true;
+    }
+    int b = 0, b2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, eval_round_kernel<PREC_FP64>, EVAL_THREADS, dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fit_loop_kernel<PREC_FP64>, EVAL_THREADS, dyn);
+    return b < b2 ? b : b2;
+}
+size_t eval_dyn_smem_fp64() { return 0; }
+
+}  // namespace gbfit

@@ -75,6 +75,51 @@ __device__ __forceinline__ void exp_shift2(float2 E, float2 q_new, float2 dq, fl
     dE.y = fabsf(dq.y) <= 0.125f ? dEs.y : En.y - E.y;
 }
 
+// ---- robust losses (Section 5 names loss functions without stating them;
+// reading R14): rho(z), rho'(z), rho''(z) with z = (r / C)^2, and the change
+// rho(z + dz) - rho(z) written without cancellation (dz is formed from the
+// residual change as in the cancellation-free actual reduction).
+template <typename T>
+__device__ __forceinline__ void loss_rho(int loss, T z, T& rho, T& r1, T& r2) {
+    switch (loss) {
+        case LOSS_SOFT_L1: {
+            T t = T(1) + z, st = sqrt(t), it = T(1) / st;
+            rho = T(2) * z / (st + T(1)); r1 = it; r2 = T(-0.5) * it / t;
+            break;
+        }
+        case LOSS_HUBER:
+            if (z <= T(1)) { rho = z; r1 = T(1); r2 = T(0); }
+            else { T sz = sqrt(z); rho = T(2) * sz - T(1); r1 = T(1) / sz; r2 = T(-0.5) * r1 / z; }
+            break;
+        case LOSS_CAUCHY: {
+            T it = T(1) / (T(1) + z);
+            rho = log1p(z); r1 = it; r2 = -it * it;
+            break;
+        }
+        case LOSS_ARCTAN: {
+            T it = T(1) / (T(1) + z * z);
+            rho = atan(z); r1 = it; r2 = T(-2) * z * it * it;
+            break;
+        }
+        default: rho = z; r1 = T(1); r2 = T(0); break;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T loss_drho(int loss, T z, T dz) {
+    const T zn = z + dz;
+    switch (loss) {
+        case LOSS_SOFT_L1: return T(2) * dz / (sqrt(T(1) + zn) + sqrt(T(1) + z));
+        case LOSS_HUBER:
+            if (z <= T(1) && zn <= T(1)) return dz;
+            if (z > T(1) && zn > T(1)) return T(2) * dz / (sqrt(zn) + sqrt(z));
+            return (zn <= T(1) ? zn : T(2) * sqrt(zn) - T(1)) - (z <= T(1) ? z : T(2) * sqrt(z) - T(1));
+        case LOSS_CAUCHY: return log1p(dz / (T(1) + z));
+        case LOSS_ARCTAN: return atan(dz / (T(1) + z * zn));
+        default: return dz;
+    }
+}
+
 // Float images of the FP64 parameters handed to the mixed prep.
 struct MixedParams {
     float x[NMAX];    // base p (rounded)

@@ -63,7 +63,7 @@ __device__ __forceinline__ void mm8(int n, const double* A, bool tA, const doubl
 // Partner of each index in round r of the parallel round-robin ordering on
 // np = 2, 4, 6, 8 indices (an index paired with itself rests that round);
 // 3 bits per index so that every lane reads the same word.
-__constant__ unsigned c_partner_packed[4][7] = {
+static __constant__ unsigned c_partner_packed[4][7] = {
     {0xfac681u, 0xfac688u, 0xfac688u, 0xfac688u, 0xfac688u, 0xfac688u, 0xfac688u},
     {0xfac053u, 0xfac4c1u, 0xfac21au, 0xfac688u, 0xfac688u, 0xfac688u, 0xfac688u},
     {0xf814e5u, 0xf93941u, 0xfa521au, 0xf8a12bu, 0xf98a54u, 0xfac688u, 0xfac688u},
@@ -77,7 +77,7 @@ __constant__ unsigned c_partner_packed[4][7] = {
 // second buffer (one __syncwarp per round).  Relative stopping test
 // |a_pq| <= 2.5e-7 sqrt(a_pp a_qq).  A, A2, R, R2: float 8x8 smem; on return
 // *Ares / *Rres point at the results.
-__device__ int jacobi32(int n, float* A, float* A2, float* R, float* R2, int max_sweeps,
+__device__ inline int jacobi32(int n, float* A, float* A2, float* R, float* R2, int max_sweeps,
                         float** Ares, float** Rres) {
     const int l = threadIdx.x & 31;
     const int np = n + (n & 1);
@@ -141,7 +141,7 @@ __device__ int jacobi32(int n, float* A, float* A2, float* R, float* R2, int max
 // factorisation, so M is positive definite exactly when all are positive;
 // returns false otherwise.  min_diag: smallest diagonal entry of M.  One
 // warp; each lane owns two entries, n rank-one steps.
-__device__ bool inv32(int n, const double* Ah, float* Mi, float& sc, float& min_diag) {
+__device__ inline bool inv32(int n, const double* Ah, float* Mi, float& sc, float& min_diag) {
     const int l = threadIdx.x & 31;
     double dmax = gmax8((l < n) ? Ah[l * 8 + l] : 0.0);
     if (!(dmax > 0.0)) return false;
@@ -191,7 +191,7 @@ __device__ __forceinline__ float apply32(int n, const float* Mi, float v) {
 // d1, d2: norms of the two corrections (FP32); their ratio estimates
 // eps32 * cond of the equilibrated matrix.  tmp: an 8-double smem vector
 // of the calling warp.
-__device__ double solve_refined(int n, const double* Ah, const float* Mi, float sc, double rhs, double* tmp,
+__device__ inline double solve_refined(int n, const double* Ah, const float* Mi, float sc, double rhs, double* tmp,
                                 float& d1, float& d2) {
     const int l = threadIdx.x & 31;
     double p = double(apply32(n, Mi, float(rhs) * sc));
@@ -225,7 +225,7 @@ __device__ __forceinline__ bool refined_ok(float d1, float d2, float min_diag) {
 // B_hat, lam = Sigma^2).  Vwarm (global, may be null): a previous basis to
 // start from.  All CTA threads call; results in S.V and S.vec[VLAM].
 // Returns the FP32 Jacobi sweeps.
-__device__ int eig_fast(int n, const double* Ah, const double* Vwarm, TrfSmem& S,
+__device__ inline int eig_fast(int n, const double* Ah, const double* Vwarm, TrfSmem& S,
                         unsigned long long* trace = nullptr) {
     const int t = threadIdx.x, warp = t >> 5, l = t & 31;
     const bool warm = Vwarm != nullptr;
@@ -366,6 +366,11 @@ __device__ void prep_pass(const FitDesc& d, FitState* st, TrfSmem& S) {
                 case 3: MPoly2::prep_mixed(S.mp, S.pfs); break;
             }
         }
+        if (l == 0) {
+            const float C = float(d.f_scale);
+            S.pfs[PF_C2] = C * C;
+            S.pfs[PF_IC2] = 1.0f / (C * C);
+        }
         __syncwarp();
         st->pf[l] = S.pfs[l];
     } else {
@@ -377,6 +382,10 @@ __device__ void prep_pass(const FitDesc& d, FitState* st, TrfSmem& S) {
                 case 2: MGauss2D::prep_plain(S.vec[VXT], S.pds); break;
                 case 3: MPoly2::prep_plain(S.vec[VXT], S.pds); break;
             }
+        }
+        if (l == 0) {
+            S.pds[PD_C2] = d.f_scale * d.f_scale;
+            S.pds[PD_IC2] = 1.0 / (d.f_scale * d.f_scale);
         }
         __syncwarp();
         if (l < PD) st->pd[l] = S.pds[l];
@@ -390,7 +399,7 @@ enum { SI_STATUS = 0, SI_NFEV, SI_NJEV, SI_FACTOR, SI_GN, SI_REJECTED, SI_PCOV }
 
 // Result record with pcov (R13) from an FP64-accurate eigen-decomposition of
 // the unscaled Gram at the solution.  All CTA threads call.
-__device__ void write_result(const FitDesc& d, FitState* st, FitResult* res, int status, TrfSmem& S) {
+__device__ inline void write_result(const FitDesc& d, FitState* st, FitResult* res, int status, TrfSmem& S) {
     const int n = d.n, t = threadIdx.x;
     if (t < n) res->popt[t] = st->x[t];
     for (int k = t; k < KMAX; k += EVAL_THREADS) res->tot[k] = S.tot[k];

@@ -46,7 +46,9 @@ class Options(ctypes.Structure):
                 ("max_nfev", ctypes.c_int), ("x_scale_jac", ctypes.c_int),
                 ("x_scale", ctypes.POINTER(ctypes.c_double)), ("absolute_sigma", ctypes.c_int),
                 ("precision", ctypes.c_int), ("tile_points", ctypes.c_int), ("group_tiles", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("loss", ctypes.c_int), ("reserved", ctypes.c_int * 1), ("f_scale", ctypes.c_double)]
+
+LOSSES = {"linear": 0, "soft_l1": 1, "huber": 2, "cauchy": 3, "arctan": 4}
 
 TUNE_BUCKETS = 32
 
@@ -79,7 +81,8 @@ class Request(ctypes.Structure):
                 ("grid_h", ctypes.c_int64), ("xdata", ctypes.c_void_p), ("ydata", ctypes.c_void_p),
                 ("sigma", ctypes.c_void_p), ("p0", ctypes.c_double * 8), ("lb", ctypes.c_double * 8),
                 ("ub", ctypes.c_double * 8), ("ftol", ctypes.c_double), ("xtol", ctypes.c_double),
-                ("gtol", ctypes.c_double), ("max_nfev", ctypes.c_int), ("tag", ctypes.c_uint64)]
+                ("gtol", ctypes.c_double), ("max_nfev", ctypes.c_int), ("tag", ctypes.c_uint64),
+                ("loss", ctypes.c_int), ("f_scale", ctypes.c_double)]
 
 
 class ResultRec(ctypes.Structure):
@@ -192,7 +195,8 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
 
 
-def _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles=0):
+def _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles=0,
+             loss="linear", f_scale=1.0):
     load()
     o = Options.from_buffer_copy(_DEFAULT_OPT)
     o.ftol, o.xtol, o.gtol = ftol, xtol, gtol
@@ -213,6 +217,8 @@ def _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, 
         raise KeyError(precision)
     o.tile_points = int(tile_points)
     o.group_tiles = int(group_tiles)
+    o.loss = LOSSES[loss] if isinstance(loss, str) else int(loss)
+    o.f_scale = float(f_scale)
     return o, keep
 
 
@@ -234,7 +240,8 @@ def _bounds(n, lb, ub):
 
 def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None, ub=None,
               grid_wh=None, ftol=1e-8, xtol=1e-8, gtol=1e-8, max_nfev=None, x_scale=1.0,
-              absolute_sigma=False, precision="mixed", tile_points=0, group_tiles=0, stream=None) -> dict:
+              absolute_sigma=False, precision="mixed", tile_points=0, group_tiles=0, loss="linear",
+              f_scale=1.0, stream=None) -> dict:
     """Fit `model` by the GPU trust-region-reflective method (gbfit_curve_fit).
 
     xdata: [m] (1D models), [2, m] (2D explicit coordinates) or None with
@@ -259,7 +266,8 @@ def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None
     p0a = _vec(p0, n)
     lbv = None if lb is None else _vec(lb, n)
     ubv = None if ub is None else _vec(ub, n)
-    opt, okeep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles)
+    opt, okeep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles,
+                          loss, f_scale)
     out = np.zeros(n + n * n + 1)                  # popt | pcov | cost
     ints = np.zeros(2, dtype=np.int32)             # nfev | status
     a = out.ctypes.data
@@ -275,7 +283,8 @@ def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None
 
 def curve_fit_batch(model: int, offsets, xdata, ydata, p0, sigma=None, lb=None, ub=None,
                     ftol=1e-8, xtol=1e-8, gtol=1e-8, max_nfev=None, x_scale=1.0,
-                    absolute_sigma=False, precision="mixed", tile_points=0, group_tiles=0, stream=None) -> dict:
+                    absolute_sigma=False, precision="mixed", tile_points=0, group_tiles=0, loss="linear",
+                    f_scale=1.0, stream=None) -> dict:
     """Many independent fits over concatenated data (gbfit_curve_fit_batch).
     tile_points / group_tiles 0: each fit's shape from the tile table."""
     lib = load()
@@ -289,7 +298,8 @@ def curve_fit_batch(model: int, offsets, xdata, ydata, p0, sigma=None, lb=None, 
     p0a = np.ascontiguousarray(np.asarray(p0, dtype=np.float64).reshape(nf, n))
     lba = None if lb is None else np.ascontiguousarray(np.broadcast_to(np.asarray(lb, np.float64), (nf, n)))
     uba = None if ub is None else np.ascontiguousarray(np.broadcast_to(np.asarray(ub, np.float64), (nf, n)))
-    opt, okeep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles)
+    opt, okeep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles,
+                          loss, f_scale)
     popt = np.zeros((nf, n))
     pcov = np.zeros((nf, n, n))
     cost = np.zeros(nf)
@@ -450,7 +460,7 @@ class Server:
         self._keep = {}
 
     def submit(self, model, xdata, ydata, p0, sigma=None, lb=None, ub=None, grid_wh=None, ftol=1e-8, xtol=1e-8,
-               gtol=1e-8, max_nfev=0, tag=0) -> int:
+               gtol=1e-8, max_nfev=0, tag=0, loss="linear", f_scale=1.0) -> int:
         n = N_PARAMS[model]
         r = Request()
         yp, dt, yk = _array_info(ydata)
@@ -471,6 +481,8 @@ class Server:
             for i in range(n):
                 r.lb[i], r.ub[i] = lbv[i], ubv[i]
         r.ftol, r.xtol, r.gtol, r.max_nfev, r.tag = ftol, xtol, gtol, int(max_nfev), int(tag)
+        r.loss = LOSSES[loss] if isinstance(loss, str) else int(loss)
+        r.f_scale = float(f_scale)
         t = ctypes.c_uint64()
         _check(load().gbfit_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
         self._keep[t.value] = (xk, yk, sk)
