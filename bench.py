@@ -68,7 +68,7 @@ HBM_PEAK_GBS = 6785.9          # MEASURED_PEAKS.json: copy bandwidth of this poo
 # the headline workload, 5 passes) from the ncu capture summarised in
 # profiles/fit_loop_mixed_gauss2d_1024.md; None whenever the kernel has
 # changed since the capture.
-TRAFFIC_BYTES_PER_LAUNCH = 8.620e6
+TRAFFIC_BYTES_PER_LAUNCH = 8.612e6
 
 
 def workload_desc():
@@ -340,21 +340,36 @@ def run_ours(args, rank, local, world):
         "gpu_launches": launches,
         "clocks": clk,
     }
-    # ---- the same workload: explicit coordinates (SoA) and the plain FP64 path
-    res["config_layouts"] = layouts_and_fp64(args, pr, y, sg, flush, dev)
     if rank == 0 and not args.no_cpu_baseline:
         rate, fits, secs, ref = oracle_rate(pr, want_result=True)
         one = oracle_rate_one_core()
         res["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
                                "sample": f"{fits} whole FP64 oracle fits of the same workload ({secs:.1f} s)",
                                "one_core": one}
-        rel = lambda a: float(np.max(np.abs(np.asarray(a) - ref["popt"]) / np.maximum(np.abs(ref["popt"]), 1.0)))
-        res["popt_rel_err_vs_oracle"] = {"mixed_grid": rel(out["popt"]),
-                                         "plain_fp64_grid": rel(res["config_layouts"]["plain_fp64_popt"])}
-        res["config_layouts"].pop("plain_fp64_popt")
-    else:
-        res["config_layouts"].pop("plain_fp64_popt")
+        res["popt_rel_err_vs_oracle"] = float(np.max(np.abs(np.asarray(out["popt"]) - ref["popt"]) /
+                                                     np.maximum(np.abs(ref["popt"]), 1.0)))
     return res
+
+
+def run_compare(args):
+    """The headline workload through explicit pixel coordinates and through
+    the plain FP64 path, against the oracle (one JSON line)."""
+    import torch
+    from oracle import trf
+    from paper_2208_12187_gb300 import build, gbfit
+    build.build()
+    gbfit.load()
+    pr = make_problem(0)
+    dev = torch.device("cuda", 0)
+    y = torch.as_tensor(pr.y).to(dev)
+    sg = torch.as_tensor(pr.sigma).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    res = layouts_and_fp64(args, pr, y, sg, flush, dev)
+    ref = trf.curve_fit_problem(pr.astype(np.float64), **TOL)
+    rel = lambda a: float(np.max(np.abs(np.asarray(a) - ref["popt"]) / np.maximum(np.abs(ref["popt"]), 1.0)))
+    for k in ("mixed_grid", "mixed_explicit_soa2", "plain_fp64_grid"):
+        res[k]["popt_rel_err_vs_oracle"] = rel(res[k].pop("popt"))
+    print(json.dumps({"mode": "compare", "workload": workload_desc(), **res}))
 
 
 def layouts_and_fp64(args, pr, y, sg, flush, dev):
@@ -364,7 +379,8 @@ def layouts_and_fp64(args, pr, y, sg, flush, dev):
     from paper_2208_12187_gb300 import gbfit, synth
     Xc = torch.as_tensor(pr.coords().astype(np.float32)).to(dev)            # [2, m]
     out = {}
-    for name, kw in (("mixed_explicit_soa2", dict(xdata=Xc, grid_wh=None, precision="mixed")),
+    for name, kw in (("mixed_grid", dict(xdata=None, grid_wh=(W, H), precision="mixed")),
+                     ("mixed_explicit_soa2", dict(xdata=Xc, grid_wh=None, precision="mixed")),
                      ("plain_fp64_grid", dict(xdata=None, grid_wh=(W, H), precision="fp64"))):
         f = lambda: gbfit.curve_fit(pr.model, kw["xdata"], y, pr.p0, sigma=sg, lb=pr.lb, ub=pr.ub,
                                     grid_wh=kw["grid_wh"], precision=kw["precision"], **TOL)
@@ -380,9 +396,8 @@ def layouts_and_fp64(args, pr, y, sg, flush, dev):
             e1.synchronize()
             ms += e0.elapsed_time(e1)
             pts += M * r["nfev"]
-        out[name] = {"value": pts / (ms / 1e3), "unit": UNIT, "ms_per_fit": ms / 3, "nfev": r["nfev"]}
-        if name == "plain_fp64_grid":
-            out["plain_fp64_popt"] = r["popt"]
+        out[name] = {"value": pts / (ms / 1e3), "unit": UNIT, "ms_per_fit": ms / 3, "nfev": r["nfev"],
+                     "popt": r["popt"]}
     return out
 
 
@@ -673,6 +688,8 @@ def main():
     ap.add_argument("--precisions", default="mixed,fp64")
     ap.add_argument("--oracle-sample", type=int, default=64)
     ap.add_argument("--serve", action="store_true")
+    ap.add_argument("--compare", action="store_true",
+                    help="headline workload: implicit grid vs explicit coordinates vs plain FP64, against the oracle")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-sample", type=int, default=200)
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
@@ -691,6 +708,8 @@ def main():
         return run_batch(args)
     if args.serve:
         return run_serve(args)
+    if args.compare:
+        return run_compare(args)
     rank, local, world = dist_setup(args)
     if args.impl == "reference":
         res = run_reference(args, rank, world)
