@@ -120,8 +120,42 @@ const char* gbfit_last_error(void);
 /* Fill *opt with defaults (tolerances 1e-8, mixed precision, D = I). */
 int gbfit_default_options(gbfit_options* opt);
 
-/* Registry query: number of parameters and coordinate dimensions of model_id. */
+/* Registry query: number of parameters and coordinate dimensions of model_id
+ * (built-in or user-defined). */
 int gbfit_model_info(int model_id, int* n_params, int* x_dims);
+
+/* ---- user-defined models (the paper's user-written fit function, whose
+ * Jacobian JAX forms by automatic differentiation: Section 2, Eq. jacobian).
+ *
+ * source: CUDA C++ text that defines, at namespace scope,
+ *     template <class T, class S> __device__ T NAME(const T* p, S x, S x2);
+ * returning h(x; p) for the n parameters p[0..n) at coordinate x (x2: second
+ * coordinate of a 2D model, 0 for 1D).  T is a number type of the library
+ * (forward-mode dual numbers: FP64 value and partials for the plain path;
+ * for the mixed path FP32 value at p, the difference h(p') - h(p) propagated
+ * without cancellation, and FP32 partials at p'); S is float or double.  The
+ * body may use + - * / between T values and plain numbers, and exp, log,
+ * sqrt, pow(T, number), sin, cos, tanh, atan, square.  Smooth models only.
+ * func_name: NAME (NULL: "model").  n_params: 1..GBFIT_MAX_PARAMS.  x_dims:
+ * 1 (layout GBFIT_X_VEC) or 2 (GBFIT_X_SOA2 / GBFIT_X_GRID).
+ *
+ * The source is compiled once, here, with NVRTC (loaded from the CUDA
+ * toolkit at run time) into the library's persistent loop kernels for both
+ * precisions; the code is loaded on the device at the model's first fit.
+ * Returns the new id (>= GBFIT_USER_MODEL_BASE) in *model_id, usable with
+ * gbfit_curve_fit, gbfit_curve_fit_batch and gbfit_evaluate (the serving,
+ * tuning and allocation-free entry points take built-in models only).
+ * Errors: GBFIT_E_INVALID_ARG (bad arguments, or the source does not compile:
+ * the start of the compiler log is in gbfit_last_error(), all of it in
+ * gbfit_model_log), GBFIT_E_UNSUPPORTED (NVRTC not found), GBFIT_E_OOM
+ * (more than GBFIT_MAX_USER_MODELS models).  Thread-safe. ---- */
+#define GBFIT_USER_MODEL_BASE 100
+#define GBFIT_MAX_USER_MODELS 64
+int gbfit_model_register(const char* source, const char* func_name, int n_params, int x_dims, int* model_id);
+
+/* Compiler log of the last gbfit_model_register call on any thread
+ * (NUL-terminated, truncated to cap bytes); *len = full length. */
+int gbfit_model_log(char* buf, size_t cap, size_t* len);
 
 /*
  * One fit (paper Section 2, Algorithm 1; the SciPy-style problem statement the
@@ -360,7 +394,8 @@ typedef struct gbfit_stats {
                                  fast path, 17 fast-path steps (count), 18 eigen
                                  decompositions (count), 19 Algorithm 2 iterations
                                  (count), 20 bounded non-full steps (count), 21 item start to
-                                 tile start, 22 tile loop (of 0), 23 spare */
+                                 tile start, 22 tile loop (of 0), 23 waits for streamed
+                                 chunks inside the tile loop (of 22) */
     double host_ms;           /* host wall time inside the run of fits (job set-up, launch,
                                  wait for the device, result copy)                    */
     double loop_busy_ms;      /* loop kernel, summed over CTAs: time in rounds' work    */

@@ -8,7 +8,8 @@ constants or helpers); the two meet only on the seeded inputs drawn by
 
 Contents
   models.py  h(x; p) and the analytic partials dh/dp for the four models,
-             vectorised NumPy FP64 (Section 2, Eqs. residual and jacobian).
+             vectorised NumPy FP64 (Section 2, Eqs. residual and jacobian);
+             any callable (X, p) -> (h, dh/dp) stands for a user-defined model.
   reduce.py  the per-evaluation quantities written from their definitions:
              r, J, cost f = r^T r / 2 (Eq. msqe), g = J^T r (Eq. gradient),
              B = J^T J (Eq. hessian, Gauss-Newton term), with 1/sigma row
@@ -20,7 +21,8 @@ Contents
              without detail, termination tests and pcov.
 
 Parity status per function (what pins it; see tests/test_oracle_*.py):
-  models.*             central differences; exact linear-model Jacobian
+  models.*             central differences; exact linear-model Jacobian;
+                       a callable equal to a built-in gives the built-in's fit
   reduce.evaluate      finite-difference gradient of the cost; Gauss-Newton
                        Hessian equals the true Hessian on noise-free data;
                        sum of split pieces equals the whole

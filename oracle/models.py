@@ -92,9 +92,15 @@ def poly2(X, p):
 _FUNCS = {GAUSS1D: gauss1d, DEXP: dexp, GAUSS2D: gauss2d, POLY2: poly2}
 
 
-def value_and_jac(model: int, X, p):
-    """(h, dh/dp) for model id `model` at parameters p; FP64."""
+def value_and_jac(model, X, p):
+    """(h, dh/dp) at parameters p; FP64.
+
+    model: a built-in model id, or a callable (X [xdims, m], p [n]) ->
+    (h [m], dh/dp [m, n]) -- a user-defined model (the paper's user-written
+    fit function, Section 2), whose partials the caller writes out."""
     X = np.asarray(X, dtype=np.float64)
     if X.ndim == 1:
         X = X[None, :]
-    return _FUNCS[model](X, np.asarray(p, dtype=np.float64))
+    f = model if callable(model) else _FUNCS[model]
+    h, J = f(X, np.asarray(p, dtype=np.float64))
+    return np.asarray(h, dtype=np.float64), np.asarray(J, dtype=np.float64)

@@ -20,6 +20,9 @@
 #include "gbfit.h"
 #include "kernels.cuh"
 #include "models.cuh"
+#include "user_models.h"
+#include <map>
+#include <utility>
 
 using namespace gbfit;
 
@@ -42,6 +45,17 @@ int fail(int code, const char* fmt, ...) {
     g_err = buf;
     return code;
 }
+
+}  // namespace
+
+namespace gbfit {
+int set_error(int code, const char* msg) {
+    g_err = msg;
+    return code;
+}
+}  // namespace gbfit
+
+namespace {
 
 #define CUDA_TRY(x)                                                                          \
     do {                                                                                     \
@@ -98,10 +112,10 @@ struct Ctx {
     // one-node graphs holding the cooperative loop launch, per precision (a
     // graph launch costs the host less than a direct cooperative launch);
     // bound to the job buffer's address
-    cudaGraphExec_t loop_exec[2] = {nullptr, nullptr};
+    std::map<std::pair<int, int>, cudaGraphExec_t> loop_exec;   // (kernel set, precision)
     void drop_graphs() {
-        for (int p = 0; p < 2; ++p)
-            if (loop_exec[p]) { cudaGraphExecDestroy(loop_exec[p]); loop_exec[p] = nullptr; }
+        for (auto& kv : loop_exec) cudaGraphExecDestroy(kv.second);
+        loop_exec.clear();
     }
 
     Engine* eng_dev() const { return (Engine*)job; }
@@ -170,20 +184,28 @@ int ensure(Ctx* c, const JobLayout& L, size_t ntiles, size_t ngroups) {
     return GBFIT_OK;
 }
 
+// Cooperative grid of a kernel set's loop kernel: every CTA resident.
+int loop_grid(const Ctx* c, const KernelSet* ks, int prec) {
+    int b = ks->blocks_per_sm[prec];
+    return c->sms * (b < 1 ? 1 : b);
+}
+
 // The cooperative loop launch (pass constants at p0, then rounds) as a
 // cached one-node graph.
-int loop_graph(Ctx* c, int prec, cudaGraphExec_t* out) {
-    if (!c->loop_exec[prec]) {
+int loop_graph(Ctx* c, const KernelSet* ks, int prec, cudaGraphExec_t* out) {
+    auto key = std::make_pair(ks->id, prec);
+    auto it = c->loop_exec.find(key);
+    if (it == c->loop_exec.end()) {
         cudaGraph_t g;
         CUDA_TRY(cudaGraphCreate(&g, 0));
         Engine* Ed = c->eng_dev();
         int do_init = 1;
         void* args[] = {&Ed, &do_init};
         cudaKernelNodeParams kp = {};
-        kp.func = kernel_fit_loop(prec);
-        kp.gridDim = dim3(c->grid_p[prec]);
+        kp.func = (void*)ks->fit_loop[prec];
+        kp.gridDim = dim3(loop_grid(c, ks, prec));
         kp.blockDim = dim3(EVAL_THREADS);
-        kp.sharedMemBytes = (unsigned)eval_dyn_smem(prec);
+        kp.sharedMemBytes = (unsigned)ks->dyn_smem[prec];
         kp.kernelParams = args;
         cudaGraphNode_t node;
         cudaError_t e = cudaGraphAddKernelNode(&node, g, nullptr, 0, &kp);
@@ -195,9 +217,9 @@ int loop_graph(Ctx* c, int prec, cudaGraphExec_t* out) {
         if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return fail(GBFIT_E_CUDA, "loop graph: %s", cudaGetErrorString(e));
-        c->loop_exec[prec] = ex;
+        it = c->loop_exec.emplace(key, ex).first;
     }
-    *out = c->loop_exec[prec];
+    *out = it->second;
     return GBFIT_OK;
 }
 
@@ -245,8 +267,8 @@ int tune_bucket(int64_t m) {
 // Shape of a batched / served fit: user values where given, else the table;
 // a fit smaller than its tile is one tile.
 void multi_shape(int model, int prec, int64_t m, int user_tile, int user_group, int* tile, int* group) {
-    int t, g;
-    {
+    int t = prec == PREC_MIXED ? 32768 : 4096, g = GROUP_TILES;   // user models: the table's defaults
+    if (model >= 0 && model < GBFIT_NUM_MODELS) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         int b = tune_bucket(m);
         t = g_tune.tile_points[model][prec][b];
@@ -305,7 +327,7 @@ gbfit_options defaults() {
 // Run nfits fits whose descriptors (data pointers already on the device) are
 // in hd[]; writes per-fit results into hr[].  One host-to-device copy of the
 // job buffer, one loop-kernel launch, one device-to-host copy of the results.
-int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::vector<double>>& p0s,
+int run_fits(Ctx* c, const KernelSet* ks, int prec, std::vector<FitDesc>& hd, const std::vector<std::vector<double>>& p0s,
              std::vector<FitResult>& hr, cudaStream_t s, int* rounds_out) {
     const auto t_host0 = std::chrono::steady_clock::now();
     size_t nf = hd.size();
@@ -348,7 +370,7 @@ int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::
     int64_t eval_launches = 0;
     {
         cudaGraphExec_t ex;
-        if ((rc = loop_graph(c, prec, &ex))) return rc;
+        if ((rc = loop_graph(c, ks, prec, &ex))) return rc;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (g_profiling) {
             CUDA_TRY(cudaEventCreate(&e0));
@@ -387,7 +409,7 @@ int run_fits(Ctx* c, int prec, std::vector<FitDesc>& hd, const std::vector<std::
         g_stats.eval_launches += eval_launches;
         g_stats.loop_busy_ms += acct[0] * 1e-6;
         g_stats.loop_wait_ms += acct[1] * 1e-6;
-        g_stats.loop_ctas += c->grid_p[prec];
+        g_stats.loop_ctas += loop_grid(c, ks, prec);
         for (size_t f = 0; f < nf; ++f) {
             for (int k = 0; k < 24; ++k) g_stats.phase_cycles[k] += hr[f].trace[k];
             g_stats.passes += hr[f].nfev;
@@ -482,16 +504,16 @@ int gbfit_default_options(gbfit_options* opt) {
 }
 
 int gbfit_model_info(int model_id, int* n_params, int* x_dims) {
-    if (model_id < 0 || model_id >= GBFIT_NUM_MODELS) return fail(GBFIT_E_INVALID_ARG, "unknown model %d", model_id);
-    if (n_params) *n_params = model_nparams(model_id);
-    if (x_dims) *x_dims = model_xdims(model_id);
+    int n, xd;
+    if (!model_shape(model_id, &n, &xd)) return fail(GBFIT_E_INVALID_ARG, "unknown model %d", model_id);
+    if (n_params) *n_params = n;
+    if (x_dims) *x_dims = xd;
     return GBFIT_OK;
 }
 
 static int check_common(int model_id, int x_layout, int dtype, const void* ydata, int* n) {
-    if (model_id < 0 || model_id >= GBFIT_NUM_MODELS) return fail(GBFIT_E_INVALID_ARG, "unknown model %d", model_id);
-    *n = model_nparams(model_id);
-    int xd = model_xdims(model_id);
+    int xd;
+    if (!model_shape(model_id, n, &xd)) return fail(GBFIT_E_INVALID_ARG, "unknown model %d", model_id);
     if (dtype != GBFIT_F32 && dtype != GBFIT_F64) return fail(GBFIT_E_INVALID_ARG, "unknown dtype %d", dtype);
     if (xd == 1 && x_layout != GBFIT_X_VEC) return fail(GBFIT_E_INVALID_ARG, "1D model needs GBFIT_X_VEC");
     if (xd == 2 && x_layout != GBFIT_X_SOA2 && x_layout != GBFIT_X_GRID)
@@ -524,6 +546,8 @@ static int single_fit(int model_id, const void* xdata, int64_t m, int x_layout, 
     bool bounded;
     if ((rc = check_params(a, &bounded))) return rc;
     if (eval_only) { bounded = false; o.max_nfev = 1; }
+    const KernelSet* ks;
+    if ((rc = kernels_for_model(model_id, &ks))) return rc;
     Ctx* c;
     if ((rc = get_ctx(&c))) return rc;
     std::lock_guard<std::mutex> lock(c->mu);
@@ -534,7 +558,7 @@ static int single_fit(int model_id, const void* xdata, int64_t m, int x_layout, 
     if ((rc = stage_data(c, x_layout == GBFIT_X_GRID ? nullptr : xdata, xbytes, ydata, (size_t)m * es, sigma,
                          (size_t)m * es, s, &sd))) return rc;
     std::vector<FitDesc> hd(1);
-    fill_desc(hd[0], a, o, bounded, m, false, c->grid_p[o.precision]);
+    fill_desc(hd[0], a, o, bounded, m, false, loop_grid(c, ks, o.precision));
     const void* x2 = (x_layout == GBFIT_X_SOA2) ? (const char*)sd.x + (size_t)m * es : nullptr;
     if (sigma && o.precision == GBFIT_PREC_FP64) {
         bool changed = false;
@@ -546,7 +570,7 @@ static int single_fit(int model_id, const void* xdata, int64_t m, int x_layout, 
     std::vector<std::vector<double>> p0s(1, std::vector<double>(p0, p0 + n));
     std::vector<FitResult> hr;
     int rounds = 0;
-    rc = run_fits(c, o.precision, hd, p0s, hr, s, &rounds);
+    rc = run_fits(c, ks, o.precision, hd, p0s, hr, s, &rounds);
     if (rc) return rc;
     *out = hr[0];
     out->rounds = rounds;
@@ -562,7 +586,8 @@ int gbfit_curve_fit(int model_id, const void* xdata, int64_t m, int x_layout, co
     int rc = single_fit(model_id, xdata, m, x_layout, grid_wh, ydata, sigma, dtype, p0, lb, ub, opt, &r,
                         cuda_stream, false);
     if (rc) return rc;
-    int n = model_nparams(model_id);
+    int n = 0, xd = 0;
+    model_shape(model_id, &n, &xd);
     if (popt) for (int i = 0; i < n; ++i) popt[i] = r.popt[i];
     if (pcov) for (int i = 0; i < n * n; ++i) pcov[i] = r.pcov[i];
     if (cost) *cost = r.cost;
@@ -581,7 +606,8 @@ int gbfit_evaluate(int model_id, const void* xdata, int64_t m, int x_layout, con
     int rc = single_fit(model_id, xdata, m, x_layout, grid_wh, ydata, sigma, dtype, p, nullptr, nullptr, &o, &r,
                         cuda_stream, true);
     if (rc) return rc;
-    int n = model_nparams(model_id);
+    int n = 0, xd = 0;
+    model_shape(model_id, &n, &xd);
     int K = n_tri(n) + n + 1;
     for (int k = 0; k < K; ++k) out[k] = r.tot[k];
     out[K - 1] = 0.5 * r.tot[K - 1];
@@ -610,6 +636,8 @@ int gbfit_curve_fit_batch(int model_id, int nfits, const int64_t* offsets, const
         if ((rc = check_params(a, &b))) return fail(rc, "fit %d: %s", f, g_err.c_str());
         bnd[f] = b;
     }
+    const KernelSet* ks;
+    if ((rc = kernels_for_model(model_id, &ks))) return rc;
     Ctx* c;
     if ((rc = get_ctx(&c))) return rc;
     std::lock_guard<std::mutex> lock(c->mu);
@@ -637,7 +665,7 @@ int gbfit_curve_fit_batch(int model_id, int nfits, const int64_t* offsets, const
         p0s[f].assign(p0 + (size_t)f * n, p0 + (size_t)(f + 1) * n);
     }
     std::vector<FitResult> hr;
-    rc = run_fits(c, o.precision, hd, p0s, hr, s, nullptr);
+    rc = run_fits(c, ks, o.precision, hd, p0s, hr, s, nullptr);
     if (rc) return rc;
     for (int f = 0; f < nfits; ++f) {
         const FitResult& r = hr[f];
@@ -674,7 +702,8 @@ int gbfit_tune_set(const gbfit_tune_table* in) {
 }
 
 int gbfit_tune_shape(int model_id, int precision, int64_t m, int* tile_points, int* group_tiles) {
-    if (model_id < 0 || model_id >= GBFIT_NUM_MODELS) return fail(GBFIT_E_INVALID_ARG, "unknown model %d", model_id);
+    if (model_id < 0 || model_id >= GBFIT_NUM_MODELS)
+        return fail(GBFIT_E_INVALID_ARG, "model %d: the tile table covers the built-in models", model_id);
     if (precision != GBFIT_PREC_FP64 && precision != GBFIT_PREC_MIXED) return fail(GBFIT_E_INVALID_ARG, "unknown precision %d", precision);
     if (m < 1) return fail(GBFIT_E_INVALID_ARG, "m must be >= 1");
     int t, g;
@@ -686,7 +715,8 @@ int gbfit_tune_shape(int model_id, int precision, int64_t m, int* tile_points, i
 
 int gbfit_autotune(int model_id, int precision, int64_t m_max, int64_t points_per_run, gbfit_tune_table* out,
                    void* cuda_stream) {
-    if (model_id < 0 || model_id >= GBFIT_NUM_MODELS) return fail(GBFIT_E_INVALID_ARG, "unknown model %d", model_id);
+    if (model_id < 0 || model_id >= GBFIT_NUM_MODELS)
+        return fail(GBFIT_E_INVALID_ARG, "model %d: the tile table covers the built-in models", model_id);
     if (precision != GBFIT_PREC_FP64 && precision != GBFIT_PREC_MIXED) return fail(GBFIT_E_INVALID_ARG, "unknown precision %d", precision);
     if (m_max < 1 || m_max > ((int64_t)1 << 31)) return fail(GBFIT_E_INVALID_ARG, "m_max out of range");
     const int64_t ppr = points_per_run > 0 ? points_per_run : ((int64_t)1 << 25);
@@ -770,7 +800,7 @@ int gbfit_autotune(int model_id, int precision, int64_t m_max, int64_t points_pe
                     std::vector<FitResult> hr;
                     std::vector<FitDesc> hdc = hd;
                     e = cudaEventRecord(e0, s);
-                    if (e == cudaSuccess && (rc = run_fits(c, precision, hdc, p0s, hr, s, nullptr))) return cleanup(rc);
+                    if (e == cudaSuccess && (rc = run_fits(c, builtin_kernels(), precision, hdc, p0s, hr, s, nullptr))) return cleanup(rc);
                     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
                     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
@@ -885,6 +915,7 @@ extern "C" int gbfit_evaluate_noalloc(int model_id, const void* xdata, int64_t m
                                       void* cuda_stream) {
     int n, rc;
     if ((rc = check_common(model_id, x_layout, dtype, ydata, &n))) return rc;
+    if (model_id >= GBFIT_NUM_MODELS) return fail(GBFIT_E_UNSUPPORTED, "the allocation-free entry point takes built-in models");
     if (!p || !out) return fail(GBFIT_E_INVALID_ARG, "p and out must not be NULL");
     if (precision != GBFIT_PREC_FP64 && precision != GBFIT_PREC_MIXED) return fail(GBFIT_E_INVALID_ARG, "unknown precision %d", precision);
     if (tile_points < 0 || tile_points > (1 << 24)) return fail(GBFIT_E_INVALID_ARG, "tile_points out of range");
@@ -1166,6 +1197,7 @@ int gbfit_server_submit(gbfit_server* s, const gbfit_request* r, uint64_t* ticke
     if (!s || !r) return fail(GBFIT_E_INVALID_ARG, "server and request must not be NULL");
     int n, rc;
     if ((rc = check_common(r->model_id, r->x_layout, r->dtype, r->ydata, &n))) return rc;
+    if (r->model_id >= GBFIT_NUM_MODELS) return fail(GBFIT_E_UNSUPPORTED, "serving takes built-in models");
     if (r->m < n) return fail(GBFIT_E_INVALID_ARG, "m = %lld < n = %d", (long long)r->m, n);
     if (r->x_layout == GBFIT_X_GRID && (r->grid_w <= 0 || r->grid_h <= 0 || r->grid_w * r->grid_h != r->m))
         return fail(GBFIT_E_INVALID_ARG, "grid_w * grid_h must equal m");

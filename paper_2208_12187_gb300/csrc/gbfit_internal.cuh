@@ -1,7 +1,6 @@
 // Internal device/host data structures of libgbfit (not part of the C ABI).
 #pragma once
-#include <cstdint>
-#include <cuda_runtime.h>
+#include "rtc_compat.cuh"
 
 namespace gbfit {
 

@@ -5,10 +5,10 @@
 
 namespace gbfit {
 
-void* kernel_eval_round_fp64() { return (void*)eval_round_kernel<PREC_FP64>; }
-void* kernel_init_fits_fp64() { return (void*)init_fits_kernel<PREC_FP64>; }
-void* kernel_fit_loop_fp64() { return (void*)fit_loop_kernel<PREC_FP64>; }
-void* kernel_init_slots_fp64() { return (void*)init_slots_kernel<PREC_FP64>; }
+void* kernel_eval_round_fp64() { return (void*)eval_round_kernel<PREC_FP64, BuiltinModels>; }
+void* kernel_init_fits_fp64() { return (void*)init_fits_kernel<PREC_FP64, BuiltinModels>; }
+void* kernel_fit_loop_fp64() { return (void*)fit_loop_kernel<PREC_FP64, BuiltinModels>; }
+void* kernel_init_slots_fp64() { return (void*)init_slots_kernel<PREC_FP64, BuiltinModels>; }
 
 // Resident CTAs per SM of the round kernels (the loop kernel's cooperative
 // grid is this times the SM count, so both kernels must fit it).
@@ -16,13 +16,13 @@ int eval_blocks_per_sm_fp64() {
     const int dyn = (int)(0);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(eval_round_kernel<PREC_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-        cudaFuncSetAttribute(fit_loop_kernel<PREC_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        cudaFuncSetAttribute(eval_round_kernel<PREC_FP64, BuiltinModels>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        cudaFuncSetAttribute(fit_loop_kernel<PREC_FP64, BuiltinModels>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         attr_set = true;
     }
     int b = 0, b2 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, eval_round_kernel<PREC_FP64>, EVAL_THREADS, dyn);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fit_loop_kernel<PREC_FP64>, EVAL_THREADS, dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, eval_round_kernel<PREC_FP64, BuiltinModels>, EVAL_THREADS, dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fit_loop_kernel<PREC_FP64, BuiltinModels>, EVAL_THREADS, dyn);
     return b < b2 ? b : b2;
 }
 size_t eval_dyn_smem_fp64() { return 0; }

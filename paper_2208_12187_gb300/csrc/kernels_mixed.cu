@@ -5,10 +5,10 @@
 
 namespace gbfit {
 
-void* kernel_eval_round_mixed() { return (void*)eval_round_kernel<PREC_MIXED>; }
-void* kernel_init_fits_mixed() { return (void*)init_fits_kernel<PREC_MIXED>; }
-void* kernel_fit_loop_mixed() { return (void*)fit_loop_kernel<PREC_MIXED>; }
-void* kernel_init_slots_mixed() { return (void*)init_slots_kernel<PREC_MIXED>; }
+void* kernel_eval_round_mixed() { return (void*)eval_round_kernel<PREC_MIXED, BuiltinModels>; }
+void* kernel_init_fits_mixed() { return (void*)init_fits_kernel<PREC_MIXED, BuiltinModels>; }
+void* kernel_fit_loop_mixed() { return (void*)fit_loop_kernel<PREC_MIXED, BuiltinModels>; }
+void* kernel_init_slots_mixed() { return (void*)init_slots_kernel<PREC_MIXED, BuiltinModels>; }
 
 // Resident CTAs per SM of the round kernels (the loop kernel's cooperative
 // grid is this times the SM count, so both kernels must fit it).
@@ -16,13 +16,13 @@ int eval_blocks_per_sm_mixed() {
     const int dyn = (int)(RING_BYTES);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(eval_round_kernel<PREC_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-        cudaFuncSetAttribute(fit_loop_kernel<PREC_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        cudaFuncSetAttribute(eval_round_kernel<PREC_MIXED, BuiltinModels>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        cudaFuncSetAttribute(fit_loop_kernel<PREC_MIXED, BuiltinModels>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         attr_set = true;
     }
     int b = 0, b2 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, eval_round_kernel<PREC_MIXED>, EVAL_THREADS, dyn);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fit_loop_kernel<PREC_MIXED>, EVAL_THREADS, dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, eval_round_kernel<PREC_MIXED, BuiltinModels>, EVAL_THREADS, dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fit_loop_kernel<PREC_MIXED, BuiltinModels>, EVAL_THREADS, dyn);
     return b < b2 ? b : b2;
 }
 size_t eval_dyn_smem_mixed() { return RING_BYTES; }

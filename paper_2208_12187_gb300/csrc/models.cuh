@@ -132,6 +132,8 @@ struct MixedParams {
 // h = A exp(-(x-mu)^2/(2 s^2)) + c,  p = (A, mu, s, c)
 struct MGauss1D {
     static constexpr int N = 4;
+    static constexpr int DIM = 1;               // coordinate dimensions
+    static constexpr bool WARP_PREP = false;
     __device__ static void prep_plain(const double* p, double* pd) {
         double s = p[2];
         double is2 = 1.0 / (s * s);
@@ -188,6 +190,8 @@ struct MGauss1D {
 // h = a1 exp(-x/t1) + a2 exp(-x/t2) + c,  p = (a1, t1, a2, t2, c)
 struct MDexp {
     static constexpr int N = 5;
+    static constexpr int DIM = 1;               // coordinate dimensions
+    static constexpr bool WARP_PREP = false;
     __device__ static void prep_plain(const double* p, double* pd) {
         double k1 = 1.0 / p[1], k2 = 1.0 / p[3];
         pd[0] = p[0]; pd[1] = k1; pd[2] = p[2]; pd[3] = k2; pd[4] = p[4];
@@ -237,6 +241,8 @@ struct MDexp {
 // h = A exp(-u^2/(2 sx^2) - v^2/(2 sy^2)) + c,  p = (A, x0, y0, sx, sy, th, c)
 struct MGauss2D {
     static constexpr int N = 7;
+    static constexpr int DIM = 2;               // coordinate dimensions
+    static constexpr bool WARP_PREP = true;
     static constexpr int PACK = 2;
     __device__ static void prep_plain(const double* p, double* pd) {
         double s, c;
@@ -381,6 +387,8 @@ struct MGauss2D {
 // h = p0 + p1 x + p2 x^2  (linear in p)
 struct MPoly2 {
     static constexpr int N = 3;
+    static constexpr int DIM = 1;               // coordinate dimensions
+    static constexpr bool WARP_PREP = false;
     static constexpr int PACK = 0;
     __device__ static void eval_mixed2(const float*, float2, float2, float2&, float2&, float2*) {}
     __device__ static void prep_plain(const double* p, double* pd) { pd[0] = p[0]; pd[1] = p[1]; pd[2] = p[2]; }
@@ -409,5 +417,29 @@ __host__ __device__ inline int model_nparams(int model) {
     return 0;
 }
 __host__ __device__ inline int model_xdims(int model) { return model == 2 ? 2 : 1; }
+
+// Mixed pass constants of model M, called by a whole warp (models with a
+// warp-parallel prep use all lanes, the others lane 0).  tmp: 16 floats.
+template <class M>
+__device__ __forceinline__ void prep_mixed_model(const MixedParams& P, float* pf, float* tmp) {
+    if constexpr (M::WARP_PREP) M::prep_mixed_warp(P, pf, tmp);
+    else if ((threadIdx.x & 31) == 0) M::prep_mixed(P, pf);
+}
+
+// A model set: the kernels are instantiated once per set and reach a fit's
+// model through dispatch(id, f), which calls f with a value of the model's
+// type.  The built-in registry is one set; a user-defined model compiled at
+// run time is a set of one.
+struct BuiltinModels {
+    template <class F>
+    __device__ __forceinline__ static void dispatch(int model, F&& f) {
+        switch (model) {
+            case 0: f(MGauss1D{}); break;
+            case 1: f(MDexp{}); break;
+            case 2: f(MGauss2D{}); break;
+            case 3: f(MPoly2{}); break;
+        }
+    }
+};
 
 }  // namespace gbfit

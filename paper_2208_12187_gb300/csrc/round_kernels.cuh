@@ -2,7 +2,7 @@
 // Per-precision device machinery of libgbfit (included by kernels_mixed.cu
 // and kernels_fp64.cu, one instantiation each, compiled in parallel).
 //
-//   eval_round_kernel<PREC>  one trust-region iteration for every running fit:
+//   eval_round_kernel<PREC, MS>  one trust-region iteration for every running fit:
 //       each CTA takes (fit, tile) work items, evaluates model, residual and
 //       Jacobian row per point in registers, reduces J^T J, J^T r and cost
 //       sums over its tile (never writing J), and writes one tile partial.
@@ -11,13 +11,10 @@
 //       trust-region step for it (trf_step), which prepares the next
 //       evaluation point.  No CTA waits for another: the hand-off is an
 //       atomic arrival counter (last arriver continues).
-//   fit_loop_kernel<PREC>  the same rounds in one cooperative launch,
+//   fit_loop_kernel<PREC, MS>  the same rounds in one cooperative launch,
 //       separated by a grid-wide barrier (bounded waits), until no fit runs
 //       or the round cap is reached.
 //   init_fits_kernel / init_slots_kernel  pass constants at p0.
-#include <cstdint>
-#include <type_traits>
-#include <cuda_runtime.h>
 #include "gbfit_internal.cuh"
 #include "models.cuh"
 #include "trf_device.cuh"
@@ -337,6 +334,7 @@ struct RingState {
     float* buf;                  // [NST][STAGE_FLOATS]
     unsigned seq;                // chunks consumed by this CTA so far (same in all threads)
     int* fail;                   // shared flag: a bounded wait gave up
+    long long wait_cycles;       // thread 0: cycles spent waiting for chunks of the current tile
 };
 
 template <class M, int LAYOUT, int WK>
@@ -396,7 +394,9 @@ __device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0,
     for (int c = 0; c < nch; ++c) {
         unsigned g = R.seq + c;
         int s = g % NST;
+        long long tw = (t == 0) ? clock64() : 0;
         if (!mbar_wait(R.bar + s, (g / NST) & 1)) *R.fail = 1;
+        if (t == 0) R.wait_cycles += clock64() - tw;
         if (*R.fail) break;
         const float* B = R.buf + s * STAGE_FLOATS;
         const int cnt = count(c);
@@ -538,7 +538,7 @@ __device__ void eval_tile_dispatch(const RoundSmem& sm, int64_t i0, int64_t i1, 
 #define RB_CASE(LAY, WKV)                                                                              \
         if (f64) tile_points<M, PREC, double, LAY, WKV, true>(d, pfl, pdl, i0, i1, check, acc, bad);   \
         else tile_points<M, PREC, float, LAY, WKV, true>(d, pfl, pdl, i0, i1, check, acc, bad);
-        if (M::N == 7) {
+        if (M::DIM == 2) {
             if (d.layout == X_GRID) {
                 if (wk == W_NONE) { RB_CASE(X_GRID, W_NONE) } else if (wk == W_ARRAY) { RB_CASE(X_GRID, W_ARRAY) } else { RB_CASE(X_GRID, W_SIGMA) }
             } else {
@@ -559,7 +559,7 @@ __device__ void eval_tile_dispatch(const RoundSmem& sm, int64_t i0, int64_t i1, 
         if (f64) tile_points<M, PREC, double, LAY, WKV>(d, pfl, pdl, i0, i1, check, acc, bad);         \
         else tile_points<M, PREC, float, LAY, WKV>(d, pfl, pdl, i0, i1, check, acc, bad);              \
     }
-    if (M::N == 7) {
+    if (M::DIM == 2) {
         if (d.layout == X_GRID) {
             if (wk == W_NONE) { GB_CASE(X_GRID, W_NONE) } else if (wk == W_ARRAY) { GB_CASE(X_GRID, W_ARRAY) } else { GB_CASE(X_GRID, W_SIGMA) }
         } else {
@@ -571,7 +571,7 @@ __device__ void eval_tile_dispatch(const RoundSmem& sm, int64_t i0, int64_t i1, 
 #undef GB_CASE
 }
 
-template <class M, int PREC>
+template <class M, int PREC, class MS>
 __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, RingState& R, long long t_item) {
     using AT = typename AccT<PREC>::T;
     constexpr int N = M::N;
@@ -583,6 +583,7 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
     if (i1 > d.m) i1 = d.m;
     bool check = sm.flag[1] == PH_INIT;
     long long t_tile = clock64();
+    R.wait_cycles = 0;
     int bad = 0;
     AT acc[K];
     eval_tile_dispatch<M, PREC>(sm, i0, i1, check, bad, acc, R);
@@ -642,9 +643,10 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
         trace_bump(stp->trace, TR_TILE, (unsigned long long)(sm.t_mark - t_tile));
         trace_bump(stp->trace, TR_PRE_TILE, (unsigned long long)(t_tile - t_item));
         trace_bump(stp->trace, TR_TILE_LOOP, (unsigned long long)(sm.t_loop - t_tile));
+        trace_bump(stp->trace, TR_RING_WAIT, (unsigned long long)R.wait_cycles);
     }
     __syncthreads();
-    trf_step<PREC>(d, stp, E.results + fit, sm.trf, E.running);
+    trf_step<PREC, MS>(d, stp, E.results + fit, sm.trf, E.running);
     __syncthreads();
 }
 
@@ -684,7 +686,7 @@ __device__ __forceinline__ void round_setup(RoundSmem& sm, float* ring_buf, Ring
 // grid-stride (static) or the next unclaimed item from the round's counter
 // (dynamic: CTAs that finish early take more, so no CTA ends a round far
 // behind the others).  Which CTA processes an item does not change any sum.
-template <int PREC>
+template <int PREC, class MS>
 __device__ __forceinline__ void run_items(RoundSmem& sm, const Engine& E, RingState& R, int first,
                                           int* next_item) {
     int n_items = *E.n_items;
@@ -717,12 +719,8 @@ __device__ __forceinline__ void run_items(RoundSmem& sm, const Engine& E, RingSt
             }
             continue;
         }
-        switch (sm.desc.model) {
-            case 0: process_item<MGauss1D, PREC>(sm, E, wi.fit, wi.tile, R, t_item); break;
-            case 1: process_item<MDexp, PREC>(sm, E, wi.fit, wi.tile, R, t_item); break;
-            case 2: process_item<MGauss2D, PREC>(sm, E, wi.fit, wi.tile, R, t_item); break;
-            case 3: process_item<MPoly2, PREC>(sm, E, wi.fit, wi.tile, R, t_item); break;
-        }
+        MS::dispatch(sm.desc.model,
+                     [&](auto m) { process_item<decltype(m), PREC, MS>(sm, E, wi.fit, wi.tile, R, t_item); });
         if (next_item) {
             if (threadIdx.x == 0) sm.flag[0] = (int)gridDim.x + atomicAdd(next_item, 1);
             __syncthreads();
@@ -734,14 +732,14 @@ __device__ __forceinline__ void run_items(RoundSmem& sm, const Engine& E, RingSt
     }
 }
 
-template <int PREC>
+template <int PREC, class MS>
 __global__ void __launch_bounds__(EVAL_THREADS, 2) eval_round_kernel(const Engine* __restrict__ Ep) {
     __shared__ RoundSmem sm;
     extern __shared__ __align__(128) float ring_buf[];
     stage_engine(sm, Ep);
     RingState R;
     round_setup<PREC>(sm, ring_buf, R);
-    run_items<PREC>(sm, sm.eng, R, blockIdx.x, nullptr);
+    run_items<PREC, MS>(sm, sm.eng, R, blockIdx.x, nullptr);
 }
 
 // ---- grid-wide round barrier of the persistent loop.  The loop kernel is
@@ -813,7 +811,7 @@ __device__ inline int grid_round_end(Engine* Ed, const Engine& E, int* ctl_smem,
 // rounds of run_items separated by the grid barrier until no fit runs or the
 // round cap is reached.  One cooperative launch replaces a graph of
 // per-round kernels.
-template <int PREC>
+template <int PREC, class MS>
 __global__ void __launch_bounds__(EVAL_THREADS, 2) fit_loop_kernel(const Engine* __restrict__ Ep, int do_init) {
     __shared__ RoundSmem sm;
     extern __shared__ __align__(128) float ring_buf[];
@@ -860,7 +858,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) fit_loop_kernel(const Engine*
                 int l = threadIdx.x;
                 if (l < 8) { sm.trf.vec[VX][l] = (l < d.n) ? st->x[l] : 0.0; sm.trf.vec[VXT][l] = sm.trf.vec[VX][l]; }
                 __syncwarp();
-                prep_pass<PREC>(d, st, sm.trf);
+                prep_pass<PREC, MS>(d, st, sm.trf);
             }
             __syncthreads();
         }
@@ -871,7 +869,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) fit_loop_kernel(const Engine*
     unsigned long long* acct = reinterpret_cast<unsigned long long*>(E.out) + 2;
     while (true) {
         unsigned long long t0 = global_ns();
-        run_items<PREC>(sm, E, R, first, E.sm_cnt + SM_IDS);
+        run_items<PREC, MS>(sm, E, R, first, E.sm_cnt + SM_IDS);
         unsigned long long t1 = global_ns();
         int c = grid_round_end(Ed, E, &sm.ctl, true);
         if (threadIdx.x == 0) {
@@ -886,7 +884,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) fit_loop_kernel(const Engine*
 }
 
 // Pass constants for the first evaluation (at p0): base = trial = p0.
-template <int PREC>
+template <int PREC, class MS>
 __global__ void init_fits_kernel(const Engine* __restrict__ Ep) {
     __shared__ TrfSmem S;
     const Engine E = *Ep;
@@ -897,14 +895,14 @@ __global__ void init_fits_kernel(const Engine* __restrict__ Ep) {
         int l = threadIdx.x;
         if (l < 8) { S.vec[VX][l] = (l < d.n) ? st->x[l] : 0.0; S.vec[VXT][l] = S.vec[VX][l]; }
         __syncwarp();
-        prep_pass<PREC>(d, st, S);
+        prep_pass<PREC, MS>(d, st, S);
         __syncwarp();
     }
 }
 
 // Pass constants at p0 for the listed fits only (serving: newly admitted
 // fits join while others are mid-fit).
-template <int PREC>
+template <int PREC, class MS>
 __global__ void init_slots_kernel(const Engine* __restrict__ Ep, const int* __restrict__ slots, int count) {
     __shared__ TrfSmem S;
     const Engine E = *Ep;
@@ -915,7 +913,7 @@ __global__ void init_slots_kernel(const Engine* __restrict__ Ep, const int* __re
         int l = threadIdx.x;
         if (l < 8) { S.vec[VX][l] = (l < d.n) ? st->x[l] : 0.0; S.vec[VXT][l] = S.vec[VX][l]; }
         __syncwarp();
-        prep_pass<PREC>(d, st, S);
+        prep_pass<PREC, MS>(d, st, S);
         __syncwarp();
     }
 }

@@ -53,7 +53,7 @@ struct FitResult {
 // Phases timed (clock64, SM cycles) inside the step, summed per fit.
 enum TracePhase { TR_TILE = 0, TR_COMBINE, TR_LOGIC, TR_EIGEN, TR_C_FENCE, TR_STEP, TR_PREP, TR_FINISH,
                   TR_C_GROUP, TR_C_FINAL, TR_E_WARM, TR_E_J32, TR_E_NS, TR_E_RR, TR_E_SWEEPS, TR_E_REFINES,
-                  TR_GN, TR_N_GN, TR_N_EIG, TR_N_ALG2IT, TR_N_BOUNDED, TR_PRE_TILE, TR_TILE_LOOP, TR_RES3 };
+                  TR_GN, TR_N_GN, TR_N_EIG, TR_N_ALG2IT, TR_N_BOUNDED, TR_PRE_TILE, TR_TILE_LOOP, TR_RING_WAIT };
 
 // Shared-memory workspace of the warp that runs one fit's step.
 struct TrfSmem {

@@ -341,7 +341,7 @@ __device__ __forceinline__ void cl_scaling(const FitDesc& d, const FitState* st,
 }
 
 // Pass constants for evaluating xt relative to x (warp 0).
-template <int PREC>
+template <int PREC, class MS>
 __device__ void prep_pass(const FitDesc& d, FitState* st, TrfSmem& S) {
     int l = threadIdx.x & 31;
     int n = d.n;
@@ -357,15 +357,7 @@ __device__ void prep_pass(const FitDesc& d, FitState* st, TrfSmem& S) {
         __syncwarp();
         S.pfs[l] = 0.0f;
         __syncwarp();
-        if (d.model == 2) {
-            MGauss2D::prep_mixed_warp(S.mp, S.pfs, S.Af);
-        } else if (l == 0) {
-            switch (d.model) {
-                case 0: MGauss1D::prep_mixed(S.mp, S.pfs); break;
-                case 1: MDexp::prep_mixed(S.mp, S.pfs); break;
-                case 3: MPoly2::prep_mixed(S.mp, S.pfs); break;
-            }
-        }
+        MS::dispatch(d.model, [&](auto m) { prep_mixed_model<decltype(m)>(S.mp, S.pfs, S.Af); });
         if (l == 0) {
             const float C = float(d.f_scale);
             S.pfs[PF_C2] = C * C;
@@ -376,12 +368,7 @@ __device__ void prep_pass(const FitDesc& d, FitState* st, TrfSmem& S) {
     } else {
         if (l == 0) {
             for (int k = 0; k < PD; ++k) S.pds[k] = 0.0;
-            switch (d.model) {
-                case 0: MGauss1D::prep_plain(S.vec[VXT], S.pds); break;
-                case 1: MDexp::prep_plain(S.vec[VXT], S.pds); break;
-                case 2: MGauss2D::prep_plain(S.vec[VXT], S.pds); break;
-                case 3: MPoly2::prep_plain(S.vec[VXT], S.pds); break;
-            }
+            MS::dispatch(d.model, [&](auto m) { decltype(m)::prep_plain(S.vec[VXT], S.pds); });
         }
         if (l == 0) {
             S.pds[PD_C2] = d.f_scale * d.f_scale;
@@ -463,8 +450,12 @@ __device__ inline void write_result(const FitDesc& d, FitState* st, FitResult* r
 // threads of the CTA; L2 loads, since other CTAs wrote it in earlier rounds.
 // Issued before the final combine so that the loads overlap it; the
 // combine's closing barrier publishes the copy.
+#ifdef __CUDACC_RTC__
+constexpr int STATE_WORDS = GBFIT_STATE_WORDS;   // given by the host compiler's layout of FitState
+#else
 constexpr int STATE_WORDS = (int)(offsetof(FitState, trace) / sizeof(uint4));
 static_assert(offsetof(FitState, trace) % sizeof(uint4) == 0, "FitState prefix must be whole 16-byte words");
+#endif
 __device__ __forceinline__ void prefetch_state(const FitState* st, TrfSmem& S) {
     const uint4* src = reinterpret_cast<const uint4*>(st);
     uint4* dst = reinterpret_cast<uint4*>(&S.stc);
@@ -476,7 +467,7 @@ __device__ __forceinline__ void prefetch_state(const FitState* st, TrfSmem& S) {
 // the evaluation at st->xt that just finished; S.stc the state as it was
 // before this step (prefetch_state).  State is read from S.stc and written
 // to st (and to S.stc where a later phase of the same step reads it).
-template <int PREC>
+template <int PREC, class MS>
 __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem& S, int* running) {
     const FitState* cst = &S.stc;
     const int n = d.n;
@@ -762,8 +753,8 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
         double x = (l < n) ? S.vec[VX][l] : 0.0;
         double xt = x + step;
         if (d.bounded && l < n) {
-            if (xt <= d.lb[l]) xt = nextafter(d.lb[l], INFINITY);
-            if (xt >= d.ub[l]) xt = nextafter(d.ub[l], -INFINITY);
+            if (xt <= d.lb[l]) xt = nextafter(d.lb[l], (double)INFINITY);
+            if (xt >= d.ub[l]) xt = nextafter(d.ub[l], -(double)INFINITY);
         }
         if (l < 8) S.vec[VXT][l] = (l < n) ? xt : 0.0;
         // ||s_h||, ||w||, ||x|| for the next iteration's radius and xtol tests
@@ -788,7 +779,7 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
         __syncwarp();
     }
     trace_add(st, TR_STEP, tclk);
-    if (warp == 0) prep_pass<PREC>(d, st, S);
+    if (warp == 0) prep_pass<PREC, MS>(d, st, S);
     trace_add(st, TR_PREP, tclk);
 }
 

@@ -26,13 +26,15 @@ X_VEC, X_SOA2, X_GRID = 0, 1, 2
 F32, F64 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 FIT_INVALID_DATA, FIT_NUMERICAL, FIT_MAX_NFEV, FIT_GTOL, FIT_FTOL, FIT_XTOL, FIT_FTOL_XTOL = -2, -1, 0, 1, 2, 3, 4
-N_PARAMS = {0: 4, 1: 5, 2: 7, 3: 3}
+N_PARAMS = {0: 4, 1: 5, 2: 7, 3: 3}     # user-defined models are added by register_model
+USER_MODEL_BASE = 100
 
 EXPORTS = ["gbfit_version", "gbfit_last_error", "gbfit_default_options", "gbfit_model_info",
            "gbfit_curve_fit", "gbfit_curve_fit_batch", "gbfit_evaluate", "gbfit_tr_subproblem",
            "gbfit_stats_reset", "gbfit_stats_get", "gbfit_set_profiling", "gbfit_evaluate_noalloc",
            "gbfit_server_create", "gbfit_server_submit", "gbfit_server_step", "gbfit_server_poll",
-           "gbfit_server_destroy", "gbfit_tune_get", "gbfit_tune_set", "gbfit_tune_shape", "gbfit_autotune"]
+           "gbfit_server_destroy", "gbfit_tune_get", "gbfit_tune_set", "gbfit_tune_shape", "gbfit_autotune",
+           "gbfit_model_register", "gbfit_model_log"]
 
 
 class GbfitError(RuntimeError):
@@ -67,7 +69,7 @@ class Stats(ctypes.Structure):
 
 PHASES = ["tile", "combine", "logic", "eigen", "comb_fence", "step", "prep", "finish", "comb_group", "comb_final",
           "eig_warm", "eig_j32", "eig_ns", "eig_rr", "j32_sweeps", "refine_passes", "gn_path", "n_gn", "n_eig",
-          "n_alg2_iters", "n_bounded_nonfull", "pre_tile", "tile_loop", "spare3"]
+          "n_alg2_iters", "n_bounded_nonfull", "pre_tile", "tile_loop", "ring_wait"]
 
 
 class ServerConfig(ctypes.Structure):
@@ -130,6 +132,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.gbfit_tune_shape.argtypes = [I, I, I64, IP, IP]
     lib.gbfit_autotune.argtypes = [I, I, I64, I64, ctypes.POINTER(TuneTable), P]
     lib.gbfit_set_profiling.argtypes = [I]
+    lib.gbfit_model_register.argtypes = [ctypes.c_char_p, ctypes.c_char_p, I, I, IP]
+    lib.gbfit_model_log.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     for name in EXPORTS:
         getattr(lib, name)
     _LIB = lib
@@ -236,6 +240,30 @@ def _bounds(n, lb, ub):
     lbv = None if lb is None else np.ascontiguousarray(np.broadcast_to(np.asarray(lb, np.float64), (n,)))
     ubv = None if ub is None else np.ascontiguousarray(np.broadcast_to(np.asarray(ub, np.float64), (n,)))
     return lbv, ubv
+
+
+def register_model(source: str, n_params: int, x_dims: int = 1, func_name: str = "model") -> int:
+    """Compile a user-defined model h(x; p) and return its model id (gbfit_model_register).
+
+    source defines ``template <class T, class S> __device__ T <func_name>(const T* p, S x, S x2)``
+    in CUDA C++ over the library's dual-number type T (see include/gbfit.h).  Compiling takes
+    some seconds (NVRTC); the id works with curve_fit, curve_fit_batch and evaluate."""
+    lib = load()
+    mid = ctypes.c_int(-1)
+    rc = lib.gbfit_model_register(source.encode(), func_name.encode(), int(n_params), int(x_dims), ctypes.byref(mid))
+    _check(rc)
+    N_PARAMS[mid.value] = int(n_params)
+    return mid.value
+
+
+def model_log() -> str:
+    """Compiler log of the last register_model call."""
+    lib = load()
+    n = ctypes.c_size_t(0)
+    lib.gbfit_model_log(None, 0, ctypes.byref(n))
+    buf = ctypes.create_string_buffer(n.value + 1)
+    lib.gbfit_model_log(buf, n.value + 1, ctypes.byref(n))
+    return buf.value.decode(errors="replace")
 
 
 def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None, ub=None,

@@ -55,6 +55,7 @@ class Problem:
     lb: Optional[np.ndarray]
     ub: Optional[np.ndarray]
     truth: np.ndarray
+    n_user: Optional[int] = None     # parameter count of a user-defined model family
 
     @property
     def m(self) -> int:
@@ -62,7 +63,7 @@ class Problem:
 
     @property
     def n(self) -> int:
-        return N_PARAMS[self.model]
+        return self.n_user if self.n_user is not None else N_PARAMS[self.model]
 
     def coords(self) -> np.ndarray:
         """Explicit coordinates as float64 [xdims, m] (grid expanded)."""
@@ -225,6 +226,83 @@ class Batch:
         ub = None if self.ub is None else self.ub[k]
         return Problem(self.model, self.x[a:b], LAYOUT_VEC, None, self.y[a:b], sig,
                        self.p0[k].copy(), lb, ub, self.truth[k])
+
+
+# ---------------------------------------------------------------- user-defined model families
+# Fit functions a user supplies as source text (the library compiles them at
+# run time; the tests write each one a second time as NumPy for the oracle).
+# Here only their forward values, to synthesise observations.  The returned
+# Problem has model = -1 until the caller puts in the registered model id.
+USER_FAMILIES = {
+    # name: (n, x_dims, formula)
+    "lorentz1d": (4, 1, "A / (1 + ((x - x0) / g)^2) + c;  p = (A, x0, g, c)"),
+    "gauss2d_axis": (6, 2, "A exp(-(X-x0)^2/(2 sx^2) - (Y-y0)^2/(2 sy^2)) + c;  p = (A, x0, y0, sx, sy, c)"),
+    "damped_sine": (5, 1, "A exp(-x / tau) sin(w x + phi) + c;  p = (A, tau, w, phi, c)"),
+}
+
+
+def _user_forward(family: str, X: np.ndarray, p: np.ndarray) -> np.ndarray:
+    if family == "lorentz1d":
+        A, x0, g, c = p
+        u = (X[0] - x0) / g
+        return A / (1.0 + u * u) + c
+    if family == "gauss2d_axis":
+        A, x0, y0, sx, sy, c = p
+        return A * np.exp(-((X[0] - x0) ** 2) / (2 * sx * sx) - ((X[1] - y0) ** 2) / (2 * sy * sy)) + c
+    if family == "damped_sine":
+        A, tau, w, phi, c = p
+        return A * np.exp(-X[0] / tau) * np.sin(w * X[0] + phi) + c
+    raise ValueError(f"unknown family {family}")
+
+
+def user_family(family: str, m: int = 5000, seed: int = 0, dtype=np.float64, layout: int = LAYOUT_VEC,
+                with_sigma: bool = False) -> Problem:
+    """Seeded problem of a user-defined model family.
+
+    lorentz1d:    x ~ U[-10, 10], truth (4, 0.5, 1.5, 0.3), noise N(0, 0.05^2), p0 = truth (1 + U(-.2, .2))
+    gauss2d_axis: W x W pixel grid (W = round(sqrt(m))), truth (50, 0.45 W, 0.55 W, 0.1 W, 0.07 W, 2),
+                  noise N(0, 1), p0: A, sx, sy, c x (1 + U(-.2, .2)), centre + U(-1, 1);
+                  bounds sx, sy in [0.5, W]
+    damped_sine:  x ~ U[0, 10], truth (3, 4, 2.5, 0.4, 0.2), noise N(0, 0.05^2), p0 = truth (1 + U(-.05, .05))
+    with_sigma: per-point sigma ~ U[0.5, 1.5] (noise scaled by it)."""
+    rng = np.random.default_rng(seed)
+    n, xd, _ = USER_FAMILIES[family]
+    lb = ub = None
+    grid = None
+    if family == "lorentz1d":
+        truth = np.array([4.0, 0.5, 1.5, 0.3])
+        x = rng.uniform(-10.0, 10.0, size=m)
+        X = x[None, :]
+        noise = 0.05
+        p0 = truth * (1.0 + rng.uniform(-0.2, 0.2, size=n))
+    elif family == "gauss2d_axis":
+        W = int(round(math.sqrt(m)))
+        m = W * W
+        truth = np.array([50.0, 0.45 * W, 0.55 * W, 0.1 * W, 0.07 * W, 2.0])
+        i = np.arange(m, dtype=np.int64)
+        X = np.stack([(i % W).astype(np.float64), (i // W).astype(np.float64)])
+        x = None if layout == LAYOUT_GRID else X.copy()
+        grid = (W, W) if layout == LAYOUT_GRID else None
+        noise = 1.0
+        p0 = truth.copy()
+        for k in (0, 3, 4, 5):
+            p0[k] *= 1.0 + rng.uniform(-0.2, 0.2)
+        p0[1:3] += rng.uniform(-1.0, 1.0, size=2)
+        lb = np.array([-np.inf, -np.inf, -np.inf, 0.5, 0.5, -np.inf])
+        ub = np.array([np.inf, np.inf, np.inf, float(W), float(W), np.inf])
+    elif family == "damped_sine":
+        truth = np.array([3.0, 4.0, 2.5, 0.4, 0.2])
+        x = rng.uniform(0.0, 10.0, size=m)
+        X = x[None, :]
+        noise = 0.05
+        p0 = truth * (1.0 + rng.uniform(-0.05, 0.05, size=n))
+    else:
+        raise ValueError(f"unknown family {family}")
+    sig = rng.uniform(0.5, 1.5, size=m) if with_sigma else None
+    e = rng.normal(0.0, noise, size=m) * (sig if sig is not None else 1.0)
+    y = _user_forward(family, X, truth) + e
+    lay = layout if xd == 2 else LAYOUT_VEC
+    return Problem(-1, x, lay, grid, y, sig, p0, lb, ub, truth, n_user=n).astype(dtype)
 
 
 def log_uniform_int(rng, lo: float, hi: float, size) -> np.ndarray:
