@@ -452,6 +452,78 @@ def run_sweep(args):
             del x, y
 
 
+# user-defined models as a user would write them (compiled at run time)
+USER_GAUSS1D_SRC = r"""
+template <class T, class S>
+__device__ T model(const T* p, S x, S x2) {
+    T d = x - p[1];
+    return p[0] * exp(-square(d) / (2.0 * square(p[2]))) + p[3];
+}
+"""
+USER_LORENTZ_SRC = r"""
+template <class T, class S>
+__device__ T model(const T* p, S x, S x2) {
+    T u = (x - p[1]) / p[2];
+    return p[0] / (1.0 + square(u)) + p[3];
+}
+"""
+
+
+def run_user(args):
+    """User-defined models: run-time compile time, and fit throughput of the
+    built-in 1D Gaussian written as a user model against the built-in itself
+    (same data, same fits), plus a Lorentzian peak."""
+    import torch
+    from paper_2208_12187_gb300 import build, gbfit, synth
+    build.build()
+    gbfit.load()
+    t0 = time.perf_counter()
+    gid = gbfit.register_model(USER_GAUSS1D_SRC, 4)
+    t_compile = time.perf_counter() - t0
+    lid = gbfit.register_model(USER_LORENTZ_SRC, 4)
+    print(json.dumps({"mode": "user", "compile_s_per_model": t_compile, "nvrtc": "both precisions, one program"}))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def timed(fit, m):
+        for _ in range(3):
+            fit()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms, pts, out = 0.0, 0.0, None
+        steps = max(3, min(args.steps, int(2e8 // m) + 1))
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0.record()
+            out = fit()
+            e1.record()
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            pts += m * out["nfev"]
+        return out, ms / steps, pts / (ms / 1e3)
+
+    for m in [int(v) for v in args.sizes.split(",")]:
+        for prec, dt in (("mixed", torch.float32), ("fp64", torch.float64)):
+            if prec not in args.precisions.split(","):
+                continue
+            pr = synth.gauss1d(m, seed=0)
+            x = torch.as_tensor(pr.x).to(dt).cuda()
+            y = torch.as_tensor(pr.y).to(dt).cuda()
+            ob, msb, rb = timed(lambda: gbfit.curve_fit(pr.model, x, y, pr.p0, precision=prec, **TOL), m)
+            ou, msu, ru = timed(lambda: gbfit.curve_fit(gid, x, y, pr.p0, precision=prec, **TOL), m)
+            lp = synth.user_family("lorentz1d", m, seed=0)
+            lx = torch.as_tensor(lp.x).to(dt).cuda()
+            ly = torch.as_tensor(lp.y).to(dt).cuda()
+            ol, msl, rl = timed(lambda: gbfit.curve_fit(lid, lx, ly, lp.p0, precision=prec, **TOL), m)
+            print(json.dumps({"mode": "user", "m": m, "precision": prec,
+                              "builtin_gauss1d": {"fit_ms": msb, "point_iters_per_s": rb, "nfev": ob["nfev"]},
+                              "user_gauss1d": {"fit_ms": msu, "point_iters_per_s": ru, "nfev": ou["nfev"],
+                                               "rate_vs_builtin": ru / rb,
+                                               "popt_rel_diff_vs_builtin": relerr_vec(ou["popt"], ob["popt"])},
+                              "user_lorentz1d": {"fit_ms": msl, "point_iters_per_s": rl, "nfev": ol["nfev"],
+                                                 "status": ol["status"]}}))
+            del x, y, lx, ly
+
+
 def run_batch(args):
     """4,096 ragged double-exponential fits in one batched launch (mixed), with
     tile shapes from the autotuner, against the plain FP64 one-fit-at-a-time
@@ -688,6 +760,7 @@ def main():
     ap.add_argument("--precisions", default="mixed,fp64")
     ap.add_argument("--oracle-sample", type=int, default=64)
     ap.add_argument("--serve", action="store_true")
+    ap.add_argument("--user", action="store_true", help="user-defined models (run-time compiled) vs built-in")
     ap.add_argument("--compare", action="store_true",
                     help="headline workload: implicit grid vs explicit coordinates vs plain FP64, against the oracle")
     ap.add_argument("--serve-requests", type=int, default=20000)
@@ -708,6 +781,8 @@ def main():
         return run_batch(args)
     if args.serve:
         return run_serve(args)
+    if args.user:
+        return run_user(args)
     if args.compare:
         return run_compare(args)
     rank, local, world = dist_setup(args)

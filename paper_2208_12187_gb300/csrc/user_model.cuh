@@ -27,7 +27,11 @@
 //   tanh a:  sinh(da) / (cosh a cosh a')
 //   atan a:  atan(da / (1 + a a'))
 // Each keeps the difference to a few FP32 roundings of itself, however small
-// it is against the values.
+// it is against the values.  The base point itself is p rounded to FP32 plus
+// a first-order correction lo carried alongside (each parameter's rounding
+// error p - float(p), propagated with the partials), so that the residual at
+// p is not off by the parameters' rounding (which, near convergence, exceeds
+// the steps themselves).
 //
 // The user source must define, at namespace scope,
 //     template <class T, class S> __device__ T model(const T* p, S x, S x2);
@@ -148,7 +152,8 @@ __device__ __forceinline__ DualD<N> square(const DualD<N>& a) { return scaled(a,
 // ------------------------------------------------------------------ FP32 difference-dual number
 template <int N>
 struct DiffF {
-    float v;      // value at the base point p
+    float v;      // value at the FP32-rounded base point
+    float lo;     // first-order correction for the parameters' rounding: value at p = v + lo
     float d;      // value at p' minus value at p
     float g[N];   // partials at p'
 };
@@ -156,6 +161,7 @@ template <int N>
 __device__ __forceinline__ DiffF<N> chain(const DiffF<N>& a, float v, float d, float k) {
     DiffF<N> r;
     r.v = v;
+    r.lo = k * a.lo;
     r.d = d;
 #pragma unroll
     for (int j = 0; j < N; ++j) r.g[j] = k * a.g[j];
@@ -165,6 +171,7 @@ template <int N>
 __device__ __forceinline__ DiffF<N> operator+(const DiffF<N>& a, const DiffF<N>& b) {
     DiffF<N> r;
     r.v = a.v + b.v;
+    r.lo = a.lo + b.lo;
     r.d = a.d + b.d;
 #pragma unroll
     for (int j = 0; j < N; ++j) r.g[j] = a.g[j] + b.g[j];
@@ -174,6 +181,7 @@ template <int N>
 __device__ __forceinline__ DiffF<N> operator-(const DiffF<N>& a, const DiffF<N>& b) {
     DiffF<N> r;
     r.v = a.v - b.v;
+    r.lo = a.lo - b.lo;
     r.d = a.d - b.d;
 #pragma unroll
     for (int j = 0; j < N; ++j) r.g[j] = a.g[j] - b.g[j];
@@ -186,6 +194,7 @@ __device__ __forceinline__ DiffF<N> operator*(const DiffF<N>& a, const DiffF<N>&
     DiffF<N> r;
     const float at = a.v + a.d, bt = b.v + b.d;
     r.v = a.v * b.v;
+    r.lo = fmaf(at, b.lo, bt * a.lo);
     r.d = fmaf(a.v, b.d, a.d * bt);
 #pragma unroll
     for (int j = 0; j < N; ++j) r.g[j] = fmaf(at, b.g[j], bt * a.g[j]);
@@ -198,6 +207,7 @@ __device__ __forceinline__ DiffF<N> operator/(const DiffF<N>& a, const DiffF<N>&
     r.v = a.v / b.v;
     r.d = fmaf(a.d, b.v, -a.v * b.d) / (b.v * bt);
     const float qt = (a.v + a.d) * ibt;
+    r.lo = fmaf(-qt, b.lo, a.lo) * ibt;
 #pragma unroll
     for (int j = 0; j < N; ++j) r.g[j] = fmaf(-qt, b.g[j], a.g[j]) * ibt;
     return r;
@@ -279,8 +289,8 @@ __device__ __forceinline__ DiffF<N> square(const DiffF<N>& a) { return a * a; }
 
 // The kernels' model interface for a user definition Def, which supplies
 // N, DIM (1 or 2) and template <class T, class S> static T h(const T* p, S x, S x2).
-// Pass constants: plain pd[0..n) = p'; mixed pf[0..n) = p (FP32),
-// pf[8..8+n) = p' - p (FP64 difference, rounded).
+// Pass constants: plain pd[0..n) = p'; mixed pf[0..n) = float(p),
+// pf[8..8+n) = p' - p (FP64 difference, rounded), pf[16..16+n) = p - float(p).
 template <class Def>
 struct MUser {
     static constexpr int N = Def::N;
@@ -305,19 +315,20 @@ struct MUser {
         for (int j = 0; j < N; ++j) J[j] = r.g[j];
     }
     __device__ static void prep_mixed(const MixedParams& P, float* pf) {
-        for (int k = 0; k < N; ++k) { pf[k] = P.x[k]; pf[8 + k] = P.dx[k]; }
+        for (int k = 0; k < N; ++k) { pf[k] = P.x[k]; pf[8 + k] = P.dx[k]; pf[16 + k] = P.xlo[k]; }
     }
     __device__ static void eval_mixed(const float* pf, float X, float Y, float& hb, float& dh, float* J) {
         ad::DiffF<N> P[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             P[j].v = pf[j];
+            P[j].lo = pf[16 + j];
             P[j].d = pf[8 + j];
 #pragma unroll
             for (int k = 0; k < N; ++k) P[j].g[k] = (j == k) ? 1.0f : 0.0f;
         }
         const ad::DiffF<N> r = Def::template h<ad::DiffF<N>, float>(P, X, Y);
-        hb = r.v;
+        hb = r.v + r.lo;
         dh = r.d;
 #pragma unroll
         for (int j = 0; j < N; ++j) J[j] = r.g[j];

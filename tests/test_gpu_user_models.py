@@ -124,10 +124,13 @@ def test_user_2d_fit_bounded(ids, precision, layout):
         assert relerr(out["popt"], ref["popt"]) <= 1e-6
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_user_written_gaussian_equals_the_builtin(ids, precision):
-    """The built-in 1D Gaussian written as a user model: same fit."""
-    pr = synth.gauss1d(30_000, seed=6)
+@pytest.mark.parametrize("precision,m", [("fp64", 30_000), ("mixed", 30_000), ("mixed", 4_000_000)])
+def test_user_written_gaussian_equals_the_builtin(ids, precision, m):
+    """The built-in 1D Gaussian written as a user model: same fit.  At 4M
+    points the mixed steps near convergence fall below the FP32 resolution of
+    the parameters; the carried rounding correction keeps the iteration count
+    at the built-in's."""
+    pr = synth.gauss1d(m, seed=6)
     if precision == "mixed":
         pr = pr.astype(np.float32)
     a = gpu_fit(gbfit.MODEL_GAUSS1D, pr, precision, **TOL)
@@ -136,6 +139,8 @@ def test_user_written_gaussian_equals_the_builtin(ids, precision):
     assert relerr(b["popt"], a["popt"]) <= tol
     if precision == "fp64":
         assert a["nfev"] == b["nfev"]
+    else:
+        assert abs(a["nfev"] - b["nfev"]) <= 1
 
 
 def test_user_model_batch(ids):
