@@ -10,6 +10,11 @@ Written from the definitions, with no blocking or reordering:
   B   = J^T J                             Eq. hessian, Gauss-Newton term
 with w_i = 1 / sigma_i (Eq. easesig; w = 1 when no sigma is given).
 
+Full covariance (Appendix C, Eq. covariance): a 2D sigma is the covariance
+matrix C = L L^T (Cholesky); the weighted residual and Jacobian are the
+solutions of L r~ = r and L J~ = J (Eqs. slsq1, slsq2), by forward
+substitution (a library triangular solve).
+
 Robust losses (Section 5 names "various loss functions" without stating
 them; reading R14): the cost becomes f = 1/2 C^2 sum rho(z_i), z_i = (r_i/C)^2,
 with f_scale C and one of the standard losses below.  Its gradient is
@@ -23,21 +28,45 @@ Jacobian and residual; the ratio's actual reduction uses the robust cost.
 from __future__ import annotations
 
 import numpy as np
+from scipy.linalg import solve_triangular
 
 from . import models
 
 
+class CovFactor:
+    """Cholesky factor L of a covariance matrix C = L L^T (lower triangular)."""
+
+    def __init__(self, C):
+        C = np.asarray(C, dtype=np.float64)
+        if C.ndim != 2 or C.shape[0] != C.shape[1]:
+            raise ValueError("a covariance matrix must be square")
+        self.L = np.linalg.cholesky(C)
+
+    def solve(self, b):
+        """L^-1 b (Eqs. slsq1, slsq2) for a vector or a matrix of columns."""
+        return solve_triangular(self.L, b, lower=True)
+
+
 def weights(sigma, m):
-    """w = 1/sigma (Appendix C, diagonal L^-1); ones when sigma is None."""
+    """w = 1/sigma (Appendix C, diagonal L^-1); ones when sigma is None; a
+    CovFactor when sigma is an [m, m] covariance matrix (Eq. covariance)."""
     if sigma is None:
         return np.ones(m)
-    return 1.0 / np.asarray(sigma, dtype=np.float64)
+    s = np.asarray(sigma, dtype=np.float64)
+    if s.ndim == 2:
+        if s.shape != (m, m):
+            raise ValueError("covariance matrix must be [m, m]")
+        return CovFactor(s)
+    return 1.0 / s
 
 
 def residual_and_jac(model, X, y, w, p):
     """Weighted residual vector r [m] and Jacobian J [m, n] at p."""
     h, dh = models.value_and_jac(model, X, p)
-    r = w * (h - np.asarray(y, dtype=np.float64))
+    r0 = h - np.asarray(y, dtype=np.float64)
+    if isinstance(w, CovFactor):
+        return w.solve(r0), w.solve(dh)
+    r = w * r0
     J = w[:, None] * dh
     return r, J
 

@@ -24,7 +24,9 @@ follows.  Where the paper is silent or garbled the reading taken is one of:
   R9  Bounds by the Coleman-Li reflective method (named, not stated): see
       coleman_li and select_bounded_step.
   R10 Pseudo-inverse: lambda = s^2 <= lambda_max 8 n eps64 counts as zero.
-  R11 sigma weights rows: J_ij / sigma_i, r_i / sigma_i (Eq. easy_jac, easy_res).
+  R11 sigma weights rows: J_ij / sigma_i, r_i / sigma_i (Eq. easy_jac, easy_res);
+      a 2D sigma is the covariance matrix C = L L^T and the method runs on
+      L^-1 r, L^-1 J (Eqs. covariance, slsq1, slsq2), pcov from those.
   R12 r = h - y (Eq. residual).
   R13 pcov = V diag(1/s^2) V^T of the unscaled J at the solution (R10 cutoff),
       times 2 f / (m - n) unless absolute_sigma.
@@ -355,7 +357,8 @@ def covariance(J, cost, m, n, absolute_sigma):
 def curve_fit(model, X, y, sigma=None, p0=None, lb=None, ub=None, ftol=1e-8, xtol=1e-8,
               gtol=1e-8, max_nfev=None, x_scale=1.0, absolute_sigma=False, record=False,
               loss="linear", f_scale=1.0):
-    """Fit model `model` to (X, y) with per-point sigma by the TRF method.
+    """Fit model `model` to (X, y) with per-point sigma (or, 2D, the
+    covariance matrix of y) by the TRF method.
 
     Returns a dict: popt, pcov, cost, nfev, njev, status and (if record) the
     per-trial history used by the invariant tests.

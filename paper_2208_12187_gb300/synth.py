@@ -75,9 +75,11 @@ class Problem:
         return x.reshape(1, -1) if x.ndim == 1 else x
 
     def astype(self, dtype) -> "Problem":
-        """Same problem with data arrays cast to dtype (parameters stay float64)."""
+        """Same problem with data arrays cast to dtype (parameters, and a
+        covariance-matrix sigma, stay float64)."""
         cast = lambda a: None if a is None else np.ascontiguousarray(a, dtype=dtype)
-        return dataclasses.replace(self, x=cast(self.x), y=cast(self.y), sigma=cast(self.sigma))
+        sg = self.sigma if (self.sigma is not None and np.ndim(self.sigma) == 2) else cast(self.sigma)
+        return dataclasses.replace(self, x=cast(self.x), y=cast(self.y), sigma=sg)
 
 
 # ---------------------------------------------------------------- forward values
@@ -303,6 +305,29 @@ def user_family(family: str, m: int = 5000, seed: int = 0, dtype=np.float64, lay
     y = _user_forward(family, X, truth) + e
     lay = layout if xd == 2 else LAYOUT_VEC
     return Problem(-1, x, lay, grid, y, sig, p0, lb, ub, truth, n_user=n).astype(dtype)
+
+
+# ---------------------------------------------------------------- correlated errors
+def ar1_covariance(m: int, rho: float, scale: float, seed: int = 0) -> np.ndarray:
+    """C_ij = s_i s_j rho^|i-j|: stationary exponential correlation between
+    neighbouring points (in index order) with per-point scales s ~ scale U[0.5, 1.5]."""
+    rng = np.random.default_rng(seed)
+    s = scale * rng.uniform(0.5, 1.5, m)
+    i = np.arange(m)
+    return np.outer(s, s) * rho ** np.abs(i[:, None] - i[None, :]).astype(np.float64)
+
+
+def with_covariance(pr: Problem, rho: float = 0.5, scale: float = 0.1, seed: int = 0) -> Problem:
+    """The problem with its noise replaced by N(0, C) for C = ar1_covariance
+    and sigma = C (the [m, m] covariance matrix, FP64)."""
+    C = ar1_covariance(pr.m, rho, scale, seed)
+    rng = np.random.default_rng(seed + 1)
+    if pr.model >= 0:
+        clean = _forward(pr.model, pr.coords(), pr.truth)
+    else:
+        raise ValueError("with_covariance takes built-in model problems")
+    y = clean + np.linalg.cholesky(C) @ rng.normal(size=pr.m)
+    return dataclasses.replace(pr, y=np.asarray(y, dtype=pr.y.dtype), sigma=C)
 
 
 def log_uniform_int(rng, lo: float, hi: float, size) -> np.ndarray:
