@@ -524,6 +524,48 @@ def run_user(args):
             del x, y, lx, ly
 
 
+def run_cov(args):
+    """Full-covariance fits (Appendix C): 1D Gaussian with AR(1)-correlated
+    noise at several m; whole-call time (staging: copy of C, Cholesky, X =
+    L^-1; then the fit) and the loop kernel's share from CUDA events."""
+    import torch
+    from paper_2208_12187_gb300 import build, gbfit, synth
+    build.build()
+    gbfit.load()
+    for m in [int(v) for v in args.sizes.split(",")]:
+        pr = synth.with_covariance(synth.gauss1d(m, seed=0), 0.5, 0.1, seed=1)
+        C = torch.as_tensor(pr.sigma).cuda()
+        for prec, dt in (("mixed", torch.float32), ("fp64", torch.float64)):
+            if prec not in args.precisions.split(","):
+                continue
+            x = torch.as_tensor(pr.x).to(dt).cuda()
+            y = torch.as_tensor(pr.y).to(dt).cuda()
+            fit = lambda: gbfit.curve_fit(pr.model, x, y, pr.p0, sigma=C, precision=prec, **TOL)
+            fit()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            steps = 3
+            gbfit.set_profiling(True)
+            gbfit.stats_reset()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(steps):
+                out = fit()
+            e1.record()
+            e1.synchronize()
+            gbfit.set_profiling(False)
+            st = gbfit.stats()
+            call_ms = e0.elapsed_time(e1) / steps
+            loop_ms = st["eval_ms"] / max(st["eval_launches"], 1)
+            nf = out["nfev"]
+            fma_per_pass = m * (m + 1) / 2 * (pr.n + (2 if prec == "mixed" else 1))
+            print(json.dumps({"mode": "cov", "m": m, "precision": prec, "nfev": nf, "status": out["status"],
+                              "call_ms": call_ms, "loop_ms": loop_ms, "staging_ms": call_ms - loop_ms,
+                              "loop_ms_per_eval": loop_ms / nf,
+                              "whitening_gflops_in_loop": 2 * fma_per_pass * nf / (loop_ms / 1e3) / 1e9}))
+            del x, y
+        del C
+
+
 def run_batch(args):
     """4,096 ragged double-exponential fits in one batched launch (mixed), with
     tile shapes from the autotuner, against the plain FP64 one-fit-at-a-time
@@ -761,6 +803,7 @@ def main():
     ap.add_argument("--oracle-sample", type=int, default=64)
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--user", action="store_true", help="user-defined models (run-time compiled) vs built-in")
+    ap.add_argument("--cov", action="store_true", help="full-covariance fits (sizes from --sizes)")
     ap.add_argument("--compare", action="store_true",
                     help="headline workload: implicit grid vs explicit coordinates vs plain FP64, against the oracle")
     ap.add_argument("--serve-requests", type=int, default=20000)
@@ -783,6 +826,8 @@ def main():
         return run_serve(args)
     if args.user:
         return run_user(args)
+    if args.cov:
+        return run_cov(args)
     if args.compare:
         return run_compare(args)
     rank, local, world = dist_setup(args)

@@ -255,6 +255,35 @@ int gbfit_autotune(int model_id, int precision, int64_t m_max, int64_t points_pe
                    gbfit_tune_table* out, void* cuda_stream);
 
 /*
+ * One fit with a full covariance matrix of the observations (Appendix C,
+ * Eq. covariance; SciPy's 2D sigma).  C = L L^T is factored once on the
+ * device (FP64 Cholesky, then X = L^-1 by forward substitution) and the
+ * method runs on L^-1 r and L^-1 J (Eqs. slsq1, slsq2): every evaluation is
+ * two rounds of the loop kernel, the points into a buffer, then rows of
+ * X [h - y, J] reduced like points (the row-parallel product takes the place
+ * of the paper's per-iteration triangular solves).
+ *   cov   [m][m] FP64, host or device, symmetric positive definite (only the
+ *         lower triangle is read); m <= GBFIT_COV_MAX_M
+ *   other arguments as gbfit_curve_fit (no sigma; linear loss only).
+ * Device memory: about 3 m^2 * 8 bytes (C / L, X in FP64, X in FP32 for the
+ * mixed path), kept between calls.  Staging costs O(m^3) FP64 work (tens of
+ * ms at m = 4096) and one synchronisation.
+ * Errors: as gbfit_curve_fit, plus GBFIT_E_INVALID_ARG when C is not
+ * positive definite, GBFIT_E_UNSUPPORTED for a robust loss.
+ */
+#define GBFIT_COV_MAX_M 8192
+int gbfit_curve_fit_cov(int model_id, const void* xdata, int64_t m, int x_layout, const int64_t* grid_wh,
+                        const void* ydata, const double* cov, int dtype, const double* p0, const double* lb,
+                        const double* ub, const gbfit_options* opt, double* popt, double* pcov, double* cost,
+                        int* nfev, int* fit_status, void* cuda_stream);
+
+/* gbfit_evaluate with a full covariance matrix: B, g and cost of the
+ * whitened problem at p (out as gbfit_evaluate). */
+int gbfit_evaluate_cov(int model_id, const void* xdata, int64_t m, int x_layout, const int64_t* grid_wh,
+                       const void* ydata, const double* cov, int dtype, const double* p, int precision,
+                       double* out, void* cuda_stream);
+
+/*
  * Evaluate the fused reduction once at parameters p (no iteration): the
  * packed upper triangle of B = J^T J (n(n+1)/2), g = J^T r (n) and cost
  * f = r^T r / 2, all FP64, for the given precision mode (paper Eqs. msqe,

@@ -107,6 +107,14 @@ struct Ctx {
     double* wbuf = nullptr; size_t cap_w = 0;
     char* databuf = nullptr; size_t cap_data = 0;
     double* small = nullptr;      // subproblem scratch
+    // full covariance: C -> L in place, 1 / L_kk, X = L^-1 (FP64 and FP32),
+    // the per-point columns of the evaluation round, barrier words + flag
+    double* cov_a = nullptr; size_t cap_cov_a = 0;
+    double* cov_rd = nullptr; size_t cap_cov_rd = 0;
+    double* cov_x = nullptr; size_t cap_cov_x = 0;
+    float* cov_xf = nullptr; size_t cap_cov_xf = 0;
+    double* cov_h = nullptr; size_t cap_cov_h = 0;
+    int* cov_sync = nullptr; size_t cap_cov_sync = 0;
     // pinned host staging
     char* hbuf = nullptr; size_t hcap = 0;
     // one-node graphs holding the cooperative loop launch, per precision (a
@@ -333,12 +341,14 @@ int run_fits(Ctx* c, const KernelSet* ks, int prec, std::vector<FitDesc>& hd, co
     size_t nf = hd.size();
     size_t ntiles = 0, ngroups = 0;
     int max_nfev = 1;
+    bool any_cov = false;
     for (auto& d : hd) {
         d.tile_base = (int64_t)ntiles;
         d.group_base = (int64_t)ngroups;
         ntiles += d.n_tiles;
         ngroups += d.n_groups;
         if (d.max_nfev > max_nfev) max_nfev = d.max_nfev;
+        any_cov = any_cov || d.cov;
     }
     JobLayout L(nf, ntiles, ngroups);
     int rc;
@@ -350,7 +360,7 @@ int run_fits(Ctx* c, const KernelSet* ks, int prec, std::vector<FitDesc>& hd, co
     E.sc[0] = (int)ntiles;
     E.sc[1] = (int)nf;
     E.sc[2] = 0;
-    E.sc[3] = max_nfev + 4;             // rounds = evaluations of a fit, plus slack
+    E.sc[3] = any_cov ? 2 * max_nfev + 6 : max_nfev + 4;   // rounds per evaluation (2 for covariance fits), plus slack
     E.sc[4] = (int)nf;
     memcpy(hb + L.eng, &E, sizeof E);
     memcpy(hb + L.desc, hd.data(), nf * sizeof(FitDesc));
@@ -362,7 +372,8 @@ int run_fits(Ctx* c, const KernelSet* ks, int prec, std::vector<FitDesc>& hd, co
         st.run = RS_RUNNING;
         st.phase = PH_INIT;
         for (int i = 0; i < hd[f].n; ++i) { st.x[i] = p0s[f][i]; st.xt[i] = p0s[f][i]; st.scale_inv[i] = 1.0; }
-        for (int t = 0; t < hd[f].n_tiles; ++t) hi[k++] = WorkItem{(int)f, t};
+        // covariance row items cost in proportion to their index: largest first
+        for (int t = 0; t < hd[f].n_tiles; ++t) hi[k++] = WorkItem{(int)f, hd[f].cov ? hd[f].n_tiles - 1 - t : t};
     }
     CUDA_TRY(cudaMemcpyAsync(c->job, hb, L.res_hdr, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemsetAsync(c->job + L.res_hdr, 0, 32, s));   // out[]: running, rounds, abort; busy / wait ns
@@ -488,6 +499,46 @@ int set_data(Ctx* c, FitDesc& d, const void* x, const void* x2, const void* y, c
     return GBFIT_OK;
 }
 
+// Full covariance (Appendix C): copy C to the device, factor C = L L^T and
+// form X = L^-1 there (cov_kernels.cu), and turn the descriptor into a
+// covariance fit: 32-point items, rounds alternating between evaluating
+// points and reducing rows of X [h - y, J].  One D2H read of the factor's
+// status word (a synchronisation) before the fit.
+int stage_cov(Ctx* c, FitDesc& d, const double* cov, int64_t m, int n, cudaStream_t s) {
+    bool ch = false;
+    int rc;
+    const size_t mm = (size_t)m * (size_t)m;
+    if ((rc = grow_dev(c->cov_a, c->cap_cov_a, mm, ch))) return rc;
+    if ((rc = grow_dev(c->cov_x, c->cap_cov_x, mm, ch))) return rc;
+    if ((rc = grow_dev(c->cov_rd, c->cap_cov_rd, (size_t)m, ch))) return rc;
+    if (d.prec == PREC_MIXED && (rc = grow_dev(c->cov_xf, c->cap_cov_xf, mm, ch))) return rc;
+    if ((rc = grow_dev(c->cov_h, c->cap_cov_h, (size_t)(n + 2) * (size_t)m, ch))) return rc;
+    if ((rc = grow_dev(c->cov_sync, c->cap_cov_sync, (size_t)4, ch))) return rc;
+    const bool dev = is_device_ptr(cov);
+    CUDA_TRY(cudaMemcpyAsync(c->cov_a, cov, mm * sizeof(double), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(c->cov_sync, 0, 4 * sizeof(int), s));
+    CUDA_TRY(launch_cov_factor(c->cov_a, c->cov_rd, c->cov_x, d.prec == PREC_MIXED ? c->cov_xf : nullptr, (int)m,
+                               (unsigned*)c->cov_sync, c->cov_sync + 2, c->sms, s));
+    int flag = 0;
+    CUDA_TRY(cudaMemcpyAsync(&flag, c->cov_sync + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    {
+        std::lock_guard<std::mutex> g(g_stats_mu);
+        g_stats.kernel_launches += d.prec == PREC_MIXED ? 3 : 2;
+    }
+    if (flag & 1) return fail(GBFIT_E_INVALID_ARG, "the covariance matrix is not positive definite");
+    if (flag & 2) return fail(GBFIT_E_TIMEOUT, "a grid barrier of the covariance factorisation timed out");
+    d.cov = 1;
+    d.xinv = d.prec == PREC_MIXED ? (const void*)c->cov_xf : (const void*)c->cov_x;
+    d.hbuf = c->cov_h;
+    d.wkind = W_NONE;
+    d.w = nullptr;
+    d.tile_points = COV_ROWS;
+    d.n_tiles = (int)((m + COV_ROWS - 1) / COV_ROWS);
+    d.n_groups = (d.n_tiles + d.group_tiles - 1) / d.group_tiles;
+    return GBFIT_OK;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -526,7 +577,7 @@ static int check_common(int model_id, int x_layout, int dtype, const void* ydata
 static int single_fit(int model_id, const void* xdata, int64_t m, int x_layout, const int64_t* grid_wh,
                       const void* ydata, const void* sigma, int dtype, const double* p0, const double* lb,
                       const double* ub, const gbfit_options* opt_in, FitResult* out, void* cuda_stream,
-                      bool eval_only) {
+                      bool eval_only, const double* cov = nullptr) {
     int n, rc;
     if ((rc = check_common(model_id, x_layout, dtype, ydata, &n))) return rc;
     gbfit_options o = opt_in ? *opt_in : defaults();
@@ -546,6 +597,11 @@ static int single_fit(int model_id, const void* xdata, int64_t m, int x_layout, 
     bool bounded;
     if ((rc = check_params(a, &bounded))) return rc;
     if (eval_only) { bounded = false; o.max_nfev = 1; }
+    if (cov) {
+        if (m > GBFIT_COV_MAX_M) return fail(GBFIT_E_INVALID_ARG, "covariance fits take m <= %d", GBFIT_COV_MAX_M);
+        if (o.loss != GBFIT_LOSS_LINEAR) return fail(GBFIT_E_UNSUPPORTED, "covariance fits take the linear loss");
+        if (sigma) return fail(GBFIT_E_INVALID_ARG, "give sigma or a covariance matrix, not both");
+    }
     const KernelSet* ks;
     if ((rc = kernels_for_model(model_id, &ks))) return rc;
     Ctx* c;
@@ -567,6 +623,7 @@ static int single_fit(int model_id, const void* xdata, int64_t m, int x_layout, 
         { std::lock_guard<std::mutex> g(g_stats_mu); g_stats.kernel_launches += 1; }
     }
     set_data(c, hd[0], sd.x, x2, sd.y, sd.sigma, 0, s);
+    if (cov && (rc = stage_cov(c, hd[0], cov, m, n, s))) return rc;
     std::vector<std::vector<double>> p0s(1, std::vector<double>(p0, p0 + n));
     std::vector<FitResult> hr;
     int rounds = 0;
@@ -605,6 +662,43 @@ int gbfit_evaluate(int model_id, const void* xdata, int64_t m, int x_layout, con
     FitResult r;
     int rc = single_fit(model_id, xdata, m, x_layout, grid_wh, ydata, sigma, dtype, p, nullptr, nullptr, &o, &r,
                         cuda_stream, true);
+    if (rc) return rc;
+    int n = 0, xd = 0;
+    model_shape(model_id, &n, &xd);
+    int K = n_tri(n) + n + 1;
+    for (int k = 0; k < K; ++k) out[k] = r.tot[k];
+    out[K - 1] = 0.5 * r.tot[K - 1];
+    return GBFIT_OK;
+}
+
+int gbfit_curve_fit_cov(int model_id, const void* xdata, int64_t m, int x_layout, const int64_t* grid_wh,
+                        const void* ydata, const double* cov, int dtype, const double* p0, const double* lb,
+                        const double* ub, const gbfit_options* opt, double* popt, double* pcov, double* cost,
+                        int* nfev, int* fit_status, void* cuda_stream) {
+    if (!cov) return fail(GBFIT_E_INVALID_ARG, "cov is NULL");
+    FitResult r;
+    int rc = single_fit(model_id, xdata, m, x_layout, grid_wh, ydata, nullptr, dtype, p0, lb, ub, opt, &r,
+                        cuda_stream, false, cov);
+    if (rc) return rc;
+    int n = 0, xd = 0;
+    model_shape(model_id, &n, &xd);
+    if (popt) for (int i = 0; i < n; ++i) popt[i] = r.popt[i];
+    if (pcov) for (int i = 0; i < n * n; ++i) pcov[i] = r.pcov[i];
+    if (cost) *cost = r.cost;
+    if (nfev) *nfev = r.nfev;
+    if (fit_status) *fit_status = r.fit_status;
+    return GBFIT_OK;
+}
+
+int gbfit_evaluate_cov(int model_id, const void* xdata, int64_t m, int x_layout, const int64_t* grid_wh,
+                       const void* ydata, const double* cov, int dtype, const double* p, int precision,
+                       double* out, void* cuda_stream) {
+    if (!cov) return fail(GBFIT_E_INVALID_ARG, "cov is NULL");
+    gbfit_options o = defaults();
+    o.precision = precision;
+    FitResult r;
+    int rc = single_fit(model_id, xdata, m, x_layout, grid_wh, ydata, nullptr, dtype, p, nullptr, nullptr, &o, &r,
+                        cuda_stream, true, cov);
     if (rc) return rc;
     int n = 0, xd = 0;
     model_shape(model_id, &n, &xd);

@@ -48,7 +48,14 @@ struct FitDesc {
     int absolute_sigma, group_tiles;
     int loss, pad2;
     double f_scale;        // robust loss scale C (1 for the linear loss)
+    // full covariance (Appendix C): rounds alternate between evaluating the
+    // points into hbuf and reducing rows of X hbuf, X = L^-1 (C = L L^T)
+    int cov, pad3;
+    const void* xinv;      // X, [m][m] column-major (X_ij at xinv[j m + i]), lower triangle, zeros above;
+                           // FP32 for the mixed path, FP64 for the plain path
+    void* hbuf;            // [columns][m]: mixed h - y, dh, J_0..J_n-1 (FP32); plain h' - y, J (FP64)
 };
+constexpr int COV_ROWS = 32;                     // points / rows per work item of a covariance fit
 
 // Mutable per-fit state, kept on the device across iterations.
 struct alignas(16) FitState {
@@ -56,7 +63,7 @@ struct alignas(16) FitState {
     int run;               // RunState
     int phase;             // Phase of the pending evaluation
     int bad_data;          // set by the INIT pass when sigma <= 0 or non-finite data
-    int pad0;
+    int cov_stage;         // covariance fits: 0 = the next round evaluates points, 1 = it reduces rows
     float pf[PF];          // mixed-precision pass constants (base x -> trial xt)
     double pd[PD];         // plain pass constants (trial xt)
     // --- TRF state ---

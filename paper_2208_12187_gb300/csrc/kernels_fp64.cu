@@ -13,7 +13,7 @@ void* kernel_init_slots_fp64() { return (void*)init_slots_kernel<PREC_FP64, Buil
 // Resident CTAs per SM of the round kernels (the loop kernel's cooperative
 // grid is this times the SM count, so both kernels must fit it).
 int eval_blocks_per_sm_fp64() {
-    const int dyn = (int)(0);
+    const int dyn = (int)(COV_SMEM_BYTES);          // scratch of the covariance row rounds
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(eval_round_kernel<PREC_FP64, BuiltinModels>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
@@ -25,6 +25,6 @@ int eval_blocks_per_sm_fp64() {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fit_loop_kernel<PREC_FP64, BuiltinModels>, EVAL_THREADS, dyn);
     return b < b2 ? b : b2;
 }
-size_t eval_dyn_smem_fp64() { return 0; }
+size_t eval_dyn_smem_fp64() { return COV_SMEM_BYTES; }
 
 }  // namespace gbfit

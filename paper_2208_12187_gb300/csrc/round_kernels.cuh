@@ -16,6 +16,7 @@
 //       or the round cap is reached.
 //   init_fits_kernel / init_slots_kernel  pass constants at p0.
 #include "gbfit_internal.cuh"
+#include "sync_device.cuh"
 #include "models.cuh"
 #include "trf_device.cuh"
 #include "trf_step.cuh"
@@ -472,6 +473,7 @@ struct RoundSmem {
     float pf[PF];
     double pd[PD];
     int flag[4];
+    int cov_stage;                     // covariance fits: the item's round (FitState::cov_stage)
     int ctl;
     int desc_fit;                      // fit whose descriptor is in desc (-1: none yet)
     union {
@@ -571,6 +573,132 @@ __device__ void eval_tile_dispatch(const RoundSmem& sm, int64_t i0, int64_t i1, 
 #undef GB_CASE
 }
 
+// ---- full covariance (Appendix C, Eqs. covariance, slsq1, slsq2).  With
+// C = L L^T the method runs on L^-1 r and L^-1 J.  A covariance fit
+// alternates two rounds per evaluation: the points of each item into hbuf,
+// then rows of Z = X hbuf (X = L^-1, precomputed), each row reduced like a
+// point.  The row-parallel product replaces the paper's per-iteration
+// triangular solves, whose rows depend on one another.
+constexpr int COV_SMEM_BYTES = 20480;            // shared scratch of the row reduction
+
+template <class M, int PREC, typename DT, int LAYOUT>
+__device__ void cov_eval_points(const FitDesc& d, const float* pfl, const double* pdl, int64_t i0, int64_t i1,
+                                bool check, int& bad) {
+    const int64_t m = d.m;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += EVAL_THREADS) {
+        double X, Y = 0.0;
+        if (LAYOUT == X_GRID) {
+            X = double(i % d.grid_w);
+            Y = double(i / d.grid_w);
+        } else {
+            X = double(ldg_t<DT>(d.x, i));
+            if (LAYOUT == X_SOA2) Y = double(ldg_t<DT>(d.x2, i));
+        }
+        const double yv = double(ldg_t<DT>(d.y, i));
+        if (check && !(isfinite(X) && isfinite(Y) && isfinite(yv))) bad = 1;
+        if constexpr (PREC == PREC_MIXED) {
+            float hb, dh, J[M::N];
+            M::eval_mixed(pfl, float(X), float(Y), hb, dh, J);
+            float* H = (float*)d.hbuf;
+            H[i] = hb - float(yv);
+            H[m + i] = dh;
+#pragma unroll
+            for (int a = 0; a < M::N; ++a) H[(2 + a) * m + i] = J[a];
+        } else {
+            double h, J[M::N];
+            M::eval_plain(pdl, X, Y, h, J);
+            double* H = (double*)d.hbuf;
+            H[i] = h - yv;
+#pragma unroll
+            for (int a = 0; a < M::N; ++a) H[(1 + a) * m + i] = J[a];
+        }
+    }
+}
+
+template <class M, int PREC>
+__device__ void cov_eval_dispatch(const FitDesc& d, const float* pfl, const double* pdl, int64_t i0, int64_t i1,
+                                  bool check, int& bad) {
+    const bool f64 = d.dtype == F64;
+    if (M::DIM == 2) {
+        if (d.layout == X_GRID) {
+            if (f64) cov_eval_points<M, PREC, double, X_GRID>(d, pfl, pdl, i0, i1, check, bad);
+            else cov_eval_points<M, PREC, float, X_GRID>(d, pfl, pdl, i0, i1, check, bad);
+        } else {
+            if (f64) cov_eval_points<M, PREC, double, X_SOA2>(d, pfl, pdl, i0, i1, check, bad);
+            else cov_eval_points<M, PREC, float, X_SOA2>(d, pfl, pdl, i0, i1, check, bad);
+        }
+    } else {
+        if (f64) cov_eval_points<M, PREC, double, X_VEC>(d, pfl, pdl, i0, i1, check, bad);
+        else cov_eval_points<M, PREC, float, X_VEC>(d, pfl, pdl, i0, i1, check, bad);
+    }
+}
+
+// Rows [32 tile, 32 tile + 32) of Z = X H into the accumulators: lane =
+// row, the warps split the column index j (chunks of H staged in shared
+// memory, X read coalesced down its columns), partial rows summed over the
+// warps in a fixed order, then warp 0 adds each row as one point.
+template <int N, int PREC>
+__device__ void cov_rows(const FitDesc& d, int tile, void* scratch, typename AccT<PREC>::T (&acc)[n_acc(N, PREC)]) {
+    using HT = typename AccT<PREC>::T;
+    constexpr int NC = (PREC == PREC_MIXED) ? N + 2 : N + 1;
+    constexpr int CJ = COV_SMEM_BYTES / (NC * (int)sizeof(HT)) / 32 * 32;
+    constexpr int NW = EVAL_THREADS / 32;
+    static_assert(NW * NC * 32 * sizeof(HT) <= COV_SMEM_BYTES, "row partials must fit the scratch");
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t m = d.m;
+    const int64_t i = (int64_t)tile * COV_ROWS + lane;
+    const bool row_ok = i < m;
+    const int64_t jend = min(m, (int64_t)(tile + 1) * COV_ROWS);
+    const HT* Xc = (const HT*)d.xinv;
+    const HT* Hg = (const HT*)d.hbuf;
+    HT* Hs = (HT*)scratch;                          // [NC][CJ]
+    HT z[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) z[c] = HT(0);
+    for (int64_t j0 = 0; j0 < jend; j0 += CJ) {
+        const int cj = (int)min((int64_t)CJ, jend - j0);
+        __syncthreads();                            // the previous chunk is consumed
+        for (int k = t; k < NC * cj; k += EVAL_THREADS) {
+            const int c = k / cj, jj = k - c * cj;
+            Hs[c * CJ + jj] = __ldcg(Hg + (int64_t)c * m + j0 + jj);   // written by other CTAs last round
+        }
+        __syncthreads();
+        for (int jj = warp; jj < cj; jj += NW) {
+            const HT x = row_ok ? Xc[(j0 + jj) * m + i] : HT(0);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) z[c] = fma(x, Hs[c * CJ + jj], z[c]);
+        }
+    }
+    __syncthreads();
+    HT* red = (HT*)scratch;                         // [NW][NC][32]
+#pragma unroll
+    for (int c = 0; c < NC; ++c) red[(warp * NC + c) * 32 + lane] = z[c];
+    __syncthreads();
+    if (warp == 0 && row_ok) {
+        HT s[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            HT v = HT(0);
+            for (int w = 0; w < NW; ++w) v += red[(w * NC + c) * 32 + lane];
+            s[c] = v;
+        }
+        constexpr int NT = n_tri(N);
+        constexpr int J0 = (PREC == PREC_MIXED) ? 2 : 1;
+        const HT r = s[0];
+        const HT rn = (PREC == PREC_MIXED) ? r + s[1] : r;
+        int idx = 0;
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int b = a; b < N; ++b) { acc[idx] = fma(s[J0 + a], s[J0 + b], acc[idx]); ++idx; }
+#pragma unroll
+        for (int a = 0; a < N; ++a) acc[NT + a] = fma(s[J0 + a], rn, acc[NT + a]);
+        acc[NT + N] = fma(rn, rn, acc[NT + N]);
+        if constexpr (PREC == PREC_MIXED) acc[NT + N + 1] += s[1] * (HT(2) * r + s[1]);
+    }
+    __syncthreads();                                // the scratch is free again
+}
+
 template <class M, int PREC, class MS>
 __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, RingState& R, long long t_item) {
     using AT = typename AccT<PREC>::T;
@@ -586,7 +714,33 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
     R.wait_cycles = 0;
     int bad = 0;
     AT acc[K];
-    eval_tile_dispatch<M, PREC>(sm, i0, i1, check, bad, acc, R);
+    if (d.cov) {
+        if (sm.cov_stage == 0) {
+            // evaluation round: the item's points into hbuf; the last item of
+            // the fit to finish opens the row round (the grid barrier
+            // publishes hbuf and the stage)
+            cov_eval_dispatch<M, PREC>(d, sm.pf, sm.pd, i0, i1, check, bad);
+            if (check) {
+                int any = __syncthreads_or(bad);
+                if (any && threadIdx.x == 0) atomicOr(&stp->bad_data, 1);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int old = arrive_acq_rel(&E.fit_cnt[fit]);
+                if (old == d.n_tiles - 1) {
+                    E.fit_cnt[fit] = 0;
+                    stp->cov_stage = 1;
+                }
+            }
+            return;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] = AT(0);
+        cov_rows<N, PREC>(d, tile, R.buf, acc);
+        check = false;
+    } else {
+        eval_tile_dispatch<M, PREC>(sm, i0, i1, check, bad, acc, R);
+    }
     if (threadIdx.x == 0) sm.t_loop = clock64();
     if (sm.ring_fail && threadIdx.x == 0) atomicOr(&stp->bad_data, 2);   // a bounded wait gave up
     if (check) {
@@ -697,7 +851,11 @@ __device__ __forceinline__ void run_items(RoundSmem& sm, const Engine& E, RingSt
         // one round trip for the item's state words, pass constants and (when
         // this CTA's previous item was another fit) descriptor; state from
         // L2, since other CTAs rewrite it between rounds
-        if (threadIdx.x == 0) { sm.flag[0] = __ldcg(&stp->run); sm.flag[1] = __ldcg(&stp->phase); }
+        if (threadIdx.x == 0) {
+            sm.flag[0] = __ldcg(&stp->run);
+            sm.flag[1] = __ldcg(&stp->phase);
+            sm.cov_stage = __ldcg(&stp->cov_stage);
+        }
         if (PREC == PREC_MIXED) { if (threadIdx.x < PF) sm.pf[threadIdx.x] = __ldcg(stp->pf + threadIdx.x); }
         else { if (threadIdx.x < PD) sm.pd[threadIdx.x] = __ldcg(stp->pd + threadIdx.x); }
         if (wi.fit != sm.desc_fit) {
@@ -748,20 +906,6 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) eval_round_kernel(const Engin
 // the bound the CTA raises the abort bit and every CTA leaves the loop.
 constexpr unsigned long long ROUND_WAIT_LIMIT_NS = 10ull * 1000 * 1000 * 1000;
 enum { CTL_STOP = 1, CTL_ABORT = 2 };
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 // All CTAs arrive; the last one closes the round (rounds, running, stop
 // decision; count_round false for the set-up barrier) and opens the next.

@@ -773,6 +773,7 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             st->njev = S.si[SI_NJEV]; st->predicted = -qval;
             st->step_norm = w_norm; st->s_norm = s_norm; st->xtol_thr = d.xtol * (d.xtol + x_norm);
             st->phase = PH_TRIAL; st->last_kind = kind; st->alg2_iters = a2it;
+            st->cov_stage = 0;
             trace_bump(st->trace, TR_N_ALG2IT, a2it);
             trace_bump(st->trace, TR_N_BOUNDED, kind != 0);
         }

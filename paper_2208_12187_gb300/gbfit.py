@@ -34,7 +34,7 @@ EXPORTS = ["gbfit_version", "gbfit_last_error", "gbfit_default_options", "gbfit_
            "gbfit_stats_reset", "gbfit_stats_get", "gbfit_set_profiling", "gbfit_evaluate_noalloc",
            "gbfit_server_create", "gbfit_server_submit", "gbfit_server_step", "gbfit_server_poll",
            "gbfit_server_destroy", "gbfit_tune_get", "gbfit_tune_set", "gbfit_tune_shape", "gbfit_autotune",
-           "gbfit_model_register", "gbfit_model_log"]
+           "gbfit_model_register", "gbfit_model_log", "gbfit_curve_fit_cov", "gbfit_evaluate_cov"]
 
 
 class GbfitError(RuntimeError):
@@ -133,6 +133,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.gbfit_autotune.argtypes = [I, I, I64, I64, ctypes.POINTER(TuneTable), P]
     lib.gbfit_set_profiling.argtypes = [I]
     lib.gbfit_model_register.argtypes = [ctypes.c_char_p, ctypes.c_char_p, I, I, IP]
+    lib.gbfit_curve_fit_cov.argtypes = [I, P, I64, I, P, P, P, I, P, P, P, P, P, P, P, P, P, P]
+    lib.gbfit_evaluate_cov.argtypes = [I, P, I64, I, P, P, P, I, P, I, P, P]
     lib.gbfit_model_log.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     for name in EXPORTS:
         getattr(lib, name)
@@ -185,6 +187,22 @@ def _array_info(a):
     if code is None:
         raise TypeError("data arrays must be float32 or float64")
     return a.ctypes.data, code, a
+
+
+def _cov_info(sigma, m):
+    """(address, keepalive) of a 2D sigma (an [m, m] covariance matrix, FP64), else None."""
+    shape = getattr(sigma, "shape", None)
+    if sigma is None or shape is None or len(shape) != 2:
+        return None
+    if tuple(shape) != (m, m):
+        raise ValueError("a 2D sigma must be the [m, m] covariance matrix")
+    tt, _ = _TORCH or _torch_types()
+    if tt is not None and isinstance(sigma, tt):
+        import torch
+        c = sigma.to(torch.float64).contiguous()
+        return c.data_ptr(), c
+    c = np.ascontiguousarray(np.asarray(sigma, dtype=np.float64))
+    return c.ctypes.data, c
 
 
 def _stream_ptr(stream):
@@ -280,8 +298,9 @@ def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None
     n = N_PARAMS[model]
     yp, dt, ykeep = _array_info(ydata)
     xp, xdt, xkeep = _array_info(xdata)
-    sp, sdt, skeep = _array_info(sigma)
     m = int(ykeep.shape[0])
+    cov = _cov_info(sigma, m)                      # 2D sigma: full covariance (gbfit_curve_fit_cov)
+    sp, sdt, skeep = _array_info(None if cov else sigma)
     if xp is not None and xdt != dt or sp is not None and sdt != dt:
         raise TypeError("xdata, ydata and sigma must share one dtype")
     gw = None
@@ -299,7 +318,10 @@ def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None
     out = np.zeros(n + n * n + 1)                  # popt | pcov | cost
     ints = np.zeros(2, dtype=np.int32)             # nfev | status
     a = out.ctypes.data
-    rc = lib.gbfit_curve_fit(model, xp, m, layout, None if gw is None else gw.ctypes.data, yp, sp, dt,
+    call = lib.gbfit_curve_fit
+    if cov:
+        call, sp = lib.gbfit_curve_fit_cov, cov[0]
+    rc = call(model, xp, m, layout, None if gw is None else gw.ctypes.data, yp, sp, dt,
                              p0a.ctypes.data, None if lbv is None else lbv.ctypes.data,
                              None if ubv is None else ubv.ctypes.data, ctypes.addressof(opt), a, a + 8 * n,
                              a + 8 * (n + n * n), ints.ctypes.data, ints.ctypes.data + 4, _stream_ptr(stream))
@@ -350,8 +372,9 @@ def evaluate(model: int, xdata, ydata, p, sigma=None, grid_wh=None, precision="f
     n = N_PARAMS[model]
     yp, dt, ykeep = _array_info(ydata)
     xp, _, xkeep = _array_info(xdata)
-    sp, _, skeep = _array_info(sigma)
     m = int(ykeep.shape[0])
+    cov = _cov_info(sigma, m)
+    sp, _, skeep = _array_info(None if cov else sigma)
     if grid_wh is not None:
         layout, gw, xp = X_GRID, (ctypes.c_int64 * 2)(int(grid_wh[0]), int(grid_wh[1])), None
     else:
@@ -360,8 +383,12 @@ def evaluate(model: int, xdata, ydata, p, sigma=None, grid_wh=None, precision="f
     nt = n * (n + 1) // 2
     out = np.zeros(nt + n + 1)
     prec = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision] if isinstance(precision, str) else int(precision)
-    rc = lib.gbfit_evaluate(model, xp, m, layout, gw, yp, sp, dt, _dptr(pa), prec, int(tile_points),
-                            _dptr(out), _stream_ptr(stream))
+    if cov:
+        rc = lib.gbfit_evaluate_cov(model, xp, m, layout, None if gw is None else ctypes.addressof(gw), yp, cov[0],
+                                    dt, pa.ctypes.data, prec, out.ctypes.data, _stream_ptr(stream))
+    else:
+        rc = lib.gbfit_evaluate(model, xp, m, layout, gw, yp, sp, dt, _dptr(pa), prec, int(tile_points),
+                                _dptr(out), _stream_ptr(stream))
     _check(rc)
     return out[:nt], out[nt:nt + n], float(out[nt + n])
 

@@ -100,3 +100,24 @@ def test_tune_table_host_api():
         gbfit.tune_set(saved)
     with pytest.raises(gbfit.GbfitError):
         gbfit.tune_shape(9, "mixed", 100)
+
+
+def test_covariance_size_limit_checked_on_the_host():
+    """m above GBFIT_COV_MAX_M is refused before any device work."""
+    import ctypes
+    import numpy as np
+    from paper_2208_12187_gb300 import build, gbfit
+    build.build()
+    lib = gbfit.load()
+    m = 8193
+    x = np.zeros(m)
+    y = np.zeros(m)
+    C = np.zeros(1)            # never read: the size check comes first
+    p0 = np.array([1.0, 0.0, 1.0, 0.0])
+    out = np.zeros(4 + 16 + 1)
+    ints = np.zeros(2, dtype=np.int32)
+    a = out.ctypes.data
+    rc = lib.gbfit_curve_fit_cov(0, x.ctypes.data, m, 0, None, y.ctypes.data, C.ctypes.data, 1, p0.ctypes.data,
+                                 None, None, None, a, a + 32, a + 160, ints.ctypes.data, ints.ctypes.data + 4, None)
+    assert rc == gbfit.E_INVALID_ARG
+    assert b"m <=" in lib.gbfit_last_error()
