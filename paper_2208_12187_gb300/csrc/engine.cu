@@ -507,29 +507,35 @@ int set_data(Ctx* c, FitDesc& d, const void* x, const void* x2, const void* y, c
 int stage_cov(Ctx* c, FitDesc& d, const double* cov, int64_t m, int n, cudaStream_t s) {
     bool ch = false;
     int rc;
+    const size_t mp = cov_padded((int)m);
     const size_t mm = (size_t)m * (size_t)m;
-    if ((rc = grow_dev(c->cov_a, c->cap_cov_a, mm, ch))) return rc;
-    if ((rc = grow_dev(c->cov_x, c->cap_cov_x, mm, ch))) return rc;
-    if ((rc = grow_dev(c->cov_rd, c->cap_cov_rd, (size_t)m, ch))) return rc;
+    if ((rc = grow_dev(c->cov_a, c->cap_cov_a, mp * mp, ch))) return rc;
+    if ((rc = grow_dev(c->cov_x, c->cap_cov_x, mp * mp, ch))) return rc;
+    if ((rc = grow_dev(c->cov_rd, c->cap_cov_rd, mp * 32, ch))) return rc;
     if (d.prec == PREC_MIXED && (rc = grow_dev(c->cov_xf, c->cap_cov_xf, mm, ch))) return rc;
     if ((rc = grow_dev(c->cov_h, c->cap_cov_h, (size_t)(n + 2) * (size_t)m, ch))) return rc;
     if ((rc = grow_dev(c->cov_sync, c->cap_cov_sync, (size_t)4, ch))) return rc;
     const bool dev = is_device_ptr(cov);
-    CUDA_TRY(cudaMemcpyAsync(c->cov_a, cov, mm * sizeof(double), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(c->cov_a, 0, mp * mp * sizeof(double), s));
+    CUDA_TRY(cudaMemcpy2DAsync(c->cov_a, mp * sizeof(double), cov, (size_t)m * sizeof(double),
+                               (size_t)m * sizeof(double), (size_t)m,
+                               dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(c->cov_x, 0, mp * mp * sizeof(double), s));
     CUDA_TRY(cudaMemsetAsync(c->cov_sync, 0, 4 * sizeof(int), s));
-    CUDA_TRY(launch_cov_factor(c->cov_a, c->cov_rd, c->cov_x, d.prec == PREC_MIXED ? c->cov_xf : nullptr, (int)m,
-                               (unsigned*)c->cov_sync, c->cov_sync + 2, c->sms, s));
+    // the compact FP64 inverse reuses the factor's storage (read before it is overwritten)
+    CUDA_TRY(launch_cov_factor(c->cov_a, c->cov_rd, c->cov_x, c->cov_a, d.prec == PREC_MIXED ? c->cov_xf : nullptr,
+                               (int)m, (unsigned*)c->cov_sync, c->cov_sync + 2, c->sms, s));
     int flag = 0;
     CUDA_TRY(cudaMemcpyAsync(&flag, c->cov_sync + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     {
         std::lock_guard<std::mutex> g(g_stats_mu);
-        g_stats.kernel_launches += d.prec == PREC_MIXED ? 3 : 2;
+        g_stats.kernel_launches += 3;
     }
     if (flag & 1) return fail(GBFIT_E_INVALID_ARG, "the covariance matrix is not positive definite");
     if (flag & 2) return fail(GBFIT_E_TIMEOUT, "a grid barrier of the covariance factorisation timed out");
     d.cov = 1;
-    d.xinv = d.prec == PREC_MIXED ? (const void*)c->cov_xf : (const void*)c->cov_x;
+    d.xinv = d.prec == PREC_MIXED ? (const void*)c->cov_xf : (const void*)c->cov_a;
     d.hbuf = c->cov_h;
     d.wkind = W_NONE;
     d.w = nullptr;

@@ -27,11 +27,15 @@ size_t eval_dyn_smem(int prec);
 cudaError_t launch_stage_weights(bool f64, const void* sigma, double* w, int64_t m, int blocks, cudaStream_t s);
 cudaError_t launch_synth_fill(int model, bool f64, void* x, void* x2, void* y, int64_t total, int64_t period,
                               uint32_t seed, int blocks, const double* truth, cudaStream_t s);
-// Full covariance: A (C, [m][m] FP64 column-major) becomes L in place,
-// X = L^-1 (FP64) and, when Xf is not null, its FP32 copy.  flag: bit 1 not
-// positive definite, bit 2 a grid barrier gave up.  sync: two zeroed words.
-cudaError_t launch_cov_factor(double* A, double* rdiag, double* X, float* Xf, int m, unsigned* sync, int* flag,
-                              int sms, cudaStream_t s);
+// Full covariance: A ([mp][mp] FP64 column-major, mp = cov_padded(m), C in
+// the top-left m x m, zeros elsewhere) is factored in place into L; X
+// ([mp][mp], zeroed) receives L^-1; W ([mp][32]) the diagonal blocks'
+// inverses; Xc ([m][m] FP64, may alias A) and Xf ([m][m] FP32, optional)
+// the compact inverse.  flag: bit 1 not positive definite, bit 2 a grid
+// barrier gave up.  sync: two zeroed words.
+size_t cov_padded(int m);
+cudaError_t launch_cov_factor(double* A, double* W, double* X, double* Xc, float* Xf, int m, unsigned* sync,
+                              int* flag, int sms, cudaStream_t s);
 cudaError_t launch_tr_subproblem(int n, const double* B, const double* g, double Delta, double alpha0,
                                  double* p_out, double* alpha_out, double* lam_out, cudaStream_t s);
 }  // namespace gbfit
