@@ -63,6 +63,18 @@ FLOPS_PER_POINT = 173
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 L2_FLUSH_BYTES = 256 << 20
+
+
+class L2Flush:
+    """Evict the workload from L2 between timed steps (untimed): write a
+    256 MiB buffer (twice the 129 MB L2)."""
+
+    def __init__(self, device):
+        import torch
+        self.w = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+
+    def zero_(self):
+        self.w.zero_()
 HBM_PEAK_GBS = 6785.9          # MEASURED_PEAKS.json: copy bandwidth of this pool's GB300s
 # DRAM bytes (read + write) per launch of the loop kernel (one whole fit of
 # the headline workload, 5 passes) from the ncu capture summarised in
@@ -240,7 +252,7 @@ def run_ours(args, rank, local, world):
     dev = torch.device("cuda", local)
     y = torch.as_tensor(pr.y).to(dev)
     sg = torch.as_tensor(pr.sigma).to(dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream()
 
     def fit(yy, ss):
@@ -363,7 +375,7 @@ def run_compare(args):
     dev = torch.device("cuda", 0)
     y = torch.as_tensor(pr.y).to(dev)
     sg = torch.as_tensor(pr.sigma).to(dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
     res = layouts_and_fp64(args, pr, y, sg, flush, dev)
     ref = trf.curve_fit_problem(pr.astype(np.float64), **TOL)
     rel = lambda a: float(np.max(np.abs(np.asarray(a) - ref["popt"]) / np.maximum(np.abs(ref["popt"]), 1.0)))
@@ -407,7 +419,7 @@ def run_sweep(args):
     from paper_2208_12187_gb300 import build, gbfit, synth
     build.build()
     gbfit.load()
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = L2Flush("cuda")
     sizes = [int(v) for v in args.sizes.split(",")]
     for m in sizes:
         pr = synth.gauss1d(m, seed=0)
@@ -482,7 +494,7 @@ def run_user(args):
     t_compile = time.perf_counter() - t0
     lid = gbfit.register_model(USER_LORENTZ_SRC, 4)
     print(json.dumps({"mode": "user", "compile_s_per_model": t_compile, "nvrtc": "both precisions, one program"}))
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = L2Flush("cuda")
 
     def timed(fit, m):
         for _ in range(3):

@@ -29,6 +29,7 @@ using namespace gbfit;
 namespace {
 
 constexpr int TILE_MIN = 2048, TILE_MAX = 65536, TILE_SPLIT = 304;   // TILE_SPLIT: grid when none is known
+constexpr size_t OWNER_MAX_FITS = 8;            // launches of at most this many fits use owner mode
 
 thread_local std::string g_err;
 
@@ -355,13 +356,15 @@ int run_fits(Ctx* c, const KernelSet* ks, int prec, std::vector<FitDesc>& hd, co
     if ((rc = ensure(c, L, ntiles, ngroups))) return rc;
     if ((rc = c->pinned(L.end))) return rc;
     char* hb = c->hbuf;
-    memset(hb, 0, L.res_hdr);
+    memset(hb, 0, L.res_hdr + 32);                  // the job image plus a zeroed result header
     Engine E = c->engine(L);
     E.sc[0] = (int)ntiles;
     E.sc[1] = (int)nf;
     E.sc[2] = 0;
     E.sc[3] = any_cov ? 2 * max_nfev + 6 : max_nfev + 4;   // rounds per evaluation (2 for covariance fits), plus slack
     E.sc[4] = (int)nf;
+    // few fits: each fit's combine and step stay on one CTA (warm code and state)
+    E.owner_mode = (nf <= OWNER_MAX_FITS && !any_cov) ? 1 : 0;
     memcpy(hb + L.eng, &E, sizeof E);
     memcpy(hb + L.desc, hd.data(), nf * sizeof(FitDesc));
     FitState* hs = (FitState*)(hb + L.state);
@@ -375,8 +378,8 @@ int run_fits(Ctx* c, const KernelSet* ks, int prec, std::vector<FitDesc>& hd, co
         // covariance row items cost in proportion to their index: largest first
         for (int t = 0; t < hd[f].n_tiles; ++t) hi[k++] = WorkItem{(int)f, hd[f].cov ? hd[f].n_tiles - 1 - t : t};
     }
-    CUDA_TRY(cudaMemcpyAsync(c->job, hb, L.res_hdr, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemsetAsync(c->job + L.res_hdr, 0, 32, s));   // out[]: running, rounds, abort; busy / wait ns
+    // one upload: the image and the zeroed header words out[] (running, rounds, abort; busy / wait ns)
+    CUDA_TRY(cudaMemcpyAsync(c->job, hb, L.res_hdr + 32, cudaMemcpyHostToDevice, s));
     double eval_ms = 0.0;
     int64_t eval_launches = 0;
     {

@@ -110,6 +110,9 @@ struct Engine {
     int* sm_cnt;           // [SM_IDS + 1] CTAs per SM of the loop kernel, then the round's next
                            // dynamic work item (all zero between launches)
     int sc[8];             // the scalars the pointers above refer to
+    int owner_mode;        // 1: fit f's final combine and step run in the CTA of rank f (launches of few
+                           // fits: that SM keeps the step's code and state warm); 0: in the last arriver
+    int owner_pad;
 };
 
 }  // namespace gbfit

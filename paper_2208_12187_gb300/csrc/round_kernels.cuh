@@ -766,13 +766,31 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
     }
     __syncthreads();
     if (!sm.flag[2]) return;
-    if (d.n_groups == 1) prefetch_state(stp, sm.trf);      // this CTA runs the step
+    if (d.n_groups == 1 && !E.owner_mode) prefetch_state(stp, sm.trf);      // this CTA runs the step
     if (threadIdx.x == 0) sm.t_fence = clock64();
     double* gout = E.group_part + (d.group_base + group) * KMAX;
     combine_rows<double>(E.tile_part_d + (d.tile_base + g0) * KMAX, gsize, K, sm.comb, sm.trf.tot);
     if (threadIdx.x == 0) {
         E.group_cnt[d.group_base + group] = 0;
         sm.t_group = clock64();
+    }
+    if (E.owner_mode) {
+        // the fit's owner CTA (owner_steps) combines the group sums and steps
+        if (threadIdx.x < K) gout[threadIdx.x] = sm.trf.tot[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int old = arrive_acq_rel(&E.fit_cnt[fit]);
+            if (old == d.n_groups - 1) {
+                trace_bump(stp->trace, TR_COMBINE, (unsigned long long)(sm.t_group - sm.t_mark));
+                trace_bump(stp->trace, TR_C_FENCE, (unsigned long long)(sm.t_fence - sm.t_mark));
+                trace_bump(stp->trace, TR_C_GROUP, (unsigned long long)(sm.t_group - sm.t_fence));
+                trace_bump(stp->trace, TR_TILE, (unsigned long long)(sm.t_mark - t_tile));
+                trace_bump(stp->trace, TR_PRE_TILE, (unsigned long long)(t_tile - t_item));
+                trace_bump(stp->trace, TR_TILE_LOOP, (unsigned long long)(sm.t_loop - t_tile));
+                trace_bump(stp->trace, TR_RING_WAIT, (unsigned long long)R.wait_cycles);
+            }
+        }
+        return;
     }
     if (d.n_groups > 1) {
         // second level: the last group of the fit combines the group sums
@@ -951,6 +969,63 @@ __device__ inline int grid_round_end(Engine* Ed, const Engine& E, int* ctl_smem,
     return *ctl_smem;
 }
 
+// Owner mode: after its items, the CTA of rank f waits (bounded) until every
+// group of fit f has published its sum, then combines the group sums in
+// index order and runs the fit's trust-region step.  The step then runs on
+// the same SM every round, with its code in that SM's instruction caches.
+template <class M, int PREC, class MS>
+__device__ void owner_combine_step(RoundSmem& sm, const Engine& E, int fit) {
+    constexpr int K = n_acc(M::N, PREC);
+    const FitDesc& d = sm.desc;
+    FitState* stp = E.state + fit;
+    long long t0 = clock64();
+    combine_rows<double>(E.group_part + d.group_base * KMAX, d.n_groups, K, sm.comb, sm.trf.tot);
+    if (threadIdx.x == 0) {
+        unsigned long long dt = (unsigned long long)(clock64() - t0);
+        trace_bump(stp->trace, TR_COMBINE, dt);
+        trace_bump(stp->trace, TR_C_FINAL, dt);
+    }
+    __syncthreads();
+    trf_step<PREC, MS>(d, stp, E.results + fit, sm.trf, E.running);
+    __syncthreads();
+}
+
+template <int PREC, class MS>
+__device__ void owner_steps(RoundSmem& sm, const Engine& E, Engine* Ed, int rank) {
+    const int nf = *E.nfits_dev;
+    for (int f = rank; f < nf; f += gridDim.x) {
+        FitState* stp = E.state + f;
+        if (threadIdx.x == 0) sm.flag[0] = __ldcg(&stp->run);
+        if (f != sm.desc_fit) {
+            const int* src = (const int*)(E.desc + f);
+            int* dst = (int*)&sm.desc;
+            for (int k = threadIdx.x; k < (int)(sizeof(FitDesc) / 4); k += EVAL_THREADS) dst[k] = src[k];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) sm.desc_fit = f;
+        if (sm.flag[0] != RS_RUNNING) {
+            __syncthreads();
+            continue;
+        }
+        prefetch_state(stp, sm.trf);                       // overlaps the wait
+        if (threadIdx.x == 0) {
+            const unsigned want = (unsigned)sm.desc.n_groups;
+            const unsigned* cnt = reinterpret_cast<const unsigned*>(E.fit_cnt + f);
+            const unsigned long long g0 = global_ns();
+            int ok = 1;
+            while (ld_acquire_u32(cnt) != want) {
+                if (global_ns() - g0 > ROUND_WAIT_LIMIT_NS) { ok = 0; break; }
+            }
+            if (ok) E.fit_cnt[f] = 0;
+            else atomicOr(&Ed->sc[7], CTL_ABORT);
+            sm.flag[3] = ok;
+        }
+        __syncthreads();
+        if (!sm.flag[3]) continue;
+        MS::dispatch(sm.desc.model, [&](auto m) { owner_combine_step<decltype(m), PREC, MS>(sm, E, f); });
+    }
+}
+
 // Persistent form of the iteration: pass constants at p0 (do_init), then
 // rounds of run_items separated by the grid barrier until no fit runs or the
 // round cap is reached.  One cooperative launch replaces a graph of
@@ -1014,6 +1089,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) fit_loop_kernel(const Engine*
     while (true) {
         unsigned long long t0 = global_ns();
         run_items<PREC, MS>(sm, E, R, first, E.sm_cnt + SM_IDS);
+        if (E.owner_mode) owner_steps<PREC, MS>(sm, E, Ed, first);
         unsigned long long t1 = global_ns();
         int c = grid_round_end(Ed, E, &sm.ctl, true);
         if (threadIdx.x == 0) {

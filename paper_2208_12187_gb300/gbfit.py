@@ -12,6 +12,7 @@ from __future__ import annotations
 import ctypes
 import math
 import os
+import threading
 from typing import Optional, Sequence
 
 import numpy as np
@@ -205,16 +206,38 @@ def _cov_info(sigma, m):
     return c.ctypes.data, c
 
 
-def _stream_ptr(stream):
-    if stream is None:
+_RAW_STREAM = None     # (current_device, current raw stream) functions of torch, once looked up
+
+
+def _current_stream_int() -> int:
+    """torch's current CUDA stream on the current device, as an integer (0 without torch or CUDA)."""
+    global _RAW_STREAM
+    if _RAW_STREAM is None:
         try:
             import torch
-            if torch.cuda.is_available():
-                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+            if not torch.cuda.is_available():
+                _RAW_STREAM = False
+            elif hasattr(torch._C, "_cuda_getCurrentRawStream"):
+                _RAW_STREAM = (torch._C._cuda_getDevice, torch._C._cuda_getCurrentRawStream)
+            else:
+                _RAW_STREAM = (None, lambda _d: torch.cuda.current_stream().cuda_stream)
         except ImportError:
-            pass
-        return ctypes.c_void_p(0)
-    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+            _RAW_STREAM = False
+    if not _RAW_STREAM:
+        return 0
+    dev_fn, raw_fn = _RAW_STREAM
+    return raw_fn(dev_fn() if dev_fn else 0)
+
+
+def _stream_int(stream) -> int:
+    if stream is None:
+        return _current_stream_int()
+    v = getattr(stream, "cuda_stream", stream)
+    return int(v or 0)
+
+
+def _stream_ptr(stream):
+    return ctypes.c_void_p(_stream_int(stream))
 
 
 def _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles=0,
@@ -245,6 +268,49 @@ def _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, 
 
 
 _PREC = {"fp64": PREC_FP64, "mixed": PREC_MIXED}
+
+
+_TLS = threading.local()
+_OPT_CACHE = {}        # option tuple -> Options (immutable once built)
+
+
+class _Scratch:
+    """Per-thread host buffer for one single-fit call's small arrays: p0, lb,
+    ub, grid (W, H), and the outputs popt | pcov | cost | nfev, status.  One
+    address lookup per thread instead of one per array per call."""
+    P0, LB, UB, GRID, OUT = 0, 8, 16, 24, 32            # offsets in doubles
+    INTS = 112                                           # nfev, status (two int32 in one double slot)
+
+    def __init__(self):
+        self.buf = (ctypes.c_double * 128)()
+        self.base = ctypes.addressof(self.buf)
+        self.v = np.frombuffer(self.buf, dtype=np.float64)
+        self.i64 = self.v.view(np.int64)
+        self.i32 = self.v.view(np.int32)
+
+
+def _scratch() -> _Scratch:
+    sc = getattr(_TLS, "sc", None)
+    if sc is None:
+        sc = _TLS.sc = _Scratch()
+    return sc
+
+
+def _cached_options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles,
+                    loss, f_scale):
+    """(address of an Options, keepalive); options without an x_scale vector are cached."""
+    if isinstance(x_scale, (int, float)) and x_scale == 1.0:
+        key = (ftol, xtol, gtol, max_nfev, absolute_sigma, precision, tile_points, group_tiles, loss, f_scale)
+        o = _OPT_CACHE.get(key)
+        if o is None:
+            o, _ = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points,
+                            group_tiles, loss, f_scale)
+            if len(_OPT_CACHE) < 256:
+                _OPT_CACHE[key] = o
+        return ctypes.addressof(o), o
+    o, keep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles,
+                       loss, f_scale)
+    return ctypes.addressof(o), (o, keep)
 
 
 def _vec(v, n):
@@ -299,35 +365,43 @@ def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None
     yp, dt, ykeep = _array_info(ydata)
     xp, xdt, xkeep = _array_info(xdata)
     m = int(ykeep.shape[0])
-    cov = _cov_info(sigma, m)                      # 2D sigma: full covariance (gbfit_curve_fit_cov)
+    cov = _cov_info(sigma, m) if sigma is not None else None   # 2D sigma: full covariance (gbfit_curve_fit_cov)
     sp, sdt, skeep = _array_info(None if cov else sigma)
     if xp is not None and xdt != dt or sp is not None and sdt != dt:
         raise TypeError("xdata, ydata and sigma must share one dtype")
-    gw = None
+    sc = _scratch()
+    v, base = sc.v, sc.base
+    gwp = None
     if grid_wh is not None:
         layout = X_GRID
-        gw = np.array([int(grid_wh[0]), int(grid_wh[1])], dtype=np.int64)
+        sc.i64[_Scratch.GRID] = int(grid_wh[0])
+        sc.i64[_Scratch.GRID + 1] = int(grid_wh[1])
+        gwp = base + 8 * _Scratch.GRID
         xp = None
     else:
         layout = X_SOA2 if (xkeep is not None and len(xkeep.shape) == 2) else X_VEC
-    p0a = _vec(p0, n)
-    lbv = None if lb is None else _vec(lb, n)
-    ubv = None if ub is None else _vec(ub, n)
-    opt, okeep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles,
-                          loss, f_scale)
-    out = np.zeros(n + n * n + 1)                  # popt | pcov | cost
-    ints = np.zeros(2, dtype=np.int32)             # nfev | status
-    a = out.ctypes.data
+    v[_Scratch.P0:_Scratch.P0 + n] = p0
+    lbp = ubp = None
+    if lb is not None:
+        v[_Scratch.LB:_Scratch.LB + n] = lb
+        lbp = base + 8 * _Scratch.LB
+    if ub is not None:
+        v[_Scratch.UB:_Scratch.UB + n] = ub
+        ubp = base + 8 * _Scratch.UB
+    optp, okeep = _cached_options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points,
+                                  group_tiles, loss, f_scale)
+    a = base + 8 * _Scratch.OUT                    # popt | pcov | cost
+    ip = base + 8 * _Scratch.INTS                  # nfev | status
     call = lib.gbfit_curve_fit
     if cov:
         call, sp = lib.gbfit_curve_fit_cov, cov[0]
-    rc = call(model, xp, m, layout, None if gw is None else gw.ctypes.data, yp, sp, dt,
-                             p0a.ctypes.data, None if lbv is None else lbv.ctypes.data,
-                             None if ubv is None else ubv.ctypes.data, ctypes.addressof(opt), a, a + 8 * n,
-                             a + 8 * (n + n * n), ints.ctypes.data, ints.ctypes.data + 4, _stream_ptr(stream))
+    rc = call(model, xp, m, layout, gwp, yp, sp, dt, base + 8 * _Scratch.P0, lbp, ubp, optp, a, a + 8 * n,
+              a + 8 * (n + n * n), ip, ip + 4, _stream_int(stream))
     if rc != OK:
         _check(rc)
-    return dict(popt=out[:n], pcov=out[n:n + n * n].reshape(n, n), cost=float(out[-1]), nfev=int(ints[0]),
+    o = v[_Scratch.OUT:_Scratch.OUT + n + n * n + 1].copy()
+    ints = sc.i32[2 * _Scratch.INTS:2 * _Scratch.INTS + 2]
+    return dict(popt=o[:n], pcov=o[n:n + n * n].reshape(n, n), cost=float(o[-1]), nfev=int(ints[0]),
                 status=int(ints[1]))
 
 
