@@ -483,14 +483,6 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             S.vec[VG][l] = cst->g[l];
         }
         const bool init = cst->phase == PH_INIT;
-        const double* srcB = init ? S.tot : cst->B;   // packed upper triangle
-        for (int e = l; e < 64; e += 32) {
-            int i = e >> 3, j = e & 7;
-            double b = 0.0;
-            if (i < n && j < n) { int a = min(i, j), c = max(i, j); b = srcB[a * n - a * (a - 1) / 2 + (c - a)]; }
-            S.B[e] = b;
-        }
-        __syncwarp();
         const double f2n = S.tot[NT + n];
         int status = FS_RUNNING;
         double f = cst->f, Delta = cst->Delta, alpha = cst->alpha;
@@ -524,14 +516,18 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             else if (ftol_ok) status = FS_FTOL;
             else if (xtol_ok) status = FS_XTOL;
         }
-        if (take) {
-            if (l < n) { S.vec[VX][l] = S.vec[VXT][l]; S.vec[VG][l] = S.tot[NT + l]; }
+        // the Gram at the (new) current point, unpacked from its packed upper triangle
+        {
+            const double* srcB = take ? S.tot : cst->B;
             for (int e = l; e < 64; e += 32) {
                 int i = e >> 3, j = e & 7;
                 double b = 0.0;
-                if (i < n && j < n) { int a = min(i, j), c = max(i, j); b = S.tot[a * n - a * (a - 1) / 2 + (c - a)]; }
+                if (i < n && j < n) { int a = min(i, j), c = max(i, j); b = srcB[a * n - a * (a - 1) / 2 + (c - a)]; }
                 S.B[e] = b;
             }
+        }
+        if (take) {
+            if (l < n) { S.vec[VX][l] = S.vec[VXT][l]; S.vec[VG][l] = S.tot[NT + l]; }
             __syncwarp();
             if (d.jac_scale && status == FS_RUNNING && l < n) {
                 double c = sqrt(S.B[l * 8 + l]);
@@ -546,6 +542,7 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
         if (status == FS_RUNNING) {
             double v, dv, sx;
             cl_scaling(d, cst, S, n, v, dv, sx);
+            if (l < 8) { S.vec[VV][l] = v; S.vec[VDV][l] = dv; S.vec[VSX][l] = sx; }   // for phase 2
             if (init) {
                 double xl = (l < n) ? S.vec[VX][l] : 0.0;
                 double dd = (l < n) ? (d.bounded ? sqrt(v) : 1.0) * sx : 1.0;
@@ -585,8 +582,8 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
 
     // ================= phase 2 (warp 0): scaled model matrix Ah = D B D + diag(C)
     if (warp == 0) {
-        double v, dv, sx;
-        cl_scaling(d, cst, S, n, v, dv, sx);
+        const double v = (l < 8) ? S.vec[VV][l] : 0.0, dv = (l < 8) ? S.vec[VDV][l] : 0.0;
+        const double sx = (l < 8) ? S.vec[VSX][l] : 1.0;
         double g = (l < n) ? S.vec[VG][l] : 0.0;
         double dl = (l < n) ? (d.bounded ? sqrt(v) : 1.0) * sx : 0.0;
         if (l < 8) {
@@ -758,10 +755,18 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
         }
         if (l < 8) S.vec[VXT][l] = (l < n) ? xt : 0.0;
         // ||s_h||, ||w||, ||x|| for the next iteration's radius and xtol tests
-        double ss = gsum8(sh * sh), ww = gsum8(step * step), xx = gsum8(x * x);
-        double nv = (l == 0) ? ss : (l == 1) ? ww : xx;
+        // the three sums in one butterfly: lanes 0-7 ||s_h||^2, 8-15 ||w||^2,
+        // 16-23 ||x||^2 (each group in gsum8's order)
+        double nv;
+        {
+            const double ww_l = __shfl_sync(FULL, step * step, l & 7), xx_l = __shfl_sync(FULL, x * x, l & 7);
+            nv = (l < 8) ? sh * sh : (l < 16) ? ww_l : (l < 24) ? xx_l : 0.0;
+            nv += __shfl_xor_sync(FULL, nv, 4);
+            nv += __shfl_xor_sync(FULL, nv, 2);
+            nv += __shfl_xor_sync(FULL, nv, 1);
+        }
         nv = sqrt(nv);
-        double s_norm = __shfl_sync(FULL, nv, 0), w_norm = __shfl_sync(FULL, nv, 1), x_norm = __shfl_sync(FULL, nv, 2);
+        double s_norm = __shfl_sync(FULL, nv, 0), w_norm = __shfl_sync(FULL, nv, 8), x_norm = __shfl_sync(FULL, nv, 16);
         if (l < n) { st->x[l] = x; st->xt[l] = xt; st->g[l] = S.vec[VG][l]; st->s_h[l] = sh; }
         for (int k = l; k < NT; k += 32) {
             int a = 0, r = k;
