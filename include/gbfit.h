@@ -412,7 +412,7 @@ typedef struct gbfit_stats {
     double point_passes;      /* sum over fits of m * nfev                             */
     double eval_ms;           /* profiling on: summed CUDA-event time of loop-kernel launches */
     int64_t eval_launches;    /* profiling on: loop-kernel launches timed              */
-    double phase_cycles[24];  /* summed over fits and iterations (SM cycles unless noted):
+    double phase_cycles[32];  /* summed over fits and iterations (SM cycles unless noted):
                                  0 own tile, 1 combine, 2 accept/terminate logic,
                                  3 n x n eigen-decomposition, 4 combine: store, fence and
                                  arrival, 5 step (solve, Algorithm 2, bounded selection),
@@ -424,7 +424,11 @@ typedef struct gbfit_stats {
                                  decompositions (count), 19 Algorithm 2 iterations
                                  (count), 20 bounded non-full steps (count), 21 item start to
                                  tile start, 22 tile loop (of 0), 23 waits for streamed
-                                 chunks inside the tile loop (of 22) */
+                                 chunks inside the tile loop (of 22); owner mode (ns of the
+                                 global timer, per round of the fit's owner CTA): 24 round
+                                 (barrier exit to barrier arrival), 25 owner's wait for the
+                                 group sums, 26 barrier (arrival to exit), 27 launch start
+                                 to the first round (once per fit); 28-31 spare */
     double host_ms;           /* host wall time inside the run of fits (job set-up, launch,
                                  wait for the device, result copy)                    */
     double loop_busy_ms;      /* loop kernel, summed over CTAs: time in rounds' work    */

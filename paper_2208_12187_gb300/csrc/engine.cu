@@ -425,7 +425,7 @@ int run_fits(Ctx* c, const KernelSet* ks, int prec, std::vector<FitDesc>& hd, co
         g_stats.loop_wait_ms += acct[1] * 1e-6;
         g_stats.loop_ctas += loop_grid(c, ks, prec);
         for (size_t f = 0; f < nf; ++f) {
-            for (int k = 0; k < 24; ++k) g_stats.phase_cycles[k] += hr[f].trace[k];
+            for (int k = 0; k < 32; ++k) g_stats.phase_cycles[k] += hr[f].trace[k];
             g_stats.passes += hr[f].nfev;
             g_stats.point_passes += double(hd[f].m) * hr[f].nfev;
         }

@@ -79,7 +79,7 @@ struct alignas(16) FitState {
     double s_h[NMAX];      // scaled step of the pending trial
     double pad1;           // (the prefix above is a whole number of 16-byte words)
     // --- (the step reads everything above from a shared-memory copy) ---
-    unsigned long long trace[24];  // SM cycles / counts per phase of the step, summed over iterations
+    unsigned long long trace[32];  // SM cycles / ns / counts per phase (TracePhase), summed over iterations
 };
 
 struct WorkItem { int fit; int tile; };

@@ -932,35 +932,45 @@ __device__ inline int grid_round_end(Engine* Ed, const Engine& E, int* ctl_smem,
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned* cnt = (unsigned*)&Ed->sc[5];
-        unsigned* gen = (unsigned*)&Ed->sc[6];
-        volatile int* ctl = &Ed->sc[7];
-        unsigned g = ld_acquire_u32(gen);
+        unsigned* gen = (unsigned*)&Ed->sc[6];      // (generation << 2) | control word of the round closed last
+        volatile int* ctl = &Ed->sc[7];             // abort requests raised during the round
+        const unsigned g = ld_acquire_u32(gen);
         unsigned old;
         asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(cnt) : "memory");
         int c;
         if (old == gridDim.x - 1) {
+            // the loads the decision needs go out together, then one release
+            const int pend = *ctl;
+            int r = 0, run = 0, cap = 0;
+            if (count_round) {
+                r = *(volatile int*)E.rounds;
+                run = *(volatile int*)E.running;
+                cap = *(volatile int*)E.max_rounds;
+            }
             *(volatile unsigned*)cnt = 0;
-            c = *ctl & CTL_ABORT;
+            c = pend & CTL_ABORT;
             if (count_round) {
                 E.sm_cnt[SM_IDS] = 0;                 // next round's dynamic items start over
-                int r = ++(*E.rounds);
-                int run = *(volatile int*)E.running;
+                r += 1;
+                *(volatile int*)E.rounds = r;
                 E.out[0] = run;
                 E.out[1] = r;
-                if (run <= 0 || r >= *E.max_rounds) c |= CTL_STOP;
+                if (run <= 0 || r >= cap) c |= CTL_STOP;
             }
-            *ctl = c;
-            st_release_u32(gen, g + 1);
+            st_release_u32(gen, (((g >> 2) + 1u) << 2) | (unsigned)c);
         } else {
-            unsigned long long t0 = global_ns();
-            while (ld_acquire_u32(gen) == g) {
+            const unsigned long long t0 = global_ns();
+            unsigned v;
+            bool timed_out = false;
+            while ((v = ld_acquire_u32(gen)) == g) {
                 __nanosleep(128);
                 if (global_ns() - t0 > ROUND_WAIT_LIMIT_NS) {
                     atomicOr((int*)ctl, CTL_ABORT);
+                    timed_out = true;
                     break;
                 }
             }
-            c = *ctl;
+            c = timed_out ? CTL_ABORT : (int)(v & 3u);   // the control word travels with the release
         }
         if (c & CTL_ABORT) atomicOr(E.out + 2, 1);
         *ctl_smem = c;
@@ -1019,6 +1029,7 @@ __device__ void owner_steps(RoundSmem& sm, const Engine& E, Engine* Ed, int rank
             if (ok) E.fit_cnt[f] = 0;
             else atomicOr(&Ed->sc[7], CTL_ABORT);
             sm.flag[3] = ok;
+            trace_bump(stp->trace, TR_OWNER_WAIT_NS, global_ns() - g0);
         }
         __syncthreads();
         if (!sm.flag[3]) continue;
@@ -1034,6 +1045,7 @@ template <int PREC, class MS>
 __global__ void __launch_bounds__(EVAL_THREADS, 2) fit_loop_kernel(const Engine* __restrict__ Ep, int do_init) {
     __shared__ RoundSmem sm;
     extern __shared__ __align__(128) float ring_buf[];
+    const unsigned long long t_launch = global_ns();
     stage_engine(sm, Ep);
     const Engine& E = sm.eng;
     Engine* Ed = const_cast<Engine*>(Ep);
@@ -1047,6 +1059,21 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) fit_loop_kernel(const Engine*
         asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
         sm.flag[0] = (int)smid;
         sm.flag[1] = atomicAdd(E.sm_cnt + (smid < SM_IDS ? smid : SM_IDS - 1), 1);
+    }
+    if (do_init) {
+        // pass constants at p0 (strided by block index: needs no rank), published by the rank barrier
+        int nf = *E.nfits_dev;
+        for (int f = blockIdx.x; f < nf; f += gridDim.x) {
+            if (threadIdx.x < 32) {
+                const FitDesc& d = E.desc[f];
+                FitState* st = E.state + f;
+                int l = threadIdx.x;
+                if (l < 8) { sm.trf.vec[VX][l] = (l < d.n) ? st->x[l] : 0.0; sm.trf.vec[VXT][l] = sm.trf.vec[VX][l]; }
+                __syncwarp();
+                prep_pass<PREC, MS>(d, st, sm.trf);
+            }
+            __syncthreads();
+        }
     }
     if (grid_round_end(Ed, E, &sm.ctl, false)) return;
     int first;
@@ -1068,24 +1095,12 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) fit_loop_kernel(const Engine*
         __syncthreads();
         first = sm.flag[2];
     }
-    if (do_init) {
-        int nf = *E.nfits_dev;
-        for (int f = blockIdx.x; f < nf; f += gridDim.x) {
-            if (threadIdx.x < 32) {
-                const FitDesc& d = E.desc[f];
-                FitState* st = E.state + f;
-                int l = threadIdx.x;
-                if (l < 8) { sm.trf.vec[VX][l] = (l < d.n) ? st->x[l] : 0.0; sm.trf.vec[VXT][l] = sm.trf.vec[VX][l]; }
-                __syncwarp();
-                prep_pass<PREC, MS>(d, st, sm.trf);
-            }
-            __syncthreads();
-        }
-        if (grid_round_end(Ed, E, &sm.ctl, false)) return;
-    }
     // time accounting of the loop (result header, 64-bit words 2..3):
     // per-CTA time in rounds' work and time waiting at the barrier
     unsigned long long* acct = reinterpret_cast<unsigned long long*>(E.out) + 2;
+    // owner mode: the owner CTA of a fit also times its rounds (global timer)
+    unsigned long long* otrace = (E.owner_mode && first < *E.nfits_dev) ? E.state[first].trace : nullptr;
+    if (otrace && threadIdx.x == 0) trace_bump(otrace, TR_START_NS, global_ns() - t_launch);
     while (true) {
         unsigned long long t0 = global_ns();
         run_items<PREC, MS>(sm, E, R, first, E.sm_cnt + SM_IDS);
@@ -1093,8 +1108,13 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) fit_loop_kernel(const Engine*
         unsigned long long t1 = global_ns();
         int c = grid_round_end(Ed, E, &sm.ctl, true);
         if (threadIdx.x == 0) {
+            const unsigned long long t2 = global_ns();
             atomicAdd(acct, t1 - t0);
-            atomicAdd(acct + 1, global_ns() - t1);
+            atomicAdd(acct + 1, t2 - t1);
+            if (otrace) {
+                trace_bump(otrace, TR_ROUND_NS, t1 - t0);
+                trace_bump(otrace, TR_BARRIER_NS, t2 - t1);
+            }
         }
         if (c) break;
     }

@@ -45,7 +45,7 @@ struct FitResult {
     double popt[NMAX];
     double pcov[NMAX * NMAX];
     double tot[KMAX];      // sums of the last evaluation (Gram, gradient, cost)
-    double trace[24];      // SM cycles per phase (see TracePhase), summed over iterations
+    double trace[32];      // per phase (see TracePhase), summed over iterations
     double cost;
     int nfev, njev, fit_status, rounds;
 };
@@ -53,7 +53,8 @@ struct FitResult {
 // Phases timed (clock64, SM cycles) inside the step, summed per fit.
 enum TracePhase { TR_TILE = 0, TR_COMBINE, TR_LOGIC, TR_EIGEN, TR_C_FENCE, TR_STEP, TR_PREP, TR_FINISH,
                   TR_C_GROUP, TR_C_FINAL, TR_E_WARM, TR_E_J32, TR_E_NS, TR_E_RR, TR_E_SWEEPS, TR_E_REFINES,
-                  TR_GN, TR_N_GN, TR_N_EIG, TR_N_ALG2IT, TR_N_BOUNDED, TR_PRE_TILE, TR_TILE_LOOP, TR_RING_WAIT };
+                  TR_GN, TR_N_GN, TR_N_EIG, TR_N_ALG2IT, TR_N_BOUNDED, TR_PRE_TILE, TR_TILE_LOOP, TR_RING_WAIT,
+                  TR_ROUND_NS, TR_OWNER_WAIT_NS, TR_BARRIER_NS, TR_START_NS, TR_RES28, TR_RES29, TR_RES30, TR_RES31 };
 
 // Shared-memory workspace of the warp that runs one fit's step.
 struct TrfSmem {

@@ -576,7 +576,7 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
         trace_add(st, TR_FINISH, tclk);
         if (t == 0) { st->run = RS_DONE; st->fit_status = status; atomicSub(running, 1); }
         __syncthreads();
-        if (t < 24) res->trace[t] = double(__ldcg(st->trace + t));
+        if (t < 32) res->trace[t] = double(__ldcg(st->trace + t));
         return;
     }
 

@@ -65,12 +65,13 @@ class Stats(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int64), ("fits", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("graph_rounds", ctypes.c_int64), ("passes", ctypes.c_int64), ("point_passes", ctypes.c_double),
                 ("eval_ms", ctypes.c_double), ("eval_launches", ctypes.c_int64),
-                ("phase_cycles", ctypes.c_double * 24), ("host_ms", ctypes.c_double),
+                ("phase_cycles", ctypes.c_double * 32), ("host_ms", ctypes.c_double),
                 ("loop_busy_ms", ctypes.c_double), ("loop_wait_ms", ctypes.c_double), ("loop_ctas", ctypes.c_int64)]
 
 PHASES = ["tile", "combine", "logic", "eigen", "comb_fence", "step", "prep", "finish", "comb_group", "comb_final",
           "eig_warm", "eig_j32", "eig_ns", "eig_rr", "j32_sweeps", "refine_passes", "gn_path", "n_gn", "n_eig",
-          "n_alg2_iters", "n_bounded_nonfull", "pre_tile", "tile_loop", "ring_wait"]
+          "n_alg2_iters", "n_bounded_nonfull", "pre_tile", "tile_loop", "ring_wait",
+          "round_ns", "owner_wait_ns", "barrier_ns", "start_ns", "spare28", "spare29", "spare30", "spare31"]
 
 
 class ServerConfig(ctypes.Structure):
