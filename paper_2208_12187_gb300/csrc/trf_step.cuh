@@ -324,12 +324,11 @@ __device__ inline int eig_fast(int n, const double* Ah, const double* Vwarm, Trf
 
 // Coleman-Li scaling at the current x, g (lane values; lanes >= n: v = dv = 0).
 // st: the fit's state (the step passes its shared-memory copy).
-__device__ __forceinline__ void cl_scaling(const FitDesc& d, const FitState* st, const TrfSmem& S, int n,
-                                           double& v, double& dv, double& sx) {
+__device__ __forceinline__ void cl_scaling_xg(const FitDesc& d, const FitState* st, int n, double x, double g,
+                                              double& v, double& dv, double& sx) {
     int l = threadIdx.x & 31;
     v = 0.0; dv = 0.0; sx = 1.0;
     if (l < n) {
-        double x = S.vec[VX][l], g = S.vec[VG][l];
         double lb = d.lb[l], ub = d.ub[l];
         v = 1.0;
         if (d.bounded) {
@@ -338,6 +337,12 @@ __device__ __forceinline__ void cl_scaling(const FitDesc& d, const FitState* st,
         }
         sx = d.jac_scale ? rcp64(st->scale_inv[l]) : d.xscale[l];
     }
+}
+__device__ __forceinline__ void cl_scaling(const FitDesc& d, const FitState* st, const TrfSmem& S, int n,
+                                           double& v, double& dv, double& sx) {
+    int l = threadIdx.x & 31;
+    double x = (l < n) ? S.vec[VX][l] : 0.0, g = (l < n) ? S.vec[VG][l] : 0.0;
+    cl_scaling_xg(d, st, n, x, g, v, dv, sx);
 }
 
 // Pass constants for evaluating xt relative to x (warp 0).
@@ -381,8 +386,51 @@ __device__ void prep_pass(const FitDesc& d, FitState* st, TrfSmem& S) {
 }
 
 // Scalar slots of TrfSmem::sd / si shared between the phases.
-enum { SD_F = 0, SD_DELTA, SD_ALPHA, SD_GNORM, SD_SC, SD_MIND };
-enum { SI_STATUS = 0, SI_NFEV, SI_NJEV, SI_FACTOR, SI_GN, SI_REJECTED, SI_PCOV };
+enum { SD_F = 0, SD_DELTA, SD_ALPHA, SD_GNORM, SD_SC, SD_MIND, SD_PT2 };
+enum { SI_STATUS = 0, SI_NFEV, SI_NJEV, SI_FACTOR, SI_GN, SI_REJECTED, SI_PCOV, SI_SPEC };
+
+// Phase 2 on one warp: D, D g and the Coleman-Li diagonal C, then the scaled
+// model matrix Ah = D B D + diag(C), from the scaling (v, dv, sx), the
+// gradient g (lane values) and the full Gram Bf.
+__device__ __forceinline__ void scaled_model(const FitDesc& d, int n, double v, double dv, double sx, double g,
+                                             const double* Bf, TrfSmem& S) {
+    const int l = threadIdx.x & 31;
+    double dl = (l < n) ? (d.bounded ? sqrt(v) : 1.0) * sx : 0.0;
+    if (l < 8) {
+        S.vec[VD][l] = dl;
+        S.vec[VGH][l] = dl * g;
+        S.vec[VC][l] = (l < n && d.bounded) ? g * dv * sx * sx : 0.0;
+    }
+    __syncwarp();
+    for (int e = l; e < 64; e += 32) {
+        int i = e >> 3, j = e & 7;
+        double a = 0.0;
+        if (i < n && j < n) a = fma(S.vec[VD][i] * S.vec[VD][j], Bf[e], (i == j) ? S.vec[VC][i] : 0.0);
+        S.Ah[e] = a;
+    }
+    __syncwarp();
+}
+
+// Gauss-Newton fast path on one warp: when Ah is safely full rank, the
+// FP64-accurate solution of Ah pt = -D g into VSTR and its squared norm in
+// pt2 (+inf when Ah is not positive definite).  Returns whether the solve is
+// trusted (refined_ok).
+__device__ __forceinline__ bool gn_try(int n, TrfSmem& S, double& pt2) {
+    const int l = threadIdx.x & 31;
+    float sc = 1.0f, mind = 0.0f;
+    bool ok = inv32(n, S.Ah, S.Lf, sc, mind);
+    ok = __all_sync(FULL, ok);
+    pt2 = INFINITY;
+    if (ok) {
+        double gh = (l < n) ? S.vec[VGH][l] : 0.0;
+        float d1, d2;
+        double pt = solve_refined(n, S.Ah, S.Lf, sc, -gh, S.vec[VTMP], d1, d2);
+        ok = refined_ok(d1, d2, mind);
+        pt2 = gsum8(pt * pt);
+        if (l < 8) S.vec[VSTR][l] = pt;
+    }
+    return ok;
+}
 
 // Result record with pcov (R13) from an FP64-accurate eigen-decomposition of
 // the unscaled Gram at the solution.  All CTA threads call.
@@ -563,6 +611,30 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             S.si[SI_REJECTED] = rejected ? 1 : 0;
             st->factor_valid = factor_valid;   // the eigen cache describes the current B only
         }
+    } else if (warp == 1) {
+        // ---- speculation (warp 1, on another sub-partition, while warp 0
+        // decides): phase 2 and the Gauss-Newton fast path at the trial point
+        // as if the trial is accepted (the common case), with the same
+        // arithmetic as the path after the decision.  Used when it is.
+        int spec = 0;
+        if (!d.jac_scale) {
+            const double x = (l < n) ? cst->xt[l] : 0.0, g = (l < n) ? S.tot[NT + l] : 0.0;
+            for (int e = l; e < 64; e += 32) {
+                int i = e >> 3, j = e & 7;
+                double b = 0.0;
+                if (i < n && j < n) { int a = min(i, j), c = max(i, j); b = S.tot[a * n - a * (a - 1) / 2 + (c - a)]; }
+                S.W[e] = b;
+            }
+            __syncwarp();
+            double v, dv, sx;
+            cl_scaling_xg(d, cst, n, x, g, v, dv, sx);
+            scaled_model(d, n, v, dv, sx, g, S.W, S);
+            double pt2;
+            const bool ok = gn_try(n, S, pt2);
+            spec = 1 | (ok ? 2 : 0);
+            if (l == 0) S.sd[SD_PT2] = pt2;
+        }
+        if (l == 0) S.si[SI_SPEC] = spec;
     }
     __syncthreads();
     trace_add(st, TR_LOGIC, tclk);
@@ -580,30 +652,10 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
         return;
     }
 
-    // ================= phase 2 (warp 0): scaled model matrix Ah = D B D + diag(C)
-    if (warp == 0) {
-        const double v = (l < 8) ? S.vec[VV][l] : 0.0, dv = (l < 8) ? S.vec[VDV][l] : 0.0;
-        const double sx = (l < 8) ? S.vec[VSX][l] : 1.0;
-        double g = (l < n) ? S.vec[VG][l] : 0.0;
-        double dl = (l < n) ? (d.bounded ? sqrt(v) : 1.0) * sx : 0.0;
-        if (l < 8) {
-            S.vec[VD][l] = dl;
-            S.vec[VGH][l] = dl * g;
-            S.vec[VC][l] = (l < n && d.bounded) ? g * dv * sx * sx : 0.0;
-        }
-        __syncwarp();
-        for (int e = l; e < 64; e += 32) {
-            int i = e >> 3, j = e & 7;
-            double a = 0.0;
-            if (i < n && j < n) a = fma(S.vec[VD][i] * S.vec[VD][j], S.B[e], (i == j) ? S.vec[VC][i] : 0.0);
-            S.Ah[e] = a;
-        }
-    }
-    __syncthreads();
-
-    // ================= Gauss-Newton fast path (warp 0): when B_hat is safely
-    // full rank (no eigenvalue near the rank cutoff) and the trial step lies in
-    // the region, the step needs no eigen-decomposition.
+    // ================= phase 2: scaled model matrix Ah = D B D + diag(C), and
+    // the Gauss-Newton fast path: when B_hat is safely full rank (no
+    // eigenvalue near the rank cutoff) and the trial step lies in the region,
+    // the step needs no eigen-decomposition.
     // Guard: the refinement must contract (ratio ~ eps32 cond of the
     // equilibrated matrix), and lambda_min >= min_diag / cond must stay far
     // above the rank cutoff lambda_max 8 n eps64 (lambda_max <= n here), so
@@ -611,26 +663,32 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
     // After a rejected trial B_hat and g_hat are unchanged and Delta has
     // shrunk below the rejected step (Algorithm 3), so the Gauss-Newton step
     // (inside the old region or not) cannot be inside the new one: skip it.
-    if (warp == 0 && !S.si[SI_REJECTED]) {
-        float sc = 1.0f, mind = 0.0f;
-        bool ok = inv32(n, S.Ah, S.Lf, sc, mind);
-        ok = __all_sync(FULL, ok);
-        bool inside = false;
-        if (ok) {
-            double gh = (l < n) ? S.vec[VGH][l] : 0.0;
-            float d1, d2;
-            double pt = solve_refined(n, S.Ah, S.Lf, sc, -gh, S.vec[VTMP], d1, d2);
-            ok = refined_ok(d1, d2, mind);
-            double Delta = S.sd[SD_DELTA];
-            inside = gsum8(pt * pt) <= Delta * Delta;
-            if (l < 8) S.vec[VSTR][l] = pt;
+    // An accepted trial takes warp 1's speculative results as they are.
+    const bool spec_used = (S.si[SI_SPEC] & 1) && !S.si[SI_REJECTED];
+    if (!spec_used) {
+        if (warp == 0) {
+            const double v = (l < 8) ? S.vec[VV][l] : 0.0, dv = (l < 8) ? S.vec[VDV][l] : 0.0;
+            const double sx = (l < 8) ? S.vec[VSX][l] : 1.0;
+            const double g = (l < n) ? S.vec[VG][l] : 0.0;
+            scaled_model(d, n, v, dv, sx, g, S.B, S);
+            if (!S.si[SI_REJECTED]) {
+                double pt2;
+                const bool ok = gn_try(n, S, pt2);
+                const double Delta = S.sd[SD_DELTA];
+                const bool inside = ok && pt2 <= Delta * Delta;
+                if (l == 0) {
+                    S.si[SI_GN] = inside ? 1 : 0;
+                    if (inside) trace_bump(st->trace, TR_N_GN, 1);
+                }
+            } else if (l == 0) {
+                S.si[SI_GN] = 0;
+            }
         }
-        if (l == 0) {
-            S.si[SI_GN] = (ok && inside) ? 1 : 0;
-            if (ok && inside) trace_bump(st->trace, TR_N_GN, 1);
-        }
-    } else if (warp == 0 && threadIdx.x == 0) {
-        S.si[SI_GN] = 0;
+    } else if (warp == 0 && l == 0) {
+        const double Delta = S.sd[SD_DELTA];
+        const bool inside = (S.si[SI_SPEC] & 2) && S.sd[SD_PT2] <= Delta * Delta;
+        S.si[SI_GN] = inside ? 1 : 0;
+        if (inside) trace_bump(st->trace, TR_N_GN, 1);
     }
     __syncthreads();
     trace_add(st, TR_GN, tclk);
