@@ -30,6 +30,7 @@ namespace {
 
 constexpr int TILE_MIN = 2048, TILE_MAX = 65536, TILE_SPLIT = 304;   // TILE_SPLIT: grid when none is known
 constexpr size_t OWNER_MAX_FITS = 8;            // launches of at most this many fits use owner mode
+constexpr bool QUEUE_MODE = true;               // larger launches run without lock-step rounds
 
 thread_local std::string g_err;
 
@@ -83,7 +84,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Byte layout of one call's job buffer: what the host uploads ([0, res_hdr))
 // and what it reads back ([res_hdr, end)) are each one contiguous copy.
 struct JobLayout {
-    size_t eng, desc, state, items, gcnt, fcnt, smcnt, res_hdr, res, end;
+    size_t eng, desc, state, items, gcnt, fcnt, smcnt, bits, ntc, res_hdr, res, end;
     JobLayout(size_t nf, size_t ntiles, size_t ngroups) {
         size_t o = 0;
         eng = o;     o += align256(sizeof(Engine));
@@ -93,6 +94,8 @@ struct JobLayout {
         gcnt = o;    o += align256(ngroups * sizeof(int));
         fcnt = o;    o += align256(nf * sizeof(int));
         smcnt = o;   o += align256((SM_IDS + 1) * sizeof(int));
+        bits = o;    o += align256((nf + 31) / 32 * sizeof(unsigned));
+        ntc = o;     o += align256(nf * sizeof(int));
         res_hdr = o; o += 256;
         res = o;     o += align256(nf * sizeof(FitResult));
         end = o;
@@ -140,6 +143,8 @@ struct Ctx {
         E.group_cnt = (int*)(job + L.gcnt);
         E.fit_cnt = (int*)(job + L.fcnt);
         E.sm_cnt = (int*)(job + L.smcnt);
+        E.fit_bits = (unsigned*)(job + L.bits);
+        E.next_tile = (int*)(job + L.ntc);
         E.tile_part_d = tile_part_d; E.group_part = group_part;
         E.n_items = &ed->sc[0]; E.running = &ed->sc[1]; E.rounds = &ed->sc[2];
         E.max_rounds = &ed->sc[3]; E.nfits_dev = &ed->sc[4];
@@ -363,10 +368,17 @@ int run_fits(Ctx* c, const KernelSet* ks, int prec, std::vector<FitDesc>& hd, co
     E.sc[2] = 0;
     E.sc[3] = any_cov ? 2 * max_nfev + 6 : max_nfev + 4;   // rounds per evaluation (2 for covariance fits), plus slack
     E.sc[4] = (int)nf;
-    // few fits: each fit's combine and step stay on one CTA (warm code and state)
+    // few fits: each fit's combine and step stay on one CTA (warm code and state);
+    // many fits: no lock-step rounds (a fit's tiles are re-armed by its own step)
     E.owner_mode = (nf <= OWNER_MAX_FITS && !any_cov) ? 1 : 0;
+    E.queue_mode = (QUEUE_MODE && nf > OWNER_MAX_FITS && !any_cov) ? 1 : 0;
     memcpy(hb + L.eng, &E, sizeof E);
     memcpy(hb + L.desc, hd.data(), nf * sizeof(FitDesc));
+    {
+        unsigned* bits = (unsigned*)(hb + L.bits);     // every fit starts with all its tiles claimable
+        for (size_t w = 0; w < (nf + 31) / 32; ++w)
+            bits[w] = (w + 1) * 32 <= nf ? 0xffffffffu : ((1u << (nf % 32)) - 1u);
+    }
     FitState* hs = (FitState*)(hb + L.state);
     WorkItem* hi = (WorkItem*)(hb + L.items);
     size_t k = 0;

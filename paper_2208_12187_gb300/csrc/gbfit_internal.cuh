@@ -112,7 +112,10 @@ struct Engine {
     int sc[8];             // the scalars the pointers above refer to
     int owner_mode;        // 1: fit f's final combine and step run in the CTA of rank f (launches of few
                            // fits: that SM keeps the step's code and state warm); 0: in the last arriver
-    int owner_pad;
+    int queue_mode;        // 1: no lock-step rounds: a fit's tiles are claimed from its own counter
+                           // and re-armed by its step (batches of many fits); 0: rounds
+    unsigned* fit_bits;    // queue mode: bit f set while fit f has unclaimed tiles ([ceil(fits / 32)])
+    int* next_tile;        // queue mode: per fit, the next tile to claim in its current evaluation
 };
 
 }  // namespace gbfit

@@ -820,6 +820,14 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
     __syncthreads();
     trf_step<PREC, MS>(d, stp, E.results + fit, sm.trf, E.running);
     __syncthreads();
+    if (E.queue_mode && threadIdx.x == 0 && sm.trf.si[SI_STATUS] == FS_RUNNING) {
+        // queue mode: the next evaluation's tiles become claimable (the CTA
+        // barrier above orders the new state before these releases)
+        unsigned old;
+        asm volatile("atom.release.gpu.global.exch.b32 %0, [%1], 0;" : "=r"(old) : "l"(E.next_tile + fit) : "memory");
+        asm volatile("atom.release.gpu.global.or.b32 %0, [%1], %2;"
+                     : "=r"(old) : "l"(E.fit_bits + (fit >> 5)), "r"(1u << (fit & 31)) : "memory");
+    }
 }
 
 // Copy the engine record into shared memory (round_setup's barrier publishes it).
@@ -1037,6 +1045,124 @@ __device__ void owner_steps(RoundSmem& sm, const Engine& E, Engine* Ed, int rank
     }
 }
 
+// ---- queue mode (launches of many fits): no lock-step rounds.  Fit f's
+// tiles of its current evaluation are claimed from next_tile[f]; bit f of
+// fit_bits says it may still have some.  The claimer of the last tile clears
+// the bit; the fit's step re-arms both for the next evaluation after writing
+// the new state (process_item).  So a fit's next pass starts as soon as its
+// step ends, and no CTA waits for the slowest fit of a round.  A CTA with
+// nothing to claim backs off and looks again; it leaves when no fit runs, on
+// the abort bit, or after a bounded idle wait (raising the abort bit).
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// Warp 0: one look over the bitmap for a claimable tile (fit, tile), or fit = -1.
+__device__ __forceinline__ void queue_claim(const Engine& E, int nf, int rank, int& fit, int& tile) {
+    const int l = threadIdx.x & 31;
+    const int nw = (nf + 31) / 32;
+    fit = -1;
+    tile = -1;
+    for (int base = 0; base < nw && fit < 0; base += 32) {
+        const int w = (rank + base + l) % nw;
+        const unsigned bits = (base + l < nw) ? __ldcg(E.fit_bits + w) : 0u;
+        unsigned any = __ballot_sync(FULL, bits != 0u);
+        while (any && fit < 0) {
+            const int src = __ffs(any) - 1;
+            any &= any - 1;
+            const unsigned b = __shfl_sync(FULL, bits, src);
+            const int ws = __shfl_sync(FULL, w, src);
+            int f = -1, t = -1;
+            if (l == 0) {
+                // one set bit of the word, from a rank-dependent position
+                const int rot = rank & 31;
+                const unsigned r = __funnelshift_r(b, b, rot);
+                const int bit = ((__ffs(r) - 1) + rot) & 31;
+                const int cand = ws * 32 + bit;
+                if (cand < nf) {
+                    const int nt = __ldg(&E.desc[cand].n_tiles);
+                    const unsigned c = atom_add_acq_rel(reinterpret_cast<unsigned*>(E.next_tile + cand), 1u);
+                    if ((int)c < nt) {
+                        f = cand;
+                        t = (int)c;
+                        if ((int)c == nt - 1) atomicAnd(E.fit_bits + ws, ~(1u << bit));   // the epoch is claimed
+                    }
+                }
+            }
+            fit = __shfl_sync(FULL, f, 0);
+            tile = __shfl_sync(FULL, t, 0);
+        }
+    }
+}
+
+template <int PREC, class MS>
+__device__ void queue_loop(RoundSmem& sm, const Engine& E, Engine* Ed, RingState& R, int rank,
+                           unsigned long long* acct) {
+    const int nf = *E.nfits_dev;
+    volatile int* ctl = &Ed->sc[7];
+    unsigned long long busy = 0, idle = 0;
+    while (true) {
+        const unsigned long long t0 = global_ns();
+        if (threadIdx.x < 32) {
+            int fit = -1, tile = -1, stop = 0;
+            unsigned back = 32;
+            while (true) {
+                queue_claim(E, nf, rank, fit, tile);
+                if (fit >= 0) break;
+                int st = 0;
+                if (threadIdx.x == 0)
+                    st = (ld_acquire_u32(reinterpret_cast<const unsigned*>(E.running)) == 0u || (*ctl & CTL_ABORT)) ? 1 : 0;
+                stop = __shfl_sync(FULL, st, 0);
+                if (stop) break;
+                if (global_ns() - t0 > ROUND_WAIT_LIMIT_NS) {
+                    if (threadIdx.x == 0) atomicOr((int*)ctl, CTL_ABORT);
+                    stop = 1;
+                    break;
+                }
+                __nanosleep(back);
+                back = back < 512 ? back * 2 : 512;
+            }
+            if (threadIdx.x == 0) { sm.flag[0] = fit; sm.flag[1] = tile; sm.flag[2] = stop; }
+        }
+        __syncthreads();
+        const int fit = sm.flag[0], tile = sm.flag[1], stop = sm.flag[2];
+        __syncthreads();
+        const unsigned long long t1 = global_ns();
+        idle += t1 - t0;
+        if (stop) break;
+        // the item's state words, pass constants and descriptor (L2: other CTAs wrote them)
+        FitState* stp = E.state + fit;
+        if (threadIdx.x == 0) {
+            sm.flag[0] = __ldcg(&stp->run);
+            sm.flag[1] = __ldcg(&stp->phase);
+            sm.cov_stage = __ldcg(&stp->cov_stage);
+        }
+        if (PREC == PREC_MIXED) { if (threadIdx.x < PF) sm.pf[threadIdx.x] = __ldcg(stp->pf + threadIdx.x); }
+        else { if (threadIdx.x < PD) sm.pd[threadIdx.x] = __ldcg(stp->pd + threadIdx.x); }
+        if (fit != sm.desc_fit) {
+            const int* src = (const int*)(E.desc + fit);
+            int* dst = (int*)&sm.desc;
+            for (int k = threadIdx.x; k < (int)(sizeof(FitDesc) / 4); k += EVAL_THREADS) dst[k] = src[k];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) sm.desc_fit = fit;
+        MS::dispatch(sm.desc.model,
+                     [&](auto m) { process_item<decltype(m), PREC, MS>(sm, E, fit, tile, R, (long long)clock64()); });
+        __syncthreads();
+        busy += global_ns() - t1;
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(acct, busy);
+        atomicAdd(acct + 1, idle);
+        const int c = *ctl;
+        if (c & CTL_ABORT) atomicOr(E.out + 2, 1);
+        E.out[0] = *(volatile int*)E.running;   // 0 unless aborted
+        E.out[1] = 1;
+    }
+}
+
 // Persistent form of the iteration: pass constants at p0 (do_init), then
 // rounds of run_items separated by the grid barrier until no fit runs or the
 // round cap is reached.  One cooperative launch replaces a graph of
@@ -1098,6 +1224,12 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) fit_loop_kernel(const Engine*
     // time accounting of the loop (result header, 64-bit words 2..3):
     // per-CTA time in rounds' work and time waiting at the barrier
     unsigned long long* acct = reinterpret_cast<unsigned long long*>(E.out) + 2;
+    if (E.queue_mode) {
+        queue_loop<PREC, MS>(sm, E, Ed, R, first, acct);
+        if (first == 0)
+            for (int k = threadIdx.x; k <= SM_IDS; k += blockDim.x) E.sm_cnt[k] = 0;
+        return;
+    }
     // owner mode: the owner CTA of a fit also times its rounds (global timer)
     unsigned long long* otrace = (E.owner_mode && first < *E.nfits_dev) ? E.state[first].trace : nullptr;
     if (otrace && threadIdx.x == 0) trace_bump(otrace, TR_START_NS, global_ns() - t_launch);
