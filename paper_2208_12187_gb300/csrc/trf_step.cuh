@@ -146,31 +146,30 @@ __device__ inline bool inv32(int n, const double* Ah, float* Mi, float& sc, floa
     double dmax = gmax8((l < n) ? Ah[l * 8 + l] : 0.0);
     if (!(dmax > 0.0)) return false;
     sc = float(rcp64(dmax));
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        int e = l + 32 * u, i = e >> 3, j = e & 7;
-        Mi[e] = (i < n && j < n) ? float(Ah[e]) * sc : (i == j ? 1.0f : 0.0f);
-    }
-    __syncwarp();
+    // the 8x8 matrix in registers: lane l holds rows i0 = l/8 and i1 = 4 + l/8
+    // of column j = l%8; the pivot row and column come in by shuffles
+    const int j = l & 7, i0 = l >> 3, i1 = i0 + 4;
+    float a0 = (i0 < n && j < n) ? float(Ah[l]) * sc : (i0 == j ? 1.0f : 0.0f);
+    float a1 = (i1 < n && j < n) ? float(Ah[l + 32]) * sc : (i1 == j ? 1.0f : 0.0f);
+    float dg = fminf((i0 == j && j < n) ? a0 : INFINITY, (i1 == j && j < n) ? a1 : INFINITY);
+    for (int o = 16; o; o >>= 1) dg = fminf(dg, __shfl_xor_sync(FULL, dg, o));
+    min_diag = fminf(1.0f, dg);
     bool ok = true;
-    min_diag = 1.0f;
-    for (int k = 0; k < n; ++k) min_diag = fminf(min_diag, Mi[k * 9]);
     for (int k = 0; k < n; ++k) {
-        float piv = Mi[k * 9];
+        const float rowk = (k < 4) ? a0 : a1;                 // the register that holds row k
+        const int kb = (k & 3) << 3;
+        const float piv = __shfl_sync(FULL, rowk, kb + k);
+        const float akj = __shfl_sync(FULL, rowk, kb + j);
+        const float ai0 = __shfl_sync(FULL, a0, (l & ~7) + k);
+        const float ai1 = __shfl_sync(FULL, a1, (l & ~7) + k);
         ok = ok && piv > 0.0f;
-        float r = __frcp_rn(piv > 0.0f ? piv : 1.0f);
-        float nv[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            int e = l + 32 * u, i = e >> 3, j = e & 7;
-            float aik = Mi[i * 8 + k], akj = Mi[k * 8 + j], aij = Mi[e];
-            nv[u] = (i == k) ? ((j == k) ? r : akj * r) : ((j == k) ? -aik * r : fmaf(-aik * r, akj, aij));
-        }
-        __syncwarp();
-        Mi[l] = nv[0];
-        Mi[l + 32] = nv[1];
-        __syncwarp();
+        const float r = __frcp_rn(piv > 0.0f ? piv : 1.0f);
+        a0 = (i0 == k) ? ((j == k) ? r : akj * r) : ((j == k) ? -ai0 * r : fmaf(-ai0 * r, akj, a0));
+        a1 = (i1 == k) ? ((j == k) ? r : akj * r) : ((j == k) ? -ai1 * r : fmaf(-ai1 * r, akj, a1));
     }
+    Mi[l] = a0;
+    Mi[l + 32] = a1;
+    __syncwarp();
     return ok;
 }
 
