@@ -891,8 +891,8 @@ int gbfit_autotune(int model_id, int precision, int64_t m_max, int64_t points_pe
         for (int k = 10; k <= 18; ++k)
             if (((int64_t)1 << k) < mb) tiles.push_back(1 << k);
         if (mb <= ((int64_t)1 << 18)) tiles.push_back((int)((mb + EVAL_THREADS - 1) / EVAL_THREADS * EVAL_THREADS));
-        float best = 1e30f;
-        int bt = tiles.back(), bg = GROUP_TILES;
+        struct Cand { int tp, g; float ms; };
+        std::vector<Cand> cands;
         for (int tp : tiles) {
             int64_t ntl = (mb + tp - 1) / tp;
             std::vector<int> groups = ntl > 8 ? std::vector<int>{8, 32, 128} : std::vector<int>{GROUP_TILES};
@@ -921,9 +921,20 @@ int gbfit_autotune(int model_id, int precision, int64_t m_max, int64_t points_pe
                     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
                     if (e != cudaSuccess) return cleanup(fail(GBFIT_E_CUDA, "autotune timing: %s", cudaGetErrorString(e)));
                 }
-                if (ms < best) { best = ms; bt = tp; bg = g; }
+                cands.push_back({tp, g, ms});
             }
         }
+        // Among shapes within 3 % of the best throughput, the one with the
+        // most tiles per fit: in a batch of mixed sizes the evaluation chains
+        // of the largest fits set the launch time, and more tiles per fit
+        // shorten each of their passes (calibration timings of near-equal
+        // shapes differ by noise).
+        float best = 1e30f;
+        for (const Cand& q : cands) best = std::min(best, q.ms);
+        int bt = tiles.back(), bg = GROUP_TILES;
+        float bms = 1e30f;
+        for (const Cand& q : cands)
+            if (q.ms <= 1.03f * best && (q.tp < bt || (q.tp == bt && q.ms < bms))) { bt = q.tp; bg = q.g; bms = q.ms; }
         tab.tile_points[model_id][precision][b] = bt;
         tab.group_tiles[model_id][precision][b] = bg;
         if (first_b < 0) first_b = b;
