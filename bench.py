@@ -80,7 +80,7 @@ HBM_PEAK_GBS = 6785.9          # MEASURED_PEAKS.json: copy bandwidth of this poo
 # the headline workload, 5 passes) from the ncu capture summarised in
 # profiles/fit_loop_mixed_gauss2d_1024.md; None whenever the kernel has
 # changed since the capture.
-TRAFFIC_BYTES_PER_LAUNCH = 8.625e6
+TRAFFIC_BYTES_PER_LAUNCH = 8.624e6
 
 
 def workload_desc():
