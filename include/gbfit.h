@@ -245,9 +245,10 @@ int gbfit_tune_shape(int model_id, int precision, int64_t m, int* tile_points, i
  * means 2^25) for candidate shapes: tile_points 2^10 .. 2^18 (and one tile
  * per fit), group_tiles 8, 32, 128.  Every fit runs exactly 4 evaluations on
  * synthetic calibration data drawn on the device (FP32 for the mixed mode,
- * FP64 for the plain one), timed with CUDA events; the fastest shape of each
- * bucket is installed (buckets below 2^10 take bucket 10's, buckets above
- * m_max keep their entries).  out (optional) receives the resulting table.
+ * FP64 for the plain one), timed with CUDA events.  Each bucket gets, among
+ * the shapes within 3 % of its fastest, the one with the most tiles per fit
+ * (the shortest passes for the largest fits of a mixed batch); buckets below
+ * 2^10 take bucket 10's, buckets above m_max keep their entries.  out (optional) receives the resulting table.
  * Allocates and frees device memory for the calibration data; takes about
  * a second per bucket.  Errors: GBFIT_E_INVALID_ARG, GBFIT_E_OOM, GBFIT_E_CUDA.
  */
