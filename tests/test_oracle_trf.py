@@ -308,3 +308,35 @@ def test_infeasible_start_rejected():
     pr = synth.gauss1d(100, seed=1)
     with pytest.raises(ValueError):
         trf.curve_fit(pr.model, pr.coords(), pr.y, None, pr.p0, np.full(4, 10.0), np.full(4, 20.0))
+
+
+@pytest.mark.parametrize("absolute_sigma", [False, True])
+@pytest.mark.parametrize("name", ["gauss1d_sigma", "gauss2d_grid_bounded", "dexp_bounded"])
+def test_pcov_matches_scipy_curve_fit(name, absolute_sigma):
+    """pcov (R13: SciPy's documented curve_fit covariance, the pseudo-inverse of
+    J^T J at the solution scaled by 2f/(m-n) unless absolute_sigma) against
+    scipy.optimize.curve_fit run on the oracle's own model function, per-point
+    sigma, nonlinear models, with and without bounds (a library run)."""
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    if name == "gauss1d_sigma":
+        pr = synth.gauss1d(3000, seed=3)
+        sigma = np.random.default_rng(4).uniform(0.05, 0.2, pr.m)
+    elif name == "gauss2d_grid_bounded":
+        pr = synth.gauss2d_grid(48, seed=5, dtype=np.float64, truth=[980.0, 24.3, 23.1, 6.0, 4.0, 0.4, 20.0])
+        sigma = pr.sigma
+    else:
+        pr = synth.dexp(3000, seed=21, dtype=np.float64)
+        sigma = np.random.default_rng(6).uniform(0.02, 0.1, pr.m)
+    X = pr.coords()
+    f = lambda _, *p: models.value_and_jac(pr.model, X, np.array(p))[0]
+    jac = lambda _, *p: models.value_and_jac(pr.model, X, np.array(p))[1]
+    lb = -np.inf if pr.lb is None else pr.lb
+    ub = np.inf if pr.ub is None else pr.ub
+    popt, pcov = scipy_opt.curve_fit(f, np.arange(pr.m), pr.y, p0=pr.p0, sigma=sigma, absolute_sigma=absolute_sigma,
+                                     bounds=(lb, ub), method="trf", jac=jac, ftol=1e-14, xtol=1e-14, gtol=1e-14)
+    out = trf.curve_fit(pr.model, X, pr.y, sigma, pr.p0, pr.lb, pr.ub, absolute_sigma=absolute_sigma, **TOL)
+    # the two stop at the same optimum up to their tolerances: within 1e-3
+    # standard errors (the double exponential's valley is flat: ~1e-6 relative)
+    se = np.sqrt(np.diag(pcov))
+    assert np.max(np.abs(out["popt"] - popt) / se) <= 1e-3
+    np.testing.assert_allclose(out["pcov"], pcov, rtol=1e-4, atol=1e-12 * np.max(np.abs(pcov)))
