@@ -413,6 +413,52 @@ def layouts_and_fp64(args, pr, y, sg, flush, dev):
     return out
 
 
+def run_phases(args):
+    """Where one fit's launch spends its time: per-iteration cycle counters of
+    the loop kernel's phases (owner CTA / stepping CTA, clock64) and the
+    owner's global-timer figures, for the headline workload and three 1D
+    workloads; warm L2 (no flush between fits), profiling on."""
+    import torch
+    from paper_2208_12187_gb300 import build, gbfit, synth
+    build.build()
+    gbfit.load()
+    g2 = synth.gauss2d_grid(1024, seed=0, dtype=np.float32)
+    y2, s2 = torch.as_tensor(g2.y).cuda(), torch.as_tensor(g2.sigma).cuda()
+    work = [("rotated 2D Gaussian 1024x1024 grid + sigma, bounded", g2.m,
+             lambda: gbfit.curve_fit(g2.model, None, y2, g2.p0, sigma=s2, lb=g2.lb, ub=g2.ub, grid_wh=g2.grid_wh,
+                                     precision="mixed", **TOL))]
+    for m in (1_000_000, 10_000_000):
+        g1 = synth.gauss1d(m, seed=0)
+        x1, y1 = torch.as_tensor(g1.x).float().cuda(), torch.as_tensor(g1.y).float().cuda()
+        work.append((f"1D Gaussian, m={m:.0e}", m, lambda g1=g1, x1=x1, y1=y1: gbfit.curve_fit(
+            g1.model, x1, y1, g1.p0, precision="mixed", **TOL)))
+    d = synth.dexp(100_000, seed=21)
+    xd, yd = torch.as_tensor(d.x).float().cuda(), torch.as_tensor(d.y).float().cuda()
+    work.append(("double exponential, m=1e5, bounded", d.m, lambda: gbfit.curve_fit(
+        d.model, xd, yd, d.p0, lb=d.lb, ub=d.ub, precision="mixed", **TOL)))
+    for name, m, fit in work:
+        for _ in range(3):
+            fit()
+        torch.cuda.synchronize()
+        gbfit.set_profiling(True)
+        gbfit.stats_reset()
+        for _ in range(args.steps):
+            out = fit()
+        st = gbfit.stats()
+        gbfit.set_profiling(False)
+        pc, it, nfits = st["phase_cycles"], max(st["passes"], 1), args.steps
+        cycles = {k: round(v / it) for k, v in pc.items() if not k.startswith(("n_", "spare")) and not k.endswith("_ns")}
+        counts = {k: round(v / it, 3) for k, v in pc.items() if k.startswith("n_") or k in ("j32_sweeps", "refine_passes")}
+        for k in counts:
+            cycles.pop(k, None)
+        timers = {k: round(v / nfits / 1e3, 2) for k, v in pc.items() if k.endswith("_ns")}
+        print(json.dumps({"mode": "phases", "workload": name, "m": m, "precision": "mixed", "nfev": int(out["nfev"]),
+                          "l2": "warm (no flush between fits)",
+                          "launch_us": st["eval_ms"] / max(st["eval_launches"], 1) * 1e3,
+                          "cycles_per_iteration": cycles, "events_per_iteration": counts,
+                          "owner_global_timer_us_per_fit": timers}))
+
+
 def run_sweep(args):
     """1D Gaussian + offset size sweep (config-0 generator), mixed and plain FP64."""
     import torch
@@ -816,6 +862,8 @@ def main():
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--user", action="store_true", help="user-defined models (run-time compiled) vs built-in")
     ap.add_argument("--cov", action="store_true", help="full-covariance fits (sizes from --sizes)")
+    ap.add_argument("--phases", action="store_true",
+                    help="per-iteration phase cycles of the loop kernel (headline and 1D workloads, warm L2)")
     ap.add_argument("--compare", action="store_true",
                     help="headline workload: implicit grid vs explicit coordinates vs plain FP64, against the oracle")
     ap.add_argument("--serve-requests", type=int, default=20000)
@@ -842,6 +890,8 @@ def main():
         return run_cov(args)
     if args.compare:
         return run_compare(args)
+    if args.phases:
+        return run_phases(args)
     rank, local, world = dist_setup(args)
     if args.impl == "reference":
         res = run_reference(args, rank, world)
