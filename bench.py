@@ -447,11 +447,12 @@ def run_phases(args):
         st = gbfit.stats()
         gbfit.set_profiling(False)
         pc, it, nfits = st["phase_cycles"], max(st["passes"], 1), args.steps
-        cycles = {k: round(v / it) for k, v in pc.items() if not k.startswith(("n_", "spare")) and not k.endswith("_ns")}
+        timer_keys = ("start_ns", "round_ns", "owner_wait_ns", "barrier_ns")      # global timer, not cycles
+        cycles = {k: round(v / it) for k, v in pc.items() if not k.startswith(("n_", "spare")) and k not in timer_keys}
         counts = {k: round(v / it, 3) for k, v in pc.items() if k.startswith("n_") or k in ("j32_sweeps", "refine_passes")}
         for k in counts:
             cycles.pop(k, None)
-        timers = {k: round(v / nfits / 1e3, 2) for k, v in pc.items() if k.endswith("_ns")}
+        timers = {k[:-3]: round(pc[k] / nfits / 1e3, 2) for k in timer_keys}
         print(json.dumps({"mode": "phases", "workload": name, "m": m, "precision": "mixed", "nfev": int(out["nfev"]),
                           "l2": "warm (no flush between fits)",
                           "launch_us": st["eval_ms"] / max(st["eval_launches"], 1) * 1e3,
