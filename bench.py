@@ -497,7 +497,6 @@ def run_sweep(args):
             cyc = st["phase_cycles"]
             bpp = 8 if prec == "mixed" else 16
             busy_ms = st["loop_busy_ms"] / max(st["loop_ctas"], 1)        # average CTA, per fit
-            tile_share = cyc["tile"] / max(sum(v for k, v in cyc.items() if not k.startswith(("n_", "spare", "j32", "refine", "eig_", "comb_", "gn"))), 1)
             print(json.dumps({"mode": "sweep", "model": "gauss1d", "m": m, "precision": prec, "nfev": nf,
                               "fit_ms": ms / steps, "point_iters_per_s": pts / (ms / 1e3),
                               "bytes_per_point": 8 if prec == "mixed" else 16,
