@@ -10,7 +10,6 @@ are read in place, host arrays are copied to the device inside the call.
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 import threading
 from typing import Optional, Sequence
