@@ -372,25 +372,32 @@ int gbfit_server_destroy(gbfit_server* s);
 
 /*
  * gbfit_evaluate without any device or pinned-host allocation (the paper has
- * no counterpart; it exists for callers that may not allocate at call time:
- * code inside host callbacks or allocation-free stream captures, under an
- * allocator that owns all device memory, or in loops that cannot afford an
- * allocation's implicit synchronisation).  Same arguments and output as
- * gbfit_evaluate, with these differences:
+ * no counterpart).  It serves callers that may not allocate memory when they
+ * call: applications whose memory manager owns all device memory (a pool
+ * sized at start-up, where a cudaMalloc beside it fails or fragments it), and
+ * loops that cannot take the implicit device-wide synchronisation of
+ * cudaMalloc / cudaFree.  Same arguments and output as gbfit_evaluate, with
+ * these differences:
  *   - xdata, ydata and sigma must be device pointers (no staging copy);
  *   - the pass's scratch (tile and group partial sums, arrival counters, the
  *     one-fit job record) lives in a fixed file-scope device array of about
  *     1 MB that every GPU loading the library keeps until the process exits;
- *     at most 2048 reduction tiles fit, i.e. m <= 134,217,728 points at the
- *     largest default tile (65536 points); larger requests fail with
- *     GBFIT_E_INVALID_ARG and a message giving the limit;
+ *     at most 2048 reduction tiles fit: m <= 134,217,728 points with
+ *     tile_points = 0 (the default tile is made coarser, up to 65536 points,
+ *     where it would need more tiles), m <= 2048 * tile_points otherwise;
+ *     larger requests fail with GBFIT_E_INVALID_ARG, before any CUDA call,
+ *     with a message giving the limit;
  *   - the first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture;
- *   - every call reuses the same array (each call re-initialises what must
- *     start at zero); calls are serialised by a host lock and each returns
- *     only after its results are back, but work of two calls that overlapped
- *     on the GPU would race on the array.
+ *   - the call is synchronous: it enqueues an upload of the job record, two
+ *     kernels and the result copy on cuda_stream, then waits on that stream
+ *     (also on its error paths, once anything is enqueued) before it returns;
+ *   - every call reuses the same array, which keeps the last call's
+ *     contents (each call re-initialises what must start at zero); calls
+ *     whose work overlapped on the GPU would race on it, which the host lock
+ *     and the wait at the end of each call prevent for calls made through
+ *     this entry point.
  */
 int gbfit_evaluate_noalloc(int model_id,
                            const void* xdata, int64_t m, int x_layout, const int64_t* grid_wh,

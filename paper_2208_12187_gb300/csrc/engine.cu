@@ -997,15 +997,14 @@ int gbfit_tr_subproblem(int n, const double* B, const double* g, double Delta, d
 
 // ====================================================================== allocation-free evaluation
 // gbfit_evaluate_noalloc serves callers that may not allocate memory on the
-// device at call time: code running where cudaMalloc / cudaFree are not
-// allowed or not wanted (inside a host callback, during a stream capture
-// that must not contain allocations, under a custom allocator that owns
-// all device memory, or in a latency-critical loop where an allocation's
-// implicit synchronisation is unacceptable).  The fused reduction pass needs
-// scratch memory for its per-tile and per-group partial sums, its arrival
-// counters and its one-fit job record; here all of it lives in the
+// device when they call: applications whose memory manager owns all device
+// memory (a pool sized at start-up), and loops that cannot take the implicit
+// device-wide synchronisation of cudaMalloc / cudaFree.  The fused reduction
+// pass needs scratch memory for its per-tile and per-group partial sums, its
+// arrival counters and its one-fit job record; here all of it lives in the
 // file-scope device array below, of fixed size, which every GPU that loads
-// this library holds until the process exits.
+// this library holds until the process exits.  The call is synchronous: it
+// waits on the caller's stream for its result.
 namespace {
 constexpr int NOALLOC_MAX_TILES = 2048;                                   // reduction tiles per call
 constexpr int NOALLOC_MAX_GROUPS = (NOALLOC_MAX_TILES + GROUP_TILES - 1) / GROUP_TILES;   // default groups
@@ -1024,6 +1023,25 @@ struct NoAllocLayout {
     static constexpr size_t end = gp + ((size_t(NOALLOC_MAX_GROUPS) * KMAX * sizeof(double) + 255) / 256) * 256;
 };
 constexpr size_t NOALLOC_SCRATCH_BYTES = NoAllocLayout::end;             // about 0.9 MB
+
+// Largest m a call takes: at the default tile choice, NOALLOC_MAX_TILES tiles
+// of the largest tile; with the caller's tile_points, NOALLOC_MAX_TILES tiles
+// of that size.
+constexpr int64_t NOALLOC_MAX_M = int64_t(NOALLOC_MAX_TILES) * TILE_MAX;
+
+// Tile size of an allocation-free call: the caller's, else the default
+// choice for this grid, made coarser when that choice would need more tiles
+// than the array holds.  For m <= NOALLOC_MAX_M the result never needs more
+// than NOALLOC_MAX_TILES tiles, whatever the grid.
+int noalloc_tile(int64_t m, int tile_points, int grid) {
+    int tp = choose_tile(m, tile_points, grid);
+    if (tile_points == 0 && (m + tp - 1) / tp > NOALLOC_MAX_TILES) {
+        int64_t t = (m + NOALLOC_MAX_TILES - 1) / NOALLOC_MAX_TILES;
+        t = ((t + EVAL_THREADS - 1) / EVAL_THREADS) * EVAL_THREADS;
+        tp = (int)std::min<int64_t>(t, TILE_MAX);
+    }
+    return tp;
+}
 
 std::mutex g_noalloc_mu;
 char* g_noalloc_dev[64] = {};                                            // device address, per device
@@ -1056,24 +1074,47 @@ extern "C" int gbfit_evaluate_noalloc(int model_id, const void* xdata, int64_t m
     }
     for (int i = 0; i < n; ++i)
         if (!std::isfinite(p[i])) return fail(GBFIT_E_INVALID_ARG, "p[%d] is not finite", i);
+    // size limits first, from host arithmetic alone (no CUDA call yet)
+    if (tile_points > 0) {
+        const int tpu = choose_tile(m, tile_points, 0);
+        const int64_t nt = (m + tpu - 1) / tpu;
+        if (nt > NOALLOC_MAX_TILES)
+            return fail(GBFIT_E_INVALID_ARG,
+                        "m = %lld needs %lld reduction tiles of %d points; the allocation-free entry point holds at "
+                        "most %d tiles (m <= %lld points at this tile size)",
+                        (long long)m, (long long)nt, tpu, NOALLOC_MAX_TILES, (long long)NOALLOC_MAX_TILES * tpu);
+    } else if (m > NOALLOC_MAX_M) {
+        return fail(GBFIT_E_INVALID_ARG,
+                    "m = %lld exceeds the allocation-free entry point's limit: it holds at most %d tiles "
+                    "(m <= %lld points at the default tile size)",
+                    (long long)m, NOALLOC_MAX_TILES, (long long)NOALLOC_MAX_M);
+    }
     int nsm = 0, dev0 = 0;
     CUDA_TRY(cudaGetDevice(&dev0));
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev0));
     const int grid_na = nsm * std::max(1, eval_blocks_per_sm(precision));
-    const int tp = choose_tile(m, tile_points, grid_na);
+    const int tp = noalloc_tile(m, tile_points, grid_na);
     const int64_t ntiles = (m + tp - 1) / tp;
-    if (ntiles > NOALLOC_MAX_TILES)
-        return fail(GBFIT_E_INVALID_ARG,
-                    "m = %lld needs %lld reduction tiles of %d points; the allocation-free entry point holds at "
-                    "most %d tiles (m <= %lld points at the largest default tile)",
-                    (long long)m, (long long)ntiles, tp, NOALLOC_MAX_TILES, (long long)NOALLOC_MAX_TILES * TILE_MAX);
+    if (ntiles > NOALLOC_MAX_TILES)                 // unreachable after the checks above
+        return fail(GBFIT_E_INVALID_ARG, "m = %lld needs %lld tiles; at most %d fit", (long long)m,
+                    (long long)ntiles, NOALLOC_MAX_TILES);
     if (!is_device_ptr(ydata) || (xdata && x_layout != GBFIT_X_GRID && !is_device_ptr(xdata)) ||
         (sigma && !is_device_ptr(sigma)))
         return fail(GBFIT_E_INVALID_ARG, "the allocation-free entry point needs device-resident data arrays");
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(GBFIT_E_CUDA, "device ordinal %d out of range", dev);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    // From the first enqueue on, every return (error paths included) first
+    // waits for this call's work on the stream, so that none of it can still
+    // use the shared array once the lock is released (declared after the
+    // lock: destroyed, and so synchronised, before the lock is let go).
+    struct SyncOnExit {
+        cudaStream_t s;
+        bool armed;
+        ~SyncOnExit() { if (armed) cudaStreamSynchronize(s); }
+    } guard{s, false};
     if (!g_noalloc_dev[dev]) {
         // one-time set-up on this device (this device is current): the
         // device address of the scratch array
@@ -1110,7 +1151,7 @@ extern "C" int gbfit_evaluate_noalloc(int model_id, const void* xdata, int64_t m
     memcpy(g_noalloc_host + LY::eng, &E, sizeof E);
     gbfit_options o = defaults();
     o.precision = prec;
-    o.tile_points = tile_points;
+    o.tile_points = tp;
     o.max_nfev = 1;
     FitArgs a{model_id, n, x_layout, dtype, m, gw, xdata, nullptr, ydata, sigma, p, nullptr, nullptr};
     FitDesc d;
@@ -1130,7 +1171,7 @@ extern "C" int gbfit_evaluate_noalloc(int model_id, const void* xdata, int64_t m
     for (int i = 0; i < n; ++i) { st->x[i] = p[i]; st->xt[i] = p[i]; st->scale_inv[i] = 1.0; }
     WorkItem* items = (WorkItem*)(g_noalloc_host + LY::items);
     for (int t = 0; t < (int)ntiles; ++t) items[t] = WorkItem{0, t};
-    cudaStream_t s = (cudaStream_t)cuda_stream;
+    guard.armed = true;
     CUDA_TRY(cudaMemcpyAsync(base, g_noalloc_host, LY::res_hdr, cudaMemcpyHostToDevice, s));
     void* args[] = {&Ed};
     CUDA_TRY(cudaLaunchKernel(kernel_init_fits(prec), dim3(1), dim3(32), args, 0, s));
@@ -1139,6 +1180,7 @@ extern "C" int gbfit_evaluate_noalloc(int model_id, const void* xdata, int64_t m
     CUDA_TRY(cudaMemcpyAsync(g_noalloc_result, base + LY::res_hdr, sizeof g_noalloc_result,
                              cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    guard.armed = false;
     const FitResult* r = (const FitResult*)(g_noalloc_result + (LY::res - LY::res_hdr));
     if (r->fit_status == -2) return fail(GBFIT_E_INVALID_ARG, "sigma <= 0 or non-finite x/y/sigma in the data");
     const int K = n_tri(n) + n + 1;

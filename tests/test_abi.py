@@ -121,3 +121,29 @@ def test_covariance_size_limit_checked_on_the_host():
                                  None, None, None, a, a + 32, a + 160, ints.ctypes.data, ints.ctypes.data + 4, None)
     assert rc == gbfit.E_INVALID_ARG
     assert b"m <=" in lib.gbfit_last_error()
+
+
+@pytest.mark.parametrize("m,tile_points,refused", [
+    (120_000_000, 0, False),          # the default tile grows so that 2048 tiles hold it
+    (134_000_000, 0, False),
+    (134_217_728, 0, False),          # 2048 tiles of 65536 points exactly
+    (134_217_729, 0, True),
+    (2048 * 256, 256, False),
+    (2048 * 256 + 1, 256, True),
+    (2048 * 2048 + 1, 2000, True),    # tile_points rounds up to 2048
+])
+def test_noalloc_size_limit_checked_on_the_host(lib, m, tile_points, refused):
+    """The allocation-free entry point's tile limit (2048 tiles) is host
+    arithmetic done before any CUDA call: sizes within it are not refused for
+    size (the call then fails later on a CPU-only host, or on the fake data
+    pointers, which are never read), sizes beyond it are."""
+    out = np.zeros(4 + 10 + 1)
+    p = np.array([1.0, 0.0, 1.0, 0.0])
+    fake = ctypes.c_void_p(256)           # never dereferenced: every failing check comes first
+    rc = lib.gbfit_evaluate_noalloc(gbfit.MODEL_GAUSS1D, fake, ctypes.c_int64(m), gbfit.X_VEC, None, fake, None,
+                                    gbfit.F32, p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), gbfit.PREC_MIXED,
+                                    tile_points, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None)
+    msg = lib.gbfit_last_error()
+    assert rc != 0
+    size_refusal = rc == gbfit.E_INVALID_ARG and b"2048 tiles" in msg
+    assert size_refusal == refused, msg

@@ -1,21 +1,23 @@
 """The allocation-free evaluation entry point (gbfit_evaluate_noalloc).
 
-Some callers cannot allocate device memory when they call the library (host
-callbacks, allocation-free stream captures, allocators that own all device
-memory, loops that cannot take an allocation's implicit synchronisation).
+Some callers cannot allocate device memory when they call the library: an
+application whose memory manager owns all device memory, or a loop that
+cannot take the implicit device-wide synchronisation of cudaMalloc.
 gbfit_evaluate_noalloc runs the same fused reduction pass as gbfit_evaluate
 with its scratch in a fixed device array instead.  This checks, through the C
-ABI, that two calls in a row return the same sums as gbfit_evaluate (to the
-plain-FP64 reduction tolerance of the parity tests, 1e-12 of each entry's
-scale, and 2e-5 in mixed precision), and that a request beyond the array's
-capacity is refused.  The file name sorts last so that a run stopping at the
-first failure has already run every other test.
+ABI, that two calls in a row return the same sums as gbfit_evaluate and as the
+FP64 oracle's definition of the sums (the parity tests' tolerances: 1e-12 of
+each entry's scale in plain FP64, 2e-5 in mixed precision), at an explicit and
+at the default tile size, and that a request beyond the array's capacity is
+refused.  The file name sorts last so that a run stopping at the first failure
+has already run every other test.
 """
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import reduce as red
 from paper_2208_12187_gb300 import build, gbfit, synth
 
 pytestmark = pytest.mark.gpu
@@ -42,22 +44,39 @@ def _close(a, b, tol):
     assert abs(fa - fb) <= tol * abs(fb)
 
 
+def _close_oracle(out, pr, p, tol):
+    """Sums against the oracle's definition (Eqs. msqe, gradient, hessian) at
+    p, on the same data, scaled per entry as in the parity tests."""
+    Bp, gg, cost = out
+    f, g, B, _, _ = red.evaluate(pr.model, pr.coords(), pr.y, red.weights(pr.sigma, pr.m), p)
+    Bg = gbfit.unpack_upper(Bp, pr.n)
+    dscale = np.sqrt(np.outer(np.diag(B), np.diag(B)))
+    assert np.max(np.abs(Bg - B) / np.maximum(dscale, 1e-300)) <= tol
+    assert np.max(np.abs(gg - g) / np.maximum(np.sqrt(np.diag(B) * 2 * f), 1e-300)) <= tol
+    assert abs(cost - f) <= tol * f
+
+
+@pytest.mark.parametrize("tile_points", [2048, 0])
 @pytest.mark.parametrize("precision,dtype,tol", [("fp64", torch.float64, 1e-12), ("mixed", torch.float32, 2e-5)])
-def test_noalloc_matches_evaluate_twice(precision, dtype, tol):
+def test_noalloc_matches_evaluate_and_oracle_twice(precision, dtype, tol, tile_points):
     cases = [synth.gauss1d(3 * 2048 + 17, seed=1, with_sigma=True),
              synth.gauss2d_grid(97, seed=4, dtype=np.float64)]
     for pr in cases:
         x = None if pr.layout == synth.LAYOUT_GRID else _dev(pr.x, dtype)
         y, s = _dev(pr.y, dtype), _dev(pr.sigma, dtype)
-        kw = dict(sigma=s, grid_wh=pr.grid_wh, precision=precision, tile_points=2048)
+        kw = dict(sigma=s, grid_wh=pr.grid_wh, precision=precision, tile_points=tile_points)
         ref = gbfit.evaluate(pr.model, x, y, pr.p0, **kw)
         first = gbfit.evaluate_noalloc(pr.model, x, y, pr.p0, **kw)
         second = gbfit.evaluate_noalloc(pr.model, x, y, pr.p0, **kw)
         _close(first, ref, tol)
         _close(second, ref, tol)
+        _close_oracle(first, pr, pr.p0, tol)
+        _close_oracle(second, pr, pr.p0, tol)
         # a different parameter point through the same shared array
         p1 = pr.p0 * 1.01
-        _close(gbfit.evaluate_noalloc(pr.model, x, y, p1, **kw), gbfit.evaluate(pr.model, x, y, p1, **kw), tol)
+        out1 = gbfit.evaluate_noalloc(pr.model, x, y, p1, **kw)
+        _close(out1, gbfit.evaluate(pr.model, x, y, p1, **kw), tol)
+        _close_oracle(out1, pr, p1, tol)
 
 
 def test_noalloc_rejects_too_many_tiles():
