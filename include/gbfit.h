@@ -109,7 +109,19 @@ typedef struct gbfit_options {
     int loss;                  /* GBFIT_LOSS_* (default linear)                                  */
     int reserved[1];
     double f_scale;            /* robust loss scale C > 0; 0 reads as 1                          */
+    /* Precision guard of GBFIT_PREC_MIXED (linear loss, no full covariance):
+     * a fit continues with FP64 evaluation passes from its current point when
+     * the equilibrated condition number of its Gram exceeds guard_cond, or
+     * when it meets a tolerance while its estimated FP32 rounding floor in
+     * popt (relative, |dp| / max(|p|, 1)) exceeds guard_floor; max_nfev
+     * bounds all evaluations together.  <= 0: the defaults below; +inf: off
+     * (every pass FP32, the fastest and least accurate form). */
+    double guard_cond;
+    double guard_floor;
 } gbfit_options;
+
+#define GBFIT_GUARD_COND_DEFAULT 1.0e3
+#define GBFIT_GUARD_FLOOR_DEFAULT 1.0e-7
 
 /* Library version (GBFIT_VERSION). */
 int gbfit_version(void);
@@ -328,6 +340,8 @@ typedef struct gbfit_server_config {
     int precision;             /* GBFIT_PREC_*                                                 */
     int rounds_per_step;       /* iterations per step (default 4)                              */
     int reserved[4];
+    double guard_cond;         /* precision guard of mixed served fits, as in gbfit_options    */
+    double guard_floor;
 } gbfit_server_config;
 
 typedef struct gbfit_request {

@@ -260,12 +260,17 @@ int choose_tile(int64_t m, int user, int grid) {
 }
 
 // ---- tile table of batched and served fits (gbfit_tune_*)
+// Largest default / autotuned tile of mixed-precision fits: a fit that the
+// precision guard moves to FP64 passes keeps its tiles, and an FP64 pass over
+// a large FP32-sized tile holds one CTA for ~1 ms (FP64 issues at 1/64 of
+// FP32 on GB300), lengthening that fit's chain of evaluations.
+constexpr int MIXED_TILE_CAP = 4096;
 std::mutex g_tune_mu;
 gbfit_tune_table g_tune = [] {
     gbfit_tune_table t;
     for (int mo = 0; mo < GBFIT_NUM_MODELS; ++mo)
         for (int b = 0; b < GBFIT_TUNE_BUCKETS; ++b) {
-            t.tile_points[mo][PREC_MIXED][b] = 32768;
+            t.tile_points[mo][PREC_MIXED][b] = MIXED_TILE_CAP;
             t.tile_points[mo][PREC_FP64][b] = 4096;
             t.group_tiles[mo][PREC_MIXED][b] = t.group_tiles[mo][PREC_FP64][b] = GROUP_TILES;
         }
@@ -281,7 +286,7 @@ int tune_bucket(int64_t m) {
 // Shape of a batched / served fit: user values where given, else the table;
 // a fit smaller than its tile is one tile.
 void multi_shape(int model, int prec, int64_t m, int user_tile, int user_group, int* tile, int* group) {
-    int t = prec == PREC_MIXED ? 32768 : 4096, g = GROUP_TILES;   // user models: the table's defaults
+    int t = prec == PREC_MIXED ? MIXED_TILE_CAP : 4096, g = GROUP_TILES;   // user models: the table's defaults
     if (model >= 0 && model < GBFIT_NUM_MODELS) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         int b = tune_bucket(m);
@@ -326,6 +331,8 @@ int check_opts(const gbfit_options* o, int n) {
     if (o->group_tiles < 0 || o->group_tiles > 1024) return fail(GBFIT_E_INVALID_ARG, "group_tiles out of range");
     if (o->loss < GBFIT_LOSS_LINEAR || o->loss > GBFIT_LOSS_ARCTAN) return fail(GBFIT_E_INVALID_ARG, "unknown loss %d", o->loss);
     if (!(o->f_scale >= 0) || !std::isfinite(o->f_scale)) return fail(GBFIT_E_INVALID_ARG, "f_scale must be > 0");
+    if (std::isnan(o->guard_cond) || std::isnan(o->guard_floor))
+        return fail(GBFIT_E_INVALID_ARG, "guard_cond and guard_floor must not be NaN");
     return GBFIT_OK;
 }
 
@@ -335,8 +342,13 @@ gbfit_options defaults() {
     o.ftol = o.xtol = o.gtol = 1e-8;
     o.precision = GBFIT_PREC_MIXED;
     o.f_scale = 1.0;
+    o.guard_cond = GBFIT_GUARD_COND_DEFAULT;
+    o.guard_floor = GBFIT_GUARD_FLOOR_DEFAULT;
     return o;
 }
+
+// Guard thresholds as used: <= 0 reads as the default, +inf is off.
+double guard_value(double v, double dflt) { return v > 0.0 ? v : dflt; }
 
 // Run nfits fits whose descriptors (data pointers already on the device) are
 // in hd[]; writes per-fit results into hr[].  One host-to-device copy of the
@@ -500,6 +512,10 @@ int fill_desc(FitDesc& d, const FitArgs& a, const gbfit_options& o, bool bounded
     d.absolute_sigma = o.absolute_sigma;
     d.loss = o.loss;
     d.f_scale = o.f_scale > 0 ? o.f_scale : 1.0;
+    // precision guard: mixed path with the linear loss (make_cov turns it off)
+    const bool gfit = o.precision == GBFIT_PREC_MIXED && o.loss == GBFIT_LOSS_LINEAR;
+    d.guard_cond = gfit ? guard_value(o.guard_cond, GBFIT_GUARD_COND_DEFAULT) : INFINITY;
+    d.guard_floor = gfit ? guard_value(o.guard_floor, GBFIT_GUARD_FLOOR_DEFAULT) : INFINITY;
     return GBFIT_OK;
 }
 
@@ -550,6 +566,7 @@ int stage_cov(Ctx* c, FitDesc& d, const double* cov, int64_t m, int n, cudaStrea
     if (flag & 1) return fail(GBFIT_E_INVALID_ARG, "the covariance matrix is not positive definite");
     if (flag & 2) return fail(GBFIT_E_TIMEOUT, "a grid barrier of the covariance factorisation timed out");
     d.cov = 1;
+    d.guard_cond = d.guard_floor = INFINITY;       // the guard's FP64 passes do not cover covariance fits
     d.xinv = d.prec == PREC_MIXED ? (const void*)c->cov_xf : (const void*)c->cov_a;
     d.hbuf = c->cov_h;
     d.wkind = W_NONE;
@@ -886,11 +903,13 @@ int gbfit_autotune(int model_id, int precision, int64_t m_max, int64_t points_pe
         o.precision = precision;
         o.ftol = o.xtol = o.gtol = 0.0;
         o.max_nfev = 4;
-        // candidates: powers of two up to 2^18 below 2 m, and one tile per fit
+        // candidates: powers of two up to 2^18 below 2 m (mixed: up to
+        // MIXED_TILE_CAP), and one tile per fit when that is within the cap
+        const int64_t tmax = precision == GBFIT_PREC_MIXED ? MIXED_TILE_CAP : ((int64_t)1 << 18);
         std::vector<int> tiles;
         for (int k = 10; k <= 18; ++k)
-            if (((int64_t)1 << k) < mb) tiles.push_back(1 << k);
-        if (mb <= ((int64_t)1 << 18)) tiles.push_back((int)((mb + EVAL_THREADS - 1) / EVAL_THREADS * EVAL_THREADS));
+            if (((int64_t)1 << k) < mb && ((int64_t)1 << k) <= tmax) tiles.push_back(1 << k);
+        if (mb <= tmax) tiles.push_back((int)((mb + EVAL_THREADS - 1) / EVAL_THREADS * EVAL_THREADS));
         struct Cand { int tp, g; float ms; };
         std::vector<Cand> cands;
         for (int tp : tiles) {
@@ -1255,6 +1274,7 @@ size_t req_data_bytes(const gbfit_request& r) {
 
 struct gbfit_server {
     int device = 0, prec = PREC_MIXED, max_slots = 0, rounds = 4, grid = 0;
+    double guard_cond = GBFIT_GUARD_COND_DEFAULT, guard_floor = GBFIT_GUARD_FLOOR_DEFAULT;
     size_t budget = 0;
     char* pool = nullptr;
     RangeAlloc pool_alloc, tile_alloc, group_alloc;
@@ -1291,6 +1311,12 @@ int gbfit_server_create(const gbfit_server_config* cfg_in, gbfit_server** out) {
     s->max_slots = cfg.max_slots;
     s->rounds = cfg.rounds_per_step;
     s->budget = cfg.hbm_budget_bytes;
+    if (std::isnan(cfg.guard_cond) || std::isnan(cfg.guard_floor)) {
+        delete s;
+        return fail(GBFIT_E_INVALID_ARG, "guard_cond and guard_floor must not be NaN");
+    }
+    s->guard_cond = guard_value(cfg.guard_cond, GBFIT_GUARD_COND_DEFAULT);
+    s->guard_floor = guard_value(cfg.guard_floor, GBFIT_GUARD_FLOOR_DEFAULT);
     auto bail = [&](int rc) { gbfit_server_destroy(s); return rc; };
     cudaError_t e = cudaGetDevice(&s->device);
     if (e != cudaSuccess) return bail(fail(GBFIT_E_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)));
@@ -1456,6 +1482,8 @@ int gbfit_server_step(gbfit_server* s, int* n_active, int* n_queued) {
         o.max_nfev = r.max_nfev;
         o.loss = r.loss;
         o.f_scale = r.f_scale;
+        o.guard_cond = s->guard_cond;
+        o.guard_floor = s->guard_floor;
         FitArgs a{r.model_id, n, r.x_layout, r.dtype, r.m, r.grid_w, nullptr, nullptr, nullptr, nullptr,
                   r.p0, r.has_bounds ? r.lb : nullptr, r.has_bounds ? r.ub : nullptr};
         bool bounded = false;

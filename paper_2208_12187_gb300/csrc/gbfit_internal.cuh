@@ -17,7 +17,9 @@ enum Layout { X_VEC = 0, X_SOA2 = 1, X_GRID = 2 };
 enum DType { F32 = 0, F64 = 1 };
 enum WKind { W_NONE = 0, W_ARRAY = 1, W_SIGMA = 2 };
 enum RunState { RS_RUNNING = 0, RS_DONE = 1 };
-enum Phase { PH_INIT = 0, PH_TRIAL = 1 };
+// PH_REINIT: the fit's current point is evaluated again in FP64 (precision
+// guard of the mixed path); the fit then continues with FP64 passes.
+enum Phase { PH_INIT = 0, PH_TRIAL = 1, PH_REINIT = 2 };
 enum Loss { LOSS_LINEAR = 0, LOSS_SOFT_L1, LOSS_HUBER, LOSS_CAUCHY, LOSS_ARCTAN };
 // pass-constant slots holding the robust loss's C^2 and 1/C^2
 constexpr int PF_C2 = PF - 1, PF_IC2 = PF - 2, PD_C2 = PD - 1, PD_IC2 = PD - 2;
@@ -27,8 +29,9 @@ constexpr int PF_C2 = PF - 1, PF_IC2 = PF - 2, PD_C2 = PD - 1, PD_IC2 = PD - 2;
 //   [NT, NT+n)     J'^T r'
 //   NT+n           sum r'^2                        (= 2 f at the evaluated point)
 //   NT+n+1         sum dr (2 r + dr)   mixed only  (= 2 (f' - f), cancellation-free)
+//   NT+n+2         sum (w h)^2         mixed only  (scale of the FP32 rounding of r, for the guard)
 __host__ __device__ constexpr int n_tri(int n) { return n * (n + 1) / 2; }
-__host__ __device__ constexpr int n_acc(int n, int prec) { return n_tri(n) + n + (prec == PREC_MIXED ? 2 : 1); }
+__host__ __device__ constexpr int n_acc(int n, int prec) { return n_tri(n) + n + (prec == PREC_MIXED ? 3 : 1); }
 
 // Immutable description of one fit (uploaded once).
 struct FitDesc {
@@ -51,6 +54,12 @@ struct FitDesc {
     // full covariance (Appendix C): rounds alternate between evaluating the
     // points into hbuf and reducing rows of X hbuf, X = L^-1 (C = L L^T)
     int cov, pad3;
+    // precision guard of the mixed path (off: +inf): a fit whose equilibrated
+    // Gram condition number exceeds guard_cond continues with FP64 passes
+    // from its current point; a fit that meets a tolerance while its
+    // estimated FP32 rounding floor in popt exceeds guard_floor finishes with
+    // FP64 passes
+    double guard_cond, guard_floor;
     const void* xinv;      // X, [m][m] column-major (X_ij at xinv[j m + i]), lower triangle, zeros above;
                            // FP32 for the mixed path, FP64 for the plain path
     void* hbuf;            // [columns][m]: mixed h - y, dh, J_0..J_n-1 (FP32); plain h' - y, J (FP64)
@@ -69,6 +78,10 @@ struct alignas(16) FitState {
     // --- TRF state ---
     int fit_status, nfev, njev, factor_valid;
     int last_kind, alg2_iters, jacobi_sweeps, has_basis;
+    int eval64;            // mixed path: 1 once the fit evaluates in FP64 (precision guard)
+    int n_eval64;          // evaluations done in FP64 by a mixed fit
+    int guard_why;         // why the guard moved the fit to FP64 (GUARD_* in trf_step.cuh; 0: it did not)
+    int pad_g;
     double f, Delta, alpha;
     double x[NMAX], xt[NMAX], g[NMAX];
     double B[NTMAX];       // packed Gram at x
@@ -77,7 +90,7 @@ struct alignas(16) FitState {
     double lam[NMAX];
     double predicted, step_norm, s_norm, xtol_thr;
     double s_h[NMAX];      // scaled step of the pending trial
-    double pad1;           // (the prefix above is a whole number of 16-byte words)
+    double floor_x;        // mixed path: estimated FP32 rounding floor of popt at x (relative)
     // --- (the step reads everything above from a shared-memory copy) ---
     unsigned long long trace[32];  // SM cycles / ns / counts per phase (TracePhase), summed over iterations
 };

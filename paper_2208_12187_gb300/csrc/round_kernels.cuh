@@ -157,6 +157,8 @@ __device__ __forceinline__ void accum_point(const float* pfl, const double* pdl,
         } else {
             acc[NT + N] = fmaf(rn, rn, acc[NT + N]);
             acc[NT + N + 1] = fmaf(dr, fmaf(2.0f, r, dr), acc[NT + N + 1]);
+            const float wh = w * hb;
+            acc[NT + N + 2] = fmaf(wh, wh, acc[NT + N + 2]);
         }
     } else {
         double h, J[N];
@@ -203,10 +205,11 @@ __device__ __forceinline__ void accum_point2(const float* pfl, float2 X, float2 
                    isfinite(yv.y))) bad = 1;
     float2 hb, dh, J[N];
     M::eval_mixed2(pfl, X, Y, hb, dh, J);
-    float2 r = sub2(hb, yv), dr = dh;
+    float2 r = sub2(hb, yv), dr = dh, wh = hb;
     if (WK == W_SIGMA) {
         r = mul2(w, r);
         dr = mul2(w, dr);
+        wh = mul2(w, hb);
 #pragma unroll
         for (int a = 0; a < N; ++a) J[a] = mul2(w, J[a]);
     }
@@ -222,6 +225,7 @@ __device__ __forceinline__ void accum_point2(const float* pfl, float2 X, float2 
         for (int a = 0; a < N; ++a) acc[NT + a] = fma2(J[a], rn, acc[NT + a]);
         acc[NT + N] = fma2(rn, rn, acc[NT + N]);
         acc[NT + N + 1] = add2(dc, acc[NT + N + 1]);
+        acc[NT + N + 2] = fma2(wh, wh, acc[NT + N + 2]);
     } else {
         int idx = 0;
 #pragma unroll
@@ -235,6 +239,7 @@ __device__ __forceinline__ void accum_point2(const float* pfl, float2 X, float2 
         for (int a = 0; a < N; ++a) acc[NT + a] = fmaf(J[a].y, rn.y, fmaf(J[a].x, rn.x, acc[NT + a]));
         acc[NT + N] = fmaf(rn.y, rn.y, fmaf(rn.x, rn.x, acc[NT + N]));
         acc[NT + N + 1] += dc.x + dc.y;
+        acc[NT + N + 2] = fmaf(wh.y, wh.y, fmaf(wh.x, wh.x, acc[NT + N + 2]));
     }
 }
 
@@ -474,6 +479,7 @@ struct RoundSmem {
     double pd[PD];
     int flag[4];
     int cov_stage;                     // covariance fits: the item's round (FitState::cov_stage)
+    int eval64;                        // mixed path: the item's fit evaluates in FP64 (precision guard)
     int ctl;
     int desc_fit;                      // fit whose descriptor is in desc (-1: none yet)
     union {
@@ -699,6 +705,23 @@ __device__ void cov_rows(const FitDesc& d, int tile, void* scratch, typename Acc
     __syncthreads();                                // the scratch is free again
 }
 
+// FP64 evaluation of points [i0, i1) inside the mixed-precision kernel (a fit
+// that the precision guard moved to FP64 passes), block-reduced: thread
+// k < n_acc(N, FP64) returns slot k of the tile sum.  Not inlined, so that its
+// FP64 registers do not enter the streaming FP32 path's allocation.
+template <class M>
+__device__ __noinline__ double tile_sum_fp64(RoundSmem& sm, int64_t i0, int64_t i1, bool check, int* bad_out) {
+    constexpr int K = n_acc(M::N, PREC_FP64);
+    double acc[K];
+    int bad = 0;
+    RingState R{};                     // the FP64 point loops take no bulk-copy ring
+    eval_tile_dispatch<M, PREC_FP64>(sm, i0, i1, check, bad, acc, R);
+    *bad_out = bad;
+    double tsum = 0.0;
+    block_reduce<K, double>(acc, sm.redd, tsum);
+    return tsum;
+}
+
 template <class M, int PREC, class MS>
 __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, RingState& R, long long t_item) {
     using AT = typename AccT<PREC>::T;
@@ -713,47 +736,61 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
     long long t_tile = clock64();
     R.wait_cycles = 0;
     int bad = 0;
-    AT acc[K];
-    if (d.cov) {
-        if (sm.cov_stage == 0) {
-            // evaluation round: the item's points into hbuf; the last item of
-            // the fit to finish opens the row round (the grid barrier
-            // publishes hbuf and the stage)
-            cov_eval_dispatch<M, PREC>(d, sm.pf, sm.pd, i0, i1, check, bad);
-            if (check) {
-                int any = __syncthreads_or(bad);
-                if (any && threadIdx.x == 0) atomicOr(&stp->bad_data, 1);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int old = arrive_acq_rel(&E.fit_cnt[fit]);
-                if (old == d.n_tiles - 1) {
-                    E.fit_cnt[fit] = 0;
-                    stp->cov_stage = 1;
-                }
-            }
-            return;
+    // slots of this evaluation: FP64 ones for a mixed fit the guard moved to FP64
+    const bool e64 = PREC == PREC_MIXED && sm.eval64 && !d.cov;
+    const int Kuse = e64 ? n_acc(N, PREC_FP64) : K;
+    double tval = 0.0;
+    if (e64) {
+        if constexpr (PREC == PREC_MIXED) tval = tile_sum_fp64<M>(sm, i0, i1, check, &bad);
+        if (threadIdx.x == 0) sm.t_loop = clock64();
+        if (check) {
+            int any = __syncthreads_or(bad);
+            if (any && threadIdx.x == 0) atomicOr(&stp->bad_data, 1);
         }
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] = AT(0);
-        cov_rows<N, PREC>(d, tile, R.buf, acc);
-        check = false;
     } else {
-        eval_tile_dispatch<M, PREC>(sm, i0, i1, check, bad, acc, R);
+        AT acc[K];
+        if (d.cov) {
+            if (sm.cov_stage == 0) {
+                // evaluation round: the item's points into hbuf; the last item of
+                // the fit to finish opens the row round (the grid barrier
+                // publishes hbuf and the stage)
+                cov_eval_dispatch<M, PREC>(d, sm.pf, sm.pd, i0, i1, check, bad);
+                if (check) {
+                    int any = __syncthreads_or(bad);
+                    if (any && threadIdx.x == 0) atomicOr(&stp->bad_data, 1);
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int old = arrive_acq_rel(&E.fit_cnt[fit]);
+                    if (old == d.n_tiles - 1) {
+                        E.fit_cnt[fit] = 0;
+                        stp->cov_stage = 1;
+                    }
+                }
+                return;
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[k] = AT(0);
+            cov_rows<N, PREC>(d, tile, R.buf, acc);
+            check = false;
+        } else {
+            eval_tile_dispatch<M, PREC>(sm, i0, i1, check, bad, acc, R);
+        }
+        if (threadIdx.x == 0) sm.t_loop = clock64();
+        if (sm.ring_fail && threadIdx.x == 0) atomicOr(&stp->bad_data, 2);   // a bounded wait gave up
+        if (check) {
+            int any = __syncthreads_or(bad);
+            if (any && threadIdx.x == 0) atomicOr(&stp->bad_data, 1);
+        }
+        AT* red = (PREC == PREC_MIXED) ? (AT*)sm.redf : (AT*)sm.redd;
+        AT tsum;
+        block_reduce<K, AT>(acc, red, tsum);
+        tval = double(tsum);
     }
-    if (threadIdx.x == 0) sm.t_loop = clock64();
-    if (sm.ring_fail && threadIdx.x == 0) atomicOr(&stp->bad_data, 2);   // a bounded wait gave up
-    if (check) {
-        int any = __syncthreads_or(bad);
-        if (any && threadIdx.x == 0) atomicOr(&stp->bad_data, 1);
-    }
-    AT* red = (PREC == PREC_MIXED) ? (AT*)sm.redf : (AT*)sm.redd;
-    AT tsum;
-    block_reduce<K, AT>(acc, red, tsum);
     if (threadIdx.x == 0) sm.t_mark = clock64();
     int64_t row = d.tile_base + tile;
-    if (threadIdx.x < K) {
-        E.tile_part_d[row * KMAX + threadIdx.x] = double(tsum);
+    if (threadIdx.x < Kuse) {
+        E.tile_part_d[row * KMAX + threadIdx.x] = tval;
     }
     // ---- last arriver of the group combines the group
     __syncthreads();
@@ -769,14 +806,14 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
     if (d.n_groups == 1 && !E.owner_mode) prefetch_state(stp, sm.trf);      // this CTA runs the step
     if (threadIdx.x == 0) sm.t_fence = clock64();
     double* gout = E.group_part + (d.group_base + group) * KMAX;
-    combine_rows<double>(E.tile_part_d + (d.tile_base + g0) * KMAX, gsize, K, sm.comb, sm.trf.tot);
+    combine_rows<double>(E.tile_part_d + (d.tile_base + g0) * KMAX, gsize, Kuse, sm.comb, sm.trf.tot);
     if (threadIdx.x == 0) {
         E.group_cnt[d.group_base + group] = 0;
         sm.t_group = clock64();
     }
     if (E.owner_mode) {
         // the fit's owner CTA (owner_steps) combines the group sums and steps
-        if (threadIdx.x < K) gout[threadIdx.x] = sm.trf.tot[threadIdx.x];
+        if (threadIdx.x < Kuse) gout[threadIdx.x] = sm.trf.tot[threadIdx.x];
         __syncthreads();
         if (threadIdx.x == 0) {
             int old = arrive_acq_rel(&E.fit_cnt[fit]);
@@ -794,7 +831,7 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
     }
     if (d.n_groups > 1) {
         // second level: the last group of the fit combines the group sums
-        if (threadIdx.x < K) gout[threadIdx.x] = sm.trf.tot[threadIdx.x];
+        if (threadIdx.x < Kuse) gout[threadIdx.x] = sm.trf.tot[threadIdx.x];
         __syncthreads();
         if (threadIdx.x == 0) {
             int old = arrive_acq_rel(&E.fit_cnt[fit]);
@@ -803,7 +840,7 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
         __syncthreads();
         if (!sm.flag[3]) return;
         prefetch_state(stp, sm.trf);
-        combine_rows<double>(E.group_part + d.group_base * KMAX, d.n_groups, K, sm.comb, sm.trf.tot);
+        combine_rows<double>(E.group_part + d.group_base * KMAX, d.n_groups, Kuse, sm.comb, sm.trf.tot);
     }
     if (threadIdx.x == 0) {
         E.fit_cnt[fit] = 0;
@@ -881,9 +918,15 @@ __device__ __forceinline__ void run_items(RoundSmem& sm, const Engine& E, RingSt
             sm.flag[0] = __ldcg(&stp->run);
             sm.flag[1] = __ldcg(&stp->phase);
             sm.cov_stage = __ldcg(&stp->cov_stage);
+            sm.eval64 = __ldcg(&stp->eval64);
         }
-        if (PREC == PREC_MIXED) { if (threadIdx.x < PF) sm.pf[threadIdx.x] = __ldcg(stp->pf + threadIdx.x); }
-        else { if (threadIdx.x < PD) sm.pd[threadIdx.x] = __ldcg(stp->pd + threadIdx.x); }
+        // mixed path: both sets of pass constants (the FP64 ones serve a fit the guard moved to FP64)
+        if (PREC == PREC_MIXED) {
+            if (threadIdx.x < PF) sm.pf[threadIdx.x] = __ldcg(stp->pf + threadIdx.x);
+            else if (threadIdx.x < PF + PD) sm.pd[threadIdx.x - PF] = __ldcg(stp->pd + threadIdx.x - PF);
+        } else if (threadIdx.x < PD) {
+            sm.pd[threadIdx.x] = __ldcg(stp->pd + threadIdx.x);
+        }
         if (wi.fit != sm.desc_fit) {
             const int* src = (const int*)(E.desc + wi.fit);
             int* dst = (int*)&sm.desc;
@@ -993,8 +1036,9 @@ __device__ inline int grid_round_end(Engine* Ed, const Engine& E, int* ctl_smem,
 // the same SM every round, with its code in that SM's instruction caches.
 template <class M, int PREC, class MS>
 __device__ void owner_combine_step(RoundSmem& sm, const Engine& E, int fit) {
-    constexpr int K = n_acc(M::N, PREC);
     const FitDesc& d = sm.desc;
+    // slots of the evaluation just finished (the prefetched state says which precision ran it)
+    const int K = (PREC == PREC_MIXED && sm.trf.stc.eval64 && !d.cov) ? n_acc(M::N, PREC_FP64) : n_acc(M::N, PREC);
     FitState* stp = E.state + fit;
     long long t0 = clock64();
     combine_rows<double>(E.group_part + d.group_base * KMAX, d.n_groups, K, sm.comb, sm.trf.tot);
@@ -1138,9 +1182,15 @@ __device__ void queue_loop(RoundSmem& sm, const Engine& E, Engine* Ed, RingState
             sm.flag[0] = __ldcg(&stp->run);
             sm.flag[1] = __ldcg(&stp->phase);
             sm.cov_stage = __ldcg(&stp->cov_stage);
+            sm.eval64 = __ldcg(&stp->eval64);
         }
-        if (PREC == PREC_MIXED) { if (threadIdx.x < PF) sm.pf[threadIdx.x] = __ldcg(stp->pf + threadIdx.x); }
-        else { if (threadIdx.x < PD) sm.pd[threadIdx.x] = __ldcg(stp->pd + threadIdx.x); }
+        // mixed path: both sets of pass constants (the FP64 ones serve a fit the guard moved to FP64)
+        if (PREC == PREC_MIXED) {
+            if (threadIdx.x < PF) sm.pf[threadIdx.x] = __ldcg(stp->pf + threadIdx.x);
+            else if (threadIdx.x < PF + PD) sm.pd[threadIdx.x - PF] = __ldcg(stp->pd + threadIdx.x - PF);
+        } else if (threadIdx.x < PD) {
+            sm.pd[threadIdx.x] = __ldcg(stp->pd + threadIdx.x);
+        }
         if (fit != sm.desc_fit) {
             const int* src = (const int*)(E.desc + fit);
             int* dst = (int*)&sm.desc;

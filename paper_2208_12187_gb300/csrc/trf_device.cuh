@@ -54,7 +54,8 @@ struct FitResult {
 enum TracePhase { TR_TILE = 0, TR_COMBINE, TR_LOGIC, TR_EIGEN, TR_C_FENCE, TR_STEP, TR_PREP, TR_FINISH,
                   TR_C_GROUP, TR_C_FINAL, TR_E_WARM, TR_E_J32, TR_E_NS, TR_E_RR, TR_E_SWEEPS, TR_E_REFINES,
                   TR_GN, TR_N_GN, TR_N_EIG, TR_N_ALG2IT, TR_N_BOUNDED, TR_PRE_TILE, TR_TILE_LOOP, TR_RING_WAIT,
-                  TR_ROUND_NS, TR_OWNER_WAIT_NS, TR_BARRIER_NS, TR_START_NS, TR_RES28, TR_RES29, TR_RES30, TR_RES31 };
+                  TR_ROUND_NS, TR_OWNER_WAIT_NS, TR_BARRIER_NS, TR_START_NS, TR_N_EVAL64, TR_N_ESC, TR_N_FIN,
+                  TR_RES31 };
 
 // Shared-memory workspace of the warp that runs one fit's step.
 struct TrfSmem {
@@ -68,7 +69,7 @@ struct TrfSmem {
     double V0[64];    // scratch matrix (starting basis)
     double H[64];     // partial products of mm8
     double vec[16][8];
-    double sd[8];
+    double sd[12];
     double pds[PD];
     float Af[64];     // FP32 Jacobi work matrix
     float Af2[64];
@@ -78,7 +79,7 @@ struct TrfSmem {
     float csf[8];
     float pfs[PF];
     MixedParams mp;
-    int si[8];
+    int si[12];
     int pairs[8];
 };
 // named rows of TrfSmem::vec

@@ -345,11 +345,12 @@ __device__ __forceinline__ void cl_scaling(const FitDesc& d, const FitState* st,
 }
 
 // Pass constants for evaluating xt relative to x (warp 0).
+// e64: the fit evaluates in FP64 although the kernel is the mixed one (guard).
 template <int PREC, class MS>
-__device__ void prep_pass(const FitDesc& d, FitState* st, TrfSmem& S) {
+__device__ void prep_pass(const FitDesc& d, FitState* st, TrfSmem& S, bool e64 = false) {
     int l = threadIdx.x & 31;
     int n = d.n;
-    if (PREC == PREC_MIXED) {
+    if (PREC == PREC_MIXED && !e64) {
         if (l < n) {
             double x = S.vec[VX][l], xt = S.vec[VXT][l];
             float xf = float(x);
@@ -385,8 +386,95 @@ __device__ void prep_pass(const FitDesc& d, FitState* st, TrfSmem& S) {
 }
 
 // Scalar slots of TrfSmem::sd / si shared between the phases.
-enum { SD_F = 0, SD_DELTA, SD_ALPHA, SD_GNORM, SD_SC, SD_MIND, SD_PT2 };
-enum { SI_STATUS = 0, SI_NFEV, SI_NJEV, SI_FACTOR, SI_GN, SI_REJECTED, SI_PCOV, SI_SPEC };
+enum { SD_F = 0, SD_DELTA, SD_ALPHA, SD_GNORM, SD_SC, SD_MIND, SD_PT2, SD_COND, SD_FLOOR };
+enum { SI_STATUS = 0, SI_NFEV, SI_NJEV, SI_FACTOR, SI_GN, SI_REJECTED, SI_PCOV, SI_SPEC, SI_ESC };
+
+// ---- precision guard of the mixed path.  FP32 evaluation has two limits:
+// the Gram is formed from FP32 products and sums, so its error relative to
+// the equilibrated matrix is ~1e-7..1e-6 and the step's error grows with the
+// equilibrated condition number; and the residuals carry FP32 rounding
+// (absolute ~C_H eps32 |w h| per point), which moves the fixed point of the
+// iteration.  guard_estimates measures both at the point just evaluated:
+//   cond  = ||M||_inf ||M^-1||_inf, M = S B S with S = diag(B)^-1/2 (M^-1 from
+//           the FP32 Gauss-Jordan inverse; +inf when M is not positive
+//           definite in FP32);
+//   floor = max_j C_H eps32 rms(w h) sqrt((B^-1)_jj) / max(|p_j|, 1): the
+//           rounding-induced shift of popt (relative, as the tolerances are
+//           stated) — random per-point errors e_i move the fixed point by
+//           B^-1 J^T e, whose covariance is (C_H eps32 rms(w h))^2 B^-1.
+// C_H = 16 covers the exponential models' argument rounding (|q| eps32 per
+// exp for exponents up to ~10), measured against FP64 fixed points.
+constexpr double GUARD_C_H = 16.0;
+constexpr double EPS32 = 5.960464477539063e-08;
+
+// Termination scale of a mixed fit the guard moved to FP64 passes after FP32
+// iterations (a finish, or an escalation past the first evaluation): its
+// tolerances are tightened 100x, since its FP64 iterations start where FP32
+// rounding left it and the requested tolerances could stop it there.  A fit
+// escalated at its first evaluation runs the plain FP64 iteration from p0
+// with the requested tolerances.
+enum { GUARD_NONE = 0, GUARD_ESC_INIT = 1, GUARD_FINISH = 2, GUARD_ESC_MID = 3 };
+__device__ __forceinline__ double guard_tol_scale(const FitState* cst) {
+    return (cst->eval64 && (cst->guard_why == GUARD_FINISH || cst->guard_why == GUARD_ESC_MID)) ? 1e-2 : 1.0;
+}
+
+// One warp.  tot: packed sums of the evaluation at xt (mixed slots, with
+// sum (w h)^2 at NT+n+2); m: points.  Writes S.sd[SD_COND] and S.sd[SD_FLOOR].
+// Uses S.A and S.Af, which nothing else touches during the step's first phase.
+__device__ inline void guard_estimates(int n, int64_t m, const double* tot, const double* xt, TrfSmem& S) {
+    const int l = threadIdx.x & 31;
+    const int NT = n_tri(n);
+    // S_l = 1/sqrt(B_ll) in lane l (FP32 suffices for an estimate)
+    float sdl = 0.0f;
+    bool pos = true;
+    if (l < n) {
+        const double bll = tot[l * n - l * (l - 1) / 2];
+        pos = bll > 0.0 && isfinite(bll);
+        sdl = pos ? rsqrtf(float(bll)) : 0.0f;
+    }
+    pos = __all_sync(FULL, pos);
+    // M = S B S (unit diagonal; identity outside n)
+    for (int e = l; e < 64; e += 32) {
+        const int i = e >> 3, j = e & 7;
+        const float si = __shfl_sync(FULL, sdl, i), sj = __shfl_sync(FULL, sdl, j);
+        double v = (i == j) ? 1.0 : 0.0;
+        if (i < n && j < n && i != j) {
+            const int a = min(i, j), c = max(i, j);
+            v = double(float(tot[a * n - a * (a - 1) / 2 + (c - a)]) * si * sj);
+        }
+        S.A[e] = v;
+    }
+    __syncwarp();
+    float sc = 1.0f, mind = 0.0f;
+    const bool inv_ok = inv32(n, S.A, S.Af, sc, mind);          // every lane takes part
+    const bool ok = pos && __all_sync(FULL, inv_ok);
+    // ||M||_inf, ||M^-1||_inf (lane l < n: row l) and (M^-1)_ll
+    float rm = 0.0f, ri = 0.0f, dinv = 0.0f;
+    if (l < n) {
+        for (int j = 0; j < n; ++j) {
+            rm += fabsf(float(S.A[l * 8 + j]));
+            ri += fabsf(S.Af[l * 8 + j]);
+        }
+        dinv = S.Af[l * 8 + l];
+    }
+    for (int o = 16; o; o >>= 1) {
+        rm = fmaxf(rm, __shfl_xor_sync(FULL, rm, o));
+        ri = fmaxf(ri, __shfl_xor_sync(FULL, ri, o));
+    }
+    // rounding floor: (B^-1)_ll = S_l^2 (M^-1)_ll
+    const double rms = sqrt(fmax(tot[NT + n + 2], 0.0) / double(m));
+    double fl = 0.0;
+    if (l < n) {
+        const double binv = (dinv > 0.0f) ? double(dinv) * double(sdl) * double(sdl) : INFINITY;
+        fl = GUARD_C_H * EPS32 * rms * sqrt(binv) / fmax(fabs(xt[l]), 1.0);
+    }
+    fl = gmax8(fl);
+    if (l == 0) {
+        S.sd[SD_COND] = ok ? double(rm) * double(ri) : INFINITY;
+        S.sd[SD_FLOOR] = ok ? fl : INFINITY;
+    }
+    __syncwarp();
+}
 
 // Phase 2 on one warp: D, D g and the Coleman-Li diagonal C, then the scaled
 // model matrix Ah = D B D + diag(C), from the scaling (v, dv, sx), the
@@ -521,6 +609,10 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
     const int t = threadIdx.x, warp = t >> 5, l = t & 31;
     const int NT = n_tri(n);
     long long tclk = clock64();
+    // the evaluation just finished ran in FP64 although this is the mixed kernel (guard)
+    const bool e64 = PREC == PREC_MIXED && cst->eval64;
+    const bool guard_on = PREC == PREC_MIXED && !e64 && (d.guard_cond < INFINITY || d.guard_floor < INFINITY);
+    if (e64 && t == 0) trace_bump(st->trace, TR_N_EVAL64, 1);
 
     // ================= phase 1 (warp 0): accept / reject, termination tests
     if (warp == 0) {
@@ -530,23 +622,28 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             S.vec[VG][l] = cst->g[l];
         }
         const bool init = cst->phase == PH_INIT;
+        const bool reinit = cst->phase == PH_REINIT;
+        const bool mixed_pass = PREC == PREC_MIXED && !cst->eval64;
         const double f2n = S.tot[NT + n];
         int status = FS_RUNNING;
         double f = cst->f, Delta = cst->Delta, alpha = cst->alpha;
         int nfev = cst->nfev, njev = cst->njev, factor_valid = cst->factor_valid;
         bool take = false, rejected = false;
-        if (init) {
+        if (init || reinit) {
+            // init: the first evaluation (at p0); reinit: the current point
+            // evaluated again in FP64 (precision guard), radius and alpha kept
             take = true;
             f = 0.5 * f2n;
-            nfev = 1; njev = 1;
+            nfev += 1; njev += 1;                 // (both 0 before a fit's first evaluation)
+            if (reinit) factor_valid = 0;
             bool fin = (l >= NT + n + 1 || isfinite(S.tot[l])) && (l + 32 >= NT + n + 1 || isfinite(S.tot[l + 32]));
             fin = __all_sync(FULL, fin);
-            if (cst->bad_data) status = FS_INVALID_DATA;
+            if (init && cst->bad_data) status = FS_INVALID_DATA;
             else if (!fin) status = FS_NUMERICAL;
         } else {
             nfev += 1;
             double f_new = 0.5 * f2n;
-            double actual = (PREC == PREC_MIXED) ? -0.5 * S.tot[NT + n + 1] : f - f_new;
+            double actual = mixed_pass ? -0.5 * S.tot[NT + n + 1] : f - f_new;
             double pred = cst->predicted;
             double gamma = (isfinite(f_new) && isfinite(actual) && pred > 0.0) ? actual * rcp64(pred) : -INFINITY;
             bool accepted;
@@ -555,8 +652,12 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             else if (gamma >= 0.25 && gamma <= 0.75) { accepted = true; Dn = Delta; }
             else { accepted = false; Dn = 0.25 * cst->s_norm; }
             rejected = !accepted;
-            bool ftol_ok = accepted && actual < d.ftol * f;
-            bool xtol_ok = cst->step_norm < cst->xtol_thr;
+            // a fit the guard moved to FP64 after an FP32 stretch stops on
+            // tolerances 100x tighter, so that it ends at the FP64 fixed
+            // point rather than where FP32 left it (see guard_tol_scale)
+            const double tsc = guard_tol_scale(cst);
+            bool ftol_ok = accepted && actual < tsc * d.ftol * f;
+            bool xtol_ok = cst->step_norm < tsc * cst->xtol_thr;
             if (accepted) { take = true; f = f_new; njev += 1; factor_valid = 0; }
             Delta = Dn;
             if (ftol_ok && xtol_ok) status = FS_FTOL_XTOL;
@@ -590,7 +691,9 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             double v, dv, sx;
             cl_scaling(d, cst, S, n, v, dv, sx);
             if (l < 8) { S.vec[VV][l] = v; S.vec[VDV][l] = dv; S.vec[VSX][l] = sx; }   // for phase 2
-            if (init) {
+            // the radius of R6 at the first evaluation, and again when a fit that
+            // met a tolerance resumes in FP64 (its last radius was sized for FP32 steps)
+            if (init || (reinit && cst->guard_why == GUARD_FINISH)) {
                 double xl = (l < n) ? S.vec[VX][l] : 0.0;
                 double dd = (l < n) ? (d.bounded ? sqrt(v) : 1.0) * sx : 1.0;
                 double q = (l < n) ? xl * rcp64(dd) : 0.0;
@@ -601,7 +704,7 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             }
             double g = (l < n) ? S.vec[VG][l] : 0.0;
             gnorm = gmax8(fabs(v * g));
-            if (gnorm < d.gtol) status = FS_GTOL;
+            if (gnorm < guard_tol_scale(cst) * d.gtol) status = FS_GTOL;
             else if (nfev >= d.max_nfev) status = FS_MAX_NFEV;
         }
         if (l == 0) {
@@ -634,9 +737,56 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             if (l == 0) S.sd[SD_PT2] = pt2;
         }
         if (l == 0) S.si[SI_SPEC] = spec;
+    } else if (warp == 2) {
+        // precision guard estimates at the point just evaluated (used when it is taken)
+        if (guard_on) guard_estimates(n, d.m, S.tot, cst->xt, S);
     }
     __syncthreads();
     trace_add(st, TR_LOGIC, tclk);
+
+    // ================= precision guard (mixed path).  FP64 passes from here
+    // on when the Gram at the new point is too ill-conditioned for FP32 steps
+    // (cond > guard_cond), or when a tolerance is met while the estimated
+    // FP32 floor of popt at the current point exceeds guard_floor.  The next
+    // evaluation is then the current point, in FP64 (the full first
+    // evaluation again when the fit is still at p0).
+    if (guard_on) {
+        if (t == 0) {
+            const int stt = S.si[SI_STATUS];
+            const bool take = !S.si[SI_REJECTED];
+            const double floor_x = take ? S.sd[SD_FLOOR] : cst->floor_x;
+            int esc = 0;
+            if (stt == FS_RUNNING && take && d.guard_cond < INFINITY && !(S.sd[SD_COND] <= d.guard_cond))
+                esc = (cst->phase == PH_INIT) ? GUARD_ESC_INIT : GUARD_ESC_MID;
+            // a finish: the floor estimate is above guard_floor, or the FP32
+            // iteration stopped on xtol (steps that shrink below xtol by
+            // rejections can stall it short of its own fixed point)
+            else if (stt >= FS_GTOL && stt <= FS_FTOL_XTOL && d.guard_floor < INFINITY &&
+                     (!(floor_x <= d.guard_floor) || stt == FS_XTOL || stt == FS_FTOL_XTOL))
+                esc = GUARD_FINISH;
+            S.si[SI_ESC] = esc;
+            if (take) st->floor_x = S.sd[SD_FLOOR];
+        }
+        __syncthreads();
+        if (S.si[SI_ESC]) {
+            const bool was_init = cst->phase == PH_INIT;
+            if (t < n) { st->x[t] = S.vec[VX][t]; st->xt[t] = S.vec[VX][t]; st->g[t] = S.vec[VG][t]; }
+            if (t < 8) S.vec[VXT][t] = S.vec[VX][t];
+            if (t == 0) {
+                st->f = S.sd[SD_F]; st->Delta = S.sd[SD_DELTA]; st->alpha = S.sd[SD_ALPHA];
+                st->nfev = S.si[SI_NFEV]; st->njev = S.si[SI_NJEV]; st->factor_valid = 0;
+                st->eval64 = 1; st->guard_why = S.si[SI_ESC];
+                st->phase = was_init ? PH_INIT : PH_REINIT;
+                st->cov_stage = 0;
+                trace_bump(st->trace, S.si[SI_ESC] == GUARD_FINISH ? TR_N_FIN : TR_N_ESC, 1);
+                S.si[SI_STATUS] = FS_RUNNING;     // the fit goes on (queue mode re-arms its tiles)
+            }
+            __syncthreads();
+            if (warp == 0) prep_pass<PREC, MS>(d, st, S, true);
+            trace_add(st, TR_PREP, tclk);
+            return;
+        }
+    }
 
     const int status = S.si[SI_STATUS];
     if (status != FS_RUNNING) {
@@ -842,7 +992,7 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
         __syncwarp();
     }
     trace_add(st, TR_STEP, tclk);
-    if (warp == 0) prep_pass<PREC, MS>(d, st, S);
+    if (warp == 0) prep_pass<PREC, MS>(d, st, S, e64);
     trace_add(st, TR_PREP, tclk);
 }
 

@@ -48,7 +48,8 @@ class Options(ctypes.Structure):
                 ("max_nfev", ctypes.c_int), ("x_scale_jac", ctypes.c_int),
                 ("x_scale", ctypes.POINTER(ctypes.c_double)), ("absolute_sigma", ctypes.c_int),
                 ("precision", ctypes.c_int), ("tile_points", ctypes.c_int), ("group_tiles", ctypes.c_int),
-                ("loss", ctypes.c_int), ("reserved", ctypes.c_int * 1), ("f_scale", ctypes.c_double)]
+                ("loss", ctypes.c_int), ("reserved", ctypes.c_int * 1), ("f_scale", ctypes.c_double),
+                ("guard_cond", ctypes.c_double), ("guard_floor", ctypes.c_double)]
 
 LOSSES = {"linear": 0, "soft_l1": 1, "huber": 2, "cauchy": 3, "arctan": 4}
 
@@ -70,12 +71,14 @@ class Stats(ctypes.Structure):
 PHASES = ["tile", "combine", "logic", "eigen", "comb_fence", "step", "prep", "finish", "comb_group", "comb_final",
           "eig_warm", "eig_j32", "eig_ns", "eig_rr", "j32_sweeps", "refine_passes", "gn_path", "n_gn", "n_eig",
           "n_alg2_iters", "n_bounded_nonfull", "pre_tile", "tile_loop", "ring_wait",
-          "round_ns", "owner_wait_ns", "barrier_ns", "start_ns", "spare28", "spare29", "spare30", "spare31"]
+          "round_ns", "owner_wait_ns", "barrier_ns", "start_ns", "n_eval64", "n_guard_escalated",
+          "n_guard_finished", "spare31"]
 
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("precision", ctypes.c_int),
-                ("rounds_per_step", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("rounds_per_step", ctypes.c_int), ("reserved", ctypes.c_int * 4),
+                ("guard_cond", ctypes.c_double), ("guard_floor", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
@@ -241,7 +244,7 @@ def _stream_ptr(stream):
 
 
 def _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles=0,
-             loss="linear", f_scale=1.0):
+             loss="linear", f_scale=1.0, guard_cond=0.0, guard_floor=0.0):
     load()
     o = Options.from_buffer_copy(_DEFAULT_OPT)
     o.ftol, o.xtol, o.gtol = ftol, xtol, gtol
@@ -264,6 +267,8 @@ def _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, 
     o.group_tiles = int(group_tiles)
     o.loss = LOSSES[loss] if isinstance(loss, str) else int(loss)
     o.f_scale = float(f_scale)
+    o.guard_cond = float(guard_cond)        # 0: library default; inf: off
+    o.guard_floor = float(guard_floor)
     return o, keep
 
 
@@ -297,19 +302,20 @@ def _scratch() -> _Scratch:
 
 
 def _cached_options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles,
-                    loss, f_scale):
+                    loss, f_scale, guard_cond=0.0, guard_floor=0.0):
     """(address of an Options, keepalive); options without an x_scale vector are cached."""
     if isinstance(x_scale, (int, float)) and x_scale == 1.0:
-        key = (ftol, xtol, gtol, max_nfev, absolute_sigma, precision, tile_points, group_tiles, loss, f_scale)
+        key = (ftol, xtol, gtol, max_nfev, absolute_sigma, precision, tile_points, group_tiles, loss, f_scale,
+               guard_cond, guard_floor)
         o = _OPT_CACHE.get(key)
         if o is None:
             o, _ = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points,
-                            group_tiles, loss, f_scale)
+                            group_tiles, loss, f_scale, guard_cond, guard_floor)
             if len(_OPT_CACHE) < 256:
                 _OPT_CACHE[key] = o
         return ctypes.addressof(o), o
     o, keep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles,
-                       loss, f_scale)
+                       loss, f_scale, guard_cond, guard_floor)
     return ctypes.addressof(o), (o, keep)
 
 
@@ -353,12 +359,13 @@ def model_log() -> str:
 def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None, ub=None,
               grid_wh=None, ftol=1e-8, xtol=1e-8, gtol=1e-8, max_nfev=None, x_scale=1.0,
               absolute_sigma=False, precision="mixed", tile_points=0, group_tiles=0, loss="linear",
-              f_scale=1.0, stream=None) -> dict:
+              f_scale=1.0, stream=None, guard_cond=0.0, guard_floor=0.0) -> dict:
     """Fit `model` by the GPU trust-region-reflective method (gbfit_curve_fit).
 
     xdata: [m] (1D models), [2, m] (2D explicit coordinates) or None with
     grid_wh=(W, H) for the implicit pixel grid.  Returns dict(popt, pcov, cost,
-    nfev, status).
+    nfev, status).  guard_cond / guard_floor: the mixed path's precision guard
+    (0: library defaults, inf: off; see gbfit_options).
     """
     lib = _LIB or load()
     n = N_PARAMS[model]
@@ -389,7 +396,7 @@ def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None
         v[_Scratch.UB:_Scratch.UB + n] = ub
         ubp = base + 8 * _Scratch.UB
     optp, okeep = _cached_options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points,
-                                  group_tiles, loss, f_scale)
+                                  group_tiles, loss, f_scale, guard_cond, guard_floor)
     a = base + 8 * _Scratch.OUT                    # popt | pcov | cost
     ip = base + 8 * _Scratch.INTS                  # nfev | status
     call = lib.gbfit_curve_fit
@@ -408,7 +415,7 @@ def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None
 def curve_fit_batch(model: int, offsets, xdata, ydata, p0, sigma=None, lb=None, ub=None,
                     ftol=1e-8, xtol=1e-8, gtol=1e-8, max_nfev=None, x_scale=1.0,
                     absolute_sigma=False, precision="mixed", tile_points=0, group_tiles=0, loss="linear",
-                    f_scale=1.0, stream=None) -> dict:
+                    f_scale=1.0, stream=None, guard_cond=0.0, guard_floor=0.0) -> dict:
     """Many independent fits over concatenated data (gbfit_curve_fit_batch).
     tile_points / group_tiles 0: each fit's shape from the tile table."""
     lib = load()
@@ -423,7 +430,7 @@ def curve_fit_batch(model: int, offsets, xdata, ydata, p0, sigma=None, lb=None, 
     lba = None if lb is None else np.ascontiguousarray(np.broadcast_to(np.asarray(lb, np.float64), (nf, n)))
     uba = None if ub is None else np.ascontiguousarray(np.broadcast_to(np.asarray(ub, np.float64), (nf, n)))
     opt, okeep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles,
-                          loss, f_scale)
+                          loss, f_scale, guard_cond, guard_floor)
     popt = np.zeros((nf, n))
     pcov = np.zeros((nf, n, n))
     cost = np.zeros(nf)
@@ -576,9 +583,11 @@ class Server:
     time, call step() to retire finished fits, admit queued ones and run
     shared iterations, poll() for results."""
 
-    def __init__(self, hbm_budget_bytes=1 << 30, max_slots=4096, precision="mixed", rounds_per_step=4):
+    def __init__(self, hbm_budget_bytes=1 << 30, max_slots=4096, precision="mixed", rounds_per_step=4,
+                 guard_cond=0.0, guard_floor=0.0):
         lib = load()
         cfg = ServerConfig()
+        cfg.guard_cond, cfg.guard_floor = float(guard_cond), float(guard_floor)
         cfg.hbm_budget_bytes = int(hbm_budget_bytes)
         cfg.max_slots = int(max_slots)
         cfg.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision] if isinstance(precision, str) else int(precision)

@@ -147,3 +147,12 @@ def test_noalloc_size_limit_checked_on_the_host(lib, m, tile_points, refused):
     assert rc != 0
     size_refusal = rc == gbfit.E_INVALID_ARG and b"2048 tiles" in msg
     assert size_refusal == refused, msg
+
+
+def test_guard_options_checked_on_the_host(lib):
+    """NaN precision-guard thresholds are refused before any device work."""
+    for kw in (dict(guard_cond=float("nan")), dict(guard_floor=float("nan"))):
+        with pytest.raises(gbfit.GbfitError) as e:
+            gbfit.curve_fit(gbfit.MODEL_GAUSS1D, np.zeros(10), np.zeros(10), [1.0, 0.0, 1.0, 0.0], **kw)
+        assert e.value.code == gbfit.E_INVALID_ARG
+        assert "guard" in str(e.value)

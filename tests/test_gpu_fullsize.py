@@ -16,19 +16,21 @@ data for the plain path, the same data rounded to FP32 for the mixed one):
     1e-8, mixed within 1e-6 relative (|dp| / max(|p|, 1)).
 
 4,096 ragged double exponentials (m log-uniform in [200, 2e5]) in one
-batched mixed launch with the autotuned tile shapes (the batch benchmark's
-launch): every fit terminates by a tolerance; on the first 16 fits, whole
-FP64 oracle fits: median popt error <= 1e-6 with (a1, t1) <-> (a2, t2)
-canonicalised, at least 60 % of them within 1e-6 (the rest stop at other
-points of a flat valley of the double exponential: their costs agree within
-2e-3), and four fits re-run alone on views of the same device buffers give
-bitwise the batch's results.
+batched mixed launch (precision guard on, its default) with the autotuned
+tile shapes (the batch benchmark's launch): every fit terminates by a
+tolerance or at max_nfev; four fits re-run alone on views of the same device
+buffers give bitwise the batch's results; on the first 24 fits, whole FP64
+oracle fits and the per-fit criterion of oracle_checks: popt within 1e-6
+where the oracle's popt is determined to that level, otherwise (standard
+error above 10 %, rounding-sensitive or tolerance-limited oracle result) an
+oracle cost at the GPU's popt no higher than the oracle's own by 1e-9.
 """
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle_checks  # noqa: E402  (tests/ is on sys.path)
 from oracle import reduce as red, trf
 from paper_2208_12187_gb300 import build, gbfit, synth
 
@@ -92,6 +94,13 @@ def test_sweep_full_size_sums_and_optimum(sweep_problem, precision):
 
 
 def test_batch_full_size_sample_against_oracle():
+    """The 4,096-fit double-exponential batch in its benchmarked launch
+    (autotuned shapes, mixed precision with its precision guard): every fit
+    ends on a tolerance or on max_nfev, fits re-run alone on views of the same
+    buffers are bitwise equal, and on a sample of 24 fits every fit meets the
+    oracle criterion of oracle_checks (popt within 1e-6 where the oracle's
+    popt is determined to that level, else a cost no higher than the
+    oracle's)."""
     bt = synth.dexp_batch(4096, seed=7, dtype=np.float32)
     saved = gbfit.tune_get()
     try:
@@ -99,7 +108,9 @@ def test_batch_full_size_sample_against_oracle():
         x = torch.as_tensor(bt.x).cuda()
         y = torch.as_tensor(bt.y).cuda()
         out = gbfit.curve_fit_batch(bt.model, bt.offsets, x, y, bt.p0, lb=bt.lb, ub=bt.ub, precision="mixed", **TOL)
-        assert np.all(np.isin(out["status"], (1, 2, 3, 4)))
+        st = out["status"]
+        assert np.all(np.isin(st, (0, 1, 2, 3, 4)))
+        assert np.all(out["nfev"][st == 0] >= 500)               # status 0 only at max_nfev (100 n)
         # alone, on views of the same buffers (same alignment), with the shape the batch gave the fit
         for k in (0, 5, 1000, 4095):
             a, b = int(bt.offsets[k]), int(bt.offsets[k + 1])
@@ -110,13 +121,7 @@ def test_batch_full_size_sample_against_oracle():
             assert out["cost"][k] == alone["cost"] and out["nfev"][k] == alone["nfev"]
     finally:
         gbfit.tune_set(saved)
-    canon = lambda p: np.asarray(p)[[2, 3, 0, 1, 4]] if p[1] > p[3] else np.asarray(p)
-    errs, cost_rel = [], []
-    for k in range(16):
-        ref = trf.curve_fit_problem(bt.fit(k).astype(np.float64), **TOL)
-        errs.append(relerr(canon(out["popt"][k]), canon(ref["popt"])))
-        cost_rel.append(abs(out["cost"][k] - ref["cost"]) / ref["cost"])
-    errs = np.array(errs)
-    assert np.median(errs) <= 1e-6
-    assert np.mean(errs <= 1e-6) >= 0.6
-    assert max(cost_rel) <= 2e-3
+    for k in range(24):
+        pr = bt.fit(k).astype(np.float64)
+        ref = trf.curve_fit_problem(pr, **TOL)
+        oracle_checks.check_mixed(pr, out["popt"][k], ref, TOL)

@@ -16,6 +16,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle_checks
 from oracle import reduce as red, trf
 from paper_2208_12187_gb300 import build, gbfit, synth
 
@@ -247,18 +248,18 @@ def test_mixed_fit_matches_oracle(name, make, _):
 
 def test_mixed_degenerate_dexp_identifiable_part():
     """t1 ~ t2: only a1 + a2 and the curve are determined; the split is not.
-    Mixed and oracle agree on the fitted curve, not on a1, a2.  In the flat
-    valley the xtol / ftol tests stop each side wherever its steps become
-    small, while the cost still creeps down, so the two stopping costs agree
-    only to ~1e-5 relative; the mixed one must not be the worse one beyond
-    1e-6."""
+    The precision guard moves this fit to FP64 passes (its Gram's equilibrated
+    condition number is far above 1e3), so the mixed fit stops where the
+    FP64 iteration does: cost within 1e-6 of the oracle's and not above it
+    beyond 1e-9 (the oracle's FP64 cost at both points), and the same fitted
+    curve."""
     pr = synth.dexp(20_000, seed=5, dtype=np.float64)
     assert abs(pr.truth[1] / pr.truth[3] - 1) < 0.1          # a near-degenerate draw
     pr32 = pr.astype(np.float32)
     ref = trf.curve_fit_problem(pr32, **TOL)
     out = gpu_fit(pr, "mixed", dtype=torch.float32, **TOL)
-    assert out["cost"] == pytest.approx(ref["cost"], rel=1e-5)
-    assert out["cost"] <= ref["cost"] * (1 + 1e-6)
+    assert out["cost"] == pytest.approx(ref["cost"], rel=1e-6)
+    assert oracle_checks.oracle_cost(pr32, out["popt"]) <= ref["cost"] * (1 + 1e-9)
     from oracle import models
     X = pr.coords()
     hg = models.value_and_jac(pr.model, X, out["popt"])[0]
@@ -302,15 +303,17 @@ def test_batch_matches_alone_and_oracle():
 
 
 def test_batch_mixed_matches_oracle():
+    """Every fit of a mixed batch against the oracle, per fit (oracle_checks:
+    popt within 1e-6 where the oracle's popt is determined to that level,
+    else no higher cost than the oracle's)."""
     bt = synth.dexp_batch(32, seed=12, m_lo=500, m_hi=50_000, dtype=np.float32)
     out = gbfit.curve_fit_batch(bt.model, bt.offsets, dev(bt.x, torch.float32), dev(bt.y, torch.float32), bt.p0,
                                 lb=bt.lb, ub=bt.ub, precision="mixed", **TOL)
-    errs = []
-    for k in range(bt.nfits):
-        ref = trf.curve_fit_problem(bt.fit(k), **TOL)
-        errs.append(relerr(out["popt"][k], ref["popt"]))
-    assert np.median(errs) <= 1e-6
     assert np.all(out["status"] >= 0)
+    for k in range(bt.nfits):
+        pr = bt.fit(k).astype(np.float64)
+        ref = trf.curve_fit_problem(pr, **TOL)
+        oracle_checks.check_mixed(pr, out["popt"][k], ref, TOL)
 
 
 def test_autotune_installs_valid_shapes_and_fits_still_match():
@@ -327,8 +330,9 @@ def test_autotune_installs_valid_shapes_and_fits_still_match():
         bt = synth.dexp_batch(16, seed=13, m_lo=1000, m_hi=30_000, dtype=np.float32)
         out = gbfit.curve_fit_batch(bt.model, bt.offsets, dev(bt.x, torch.float32), dev(bt.y, torch.float32), bt.p0,
                                     lb=bt.lb, ub=bt.ub, precision="mixed", **TOL)
-        errs = [relerr(out["popt"][k], trf.curve_fit_problem(bt.fit(k), **TOL)["popt"]) for k in range(bt.nfits)]
-        assert np.median(errs) <= 1e-6
+        for k in range(bt.nfits):
+            pr = bt.fit(k).astype(np.float64)
+            oracle_checks.check_mixed(pr, out["popt"][k], trf.curve_fit_problem(pr, **TOL), TOL)
     finally:
         gbfit.tune_set(saved)
     assert np.array_equal(gbfit.tune_get()["tile_points"], saved["tile_points"])

@@ -5,13 +5,19 @@ small pool (forcing queueing) and few slots; more requests arrive while
 others are running.  Each result must equal, bit for bit, the same fit run
 alone through gbfit_curve_fit with the same reduction shape (a served fit's
 shape depends only on its own m, through the tile table),
-and match the FP64 oracle (plain: 1e-8, mixed: 1e-6 relative on popt).
+and match the FP64 oracle: plain 1e-8 relative on popt; mixed by the per-fit
+criterion of oracle_checks (popt within 1e-6 where the oracle's popt is
+determined to that level, else no higher cost than the oracle's).  The mixed
+stream includes near-degenerate double exponentials (t2 within 30 % of t1),
+whose Gram is ill-conditioned enough for the precision guard to move them to
+FP64 passes while they share launches with FP32 fits.
 """
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle_checks
 from oracle import trf
 from paper_2208_12187_gb300 import build, gbfit, synth
 
@@ -27,7 +33,7 @@ def lib():
     return gbfit.load()
 
 
-def _requests(dtype):
+def _requests(dtype, degenerate=False):
     rng = np.random.default_rng(5)
     reqs = []
     for k in range(18):
@@ -35,6 +41,9 @@ def _requests(dtype):
         m = int(np.exp(rng.uniform(np.log(2e3), np.log(2e5))))
         if kind == 0:
             pr = synth.gauss1d(m, seed=k, with_sigma=bool(k % 2), dtype=dtype)
+        elif kind == 1 and degenerate and k % 2 == 0:
+            t1 = 1.0 + 0.2 * k
+            pr = synth.dexp(m, seed=k, truth=[4.0, t1, 6.0, t1 * (1.15 + 0.01 * k), 0.5], dtype=dtype)
         elif kind == 1:
             pr = synth.dexp(m, seed=k, truth=[4.0, 0.5 + 0.1 * k, 6.0, 5.0 + k, 0.5], dtype=dtype)
         else:
@@ -46,7 +55,7 @@ def _requests(dtype):
 
 @pytest.mark.parametrize("precision,dtype,rel", [("mixed", np.float32, 1e-6), ("fp64", np.float64, 1e-8)])
 def test_served_equals_alone_and_oracle(precision, dtype, rel):
-    reqs = _requests(dtype)
+    reqs = _requests(dtype, degenerate=precision == "mixed")
     srv = gbfit.Server(hbm_budget_bytes=8 << 20, max_slots=5, precision=precision, rounds_per_step=3)
     tickets = {}
 
@@ -84,8 +93,11 @@ def test_served_equals_alone_and_oracle(precision, dtype, rel):
         np.testing.assert_array_equal(r["popt"], alone["popt"])
         assert r["nfev"] == alone["nfev"]
         ref = trf.curve_fit_problem(pr, **TOL)
-        err = np.max(np.abs(r["popt"] - ref["popt"]) / np.maximum(np.abs(ref["popt"]), 1.0))
-        assert err <= rel, (k, err)
+        if precision == "mixed":
+            oracle_checks.check_mixed(pr.astype(np.float64), r["popt"], ref, TOL, rel=rel)
+        else:
+            err = np.max(np.abs(r["popt"] - ref["popt"]) / np.maximum(np.abs(ref["popt"]), 1.0))
+            assert err <= rel, (k, err)
 
 
 def test_budget_refusal():
