@@ -91,6 +91,8 @@ struct alignas(16) FitState {
     double predicted, step_norm, s_norm, xtol_thr;
     double s_h[NMAX];      // scaled step of the pending trial
     double floor_x;        // mixed path: estimated FP32 rounding floor of popt at x (relative)
+    double serel_x;        // mixed path: largest standard error relative to its parameter at x
+    double pad_s;          // (the prefix above is a whole number of 16-byte words)
     // --- (the step reads everything above from a shared-memory copy) ---
     unsigned long long trace[32];  // SM cycles / ns / counts per phase (TracePhase), summed over iterations
 };

@@ -386,7 +386,7 @@ __device__ void prep_pass(const FitDesc& d, FitState* st, TrfSmem& S, bool e64 =
 }
 
 // Scalar slots of TrfSmem::sd / si shared between the phases.
-enum { SD_F = 0, SD_DELTA, SD_ALPHA, SD_GNORM, SD_SC, SD_MIND, SD_PT2, SD_COND, SD_FLOOR };
+enum { SD_F = 0, SD_DELTA, SD_ALPHA, SD_GNORM, SD_SC, SD_MIND, SD_PT2, SD_COND, SD_FLOOR, SD_SEREL };
 enum { SI_STATUS = 0, SI_NFEV, SI_NJEV, SI_FACTOR, SI_GN, SI_REJECTED, SI_PCOV, SI_SPEC, SI_ESC };
 
 // ---- precision guard of the mixed path.  FP32 evaluation has two limits:
@@ -402,9 +402,15 @@ enum { SI_STATUS = 0, SI_NFEV, SI_NJEV, SI_FACTOR, SI_GN, SI_REJECTED, SI_PCOV, 
 //           rounding-induced shift of popt (relative, as the tolerances are
 //           stated) — random per-point errors e_i move the fixed point by
 //           B^-1 J^T e, whose covariance is (C_H eps32 rms(w h))^2 B^-1.
+//   serel = max_j se_j / |p_j| with se_j^2 = 2f/(m-n) (B^-1)_jj: a fit whose
+//           parameters are this poorly determined has a flat cost valley in
+//           which an FP32 iteration stops measurably above the FP64 minimum
+//           (cost excess 1e-9..1e-8 relative at serel ~0.1), so it too
+//           finishes in FP64 beyond GUARD_SE_REL.
 // C_H = 16 covers the exponential models' argument rounding (|q| eps32 per
 // exp for exponents up to ~10), measured against FP64 fixed points.
 constexpr double GUARD_C_H = 16.0;
+constexpr double GUARD_SE_REL = 0.05;
 constexpr double EPS32 = 5.960464477539063e-08;
 
 // Termination scale of a mixed fit the guard moved to FP64 passes after FP32
@@ -461,17 +467,21 @@ __device__ inline void guard_estimates(int n, int64_t m, const double* tot, cons
         rm = fmaxf(rm, __shfl_xor_sync(FULL, rm, o));
         ri = fmaxf(ri, __shfl_xor_sync(FULL, ri, o));
     }
-    // rounding floor: (B^-1)_ll = S_l^2 (M^-1)_ll
+    // rounding floor and relative standard errors: (B^-1)_ll = S_l^2 (M^-1)_ll
     const double rms = sqrt(fmax(tot[NT + n + 2], 0.0) / double(m));
-    double fl = 0.0;
+    const double s2 = (m > n) ? tot[NT + n] / double(m - n) : INFINITY;     // 2f / (m - n)
+    double fl = 0.0, se = 0.0;
     if (l < n) {
         const double binv = (dinv > 0.0f) ? double(dinv) * double(sdl) * double(sdl) : INFINITY;
         fl = GUARD_C_H * EPS32 * rms * sqrt(binv) / fmax(fabs(xt[l]), 1.0);
+        se = sqrt(s2 * binv) / fabs(xt[l]);
     }
     fl = gmax8(fl);
+    se = gmax8(se);
     if (l == 0) {
         S.sd[SD_COND] = ok ? double(rm) * double(ri) : INFINITY;
         S.sd[SD_FLOOR] = ok ? fl : INFINITY;
+        S.sd[SD_SEREL] = ok ? se : INFINITY;
     }
     __syncwarp();
 }
@@ -755,17 +765,20 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             const int stt = S.si[SI_STATUS];
             const bool take = !S.si[SI_REJECTED];
             const double floor_x = take ? S.sd[SD_FLOOR] : cst->floor_x;
+            const double serel_x = take ? S.sd[SD_SEREL] : cst->serel_x;
             int esc = 0;
             if (stt == FS_RUNNING && take && d.guard_cond < INFINITY && !(S.sd[SD_COND] <= d.guard_cond))
                 esc = (cst->phase == PH_INIT) ? GUARD_ESC_INIT : GUARD_ESC_MID;
-            // a finish: the floor estimate is above guard_floor, or the FP32
+            // a finish: the floor estimate is above guard_floor, a parameter's
+            // standard error is above GUARD_SE_REL of it, or the FP32
             // iteration stopped on xtol (steps that shrink below xtol by
             // rejections can stall it short of its own fixed point)
             else if (stt >= FS_GTOL && stt <= FS_FTOL_XTOL && d.guard_floor < INFINITY &&
-                     (!(floor_x <= d.guard_floor) || stt == FS_XTOL || stt == FS_FTOL_XTOL))
+                     (!(floor_x <= d.guard_floor) || !(serel_x <= GUARD_SE_REL) || stt == FS_XTOL ||
+                      stt == FS_FTOL_XTOL))
                 esc = GUARD_FINISH;
             S.si[SI_ESC] = esc;
-            if (take) st->floor_x = S.sd[SD_FLOOR];
+            if (take) { st->floor_x = S.sd[SD_FLOOR]; st->serel_x = S.sd[SD_SEREL]; }
         }
         __syncthreads();
         if (S.si[SI_ESC]) {
