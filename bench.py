@@ -15,9 +15,14 @@ A step is one whole fit (gbfit_curve_fit) from p0 to termination.
   e2e        = the same metric through the C ABI with pinned HOST buffers: the
                host->device copy of y and sigma and the result read-back are
                inside the timed region (host wall clock around the call).
-  roofline   = the evaluation-pass kernel (eval_round_kernel<mixed>), timed per
-               launch with CUDA events in the library's profiling mode, against
-               the FP32 issue peak (the pass is bound by FP32 arithmetic, not HBM).
+  roofline   = the persistent loop kernel (fit_loop_kernel<mixed>; one launch =
+               one whole fit: every evaluation pass and trust-region step),
+               timed per launch with CUDA events in the library's profiling
+               mode, against the FP32 issue peak (the pass is bound by FP32
+               arithmetic, not HBM).
+  kernel_roofline = the fused evaluation pass alone (one gbfit_evaluate launch)
+               for the 1D Gaussian at 1e6 / 1e7 / 5e7 points and the headline
+               2D Gaussian, against the HBM copy peak and the FP32 peak.
   cpu_baseline = the FP64 oracle (test infrastructure) on the same workload,
                on rank 0 only.
 --impl reference times that oracle as the reference arm.
@@ -56,9 +61,10 @@ TOL = dict(ftol=1e-10, xtol=1e-10, gtol=1e-10)
 # and the Gram / gradient / cost accumulation.
 # Count of the current formulation (FFMA = 2, FADD / FMUL = 1, exp / rcp
 # on the MUFU not counted): model value, difference form and Jacobian row 86,
-# weights, residuals and the Gram / gradient / cost accumulation 87.
+# weights, residuals and the Gram / gradient / cost / actual-reduction /
+# (w h)^2 accumulation 90.
 BYTES_PER_POINT = 8
-FLOPS_PER_POINT = 173
+FLOPS_PER_POINT = 176
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 L2_FLUSH_BYTES = 256 << 20
@@ -74,12 +80,90 @@ class L2Flush:
 
     def zero_(self):
         self.w.zero_()
-HBM_PEAK_GBS = 6785.9          # MEASURED_PEAKS.json: copy bandwidth of the GB300s
 # DRAM bytes (read + write) per launch of the loop kernel (one whole fit of
 # the headline workload, 5 passes) from the ncu capture summarised in
 # profiles/fit_loop_mixed_gauss2d_1024.md; None whenever the kernel has
 # changed since the capture.
-TRAFFIC_BYTES_PER_LAUNCH = 8.624e6
+TRAFFIC_BYTES_PER_LAUNCH = None
+
+
+def measured_peaks():
+    """HBM copy bandwidth (GB/s) from MEASURED_PEAKS.json (driver-written),
+    else the profiling recipe's fallback; and which one it is."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (no MEASURED_PEAKS.json)"
+
+
+# Algorithmic work per point of one fused evaluation pass (model value,
+# cancellation-free difference, Jacobian row, residual, Gram / gradient /
+# cost / actual-reduction / (w h)^2 sums; FMA = 2 FLOP, MUFU not counted):
+# 1D Gaussian + offset on x, y FP32 (no sigma): 35 model + 38 accumulation;
+# rotated 2D Gaussian on the grid with sigma: 86 model + 90 accumulation.
+PASS_WORK = {"gauss1d_xy": (8, 73), "gauss2d_grid_sigma": (8, 176)}
+# Plain FP64 pass (1D Gaussian on x, y FP64): 16 bytes per point; FP64
+# instructions per point counted by ncu (profiles/eval_fp64_gauss1d_5e7.md).
+FP64_PEAK_GFMA = 590.0        # FP64 FMA rate measured on this pool's GB300 (probe kernel, 1/62 of FP32)
+
+
+def kernel_roofline(dev, flush):
+    """The fused Jacobian-reduction pass alone: one gbfit_evaluate launch (one
+    evaluation pass over m points, its combine and an evaluation-only step),
+    CUDA events around the launch (library profiling mode), L2 flushed before
+    each launch; against the HBM copy peak and the FP32 issue peak."""
+    import torch
+    from paper_2208_12187_gb300 import gbfit, synth
+    hbm, hbm_src = measured_peaks()
+    out = []
+
+    def timed(call, reps=5):
+        call()
+        gbfit.set_profiling(True)
+        gbfit.stats_reset()
+        for _ in range(reps):
+            flush.zero_()
+            call()
+        st = gbfit.stats()
+        gbfit.set_profiling(False)
+        return st["eval_ms"] / max(st["eval_launches"], 1)
+
+    def record(name, m, ms, bpp, fpp, extra):
+        t = ms / 1e3
+        gbs = m * bpp / t / 1e9
+        tfs = m * fpp / t / 1e12
+        t_roof = max(m * bpp / (hbm * 1e9), m * fpp / (FP32_PEAK_TFLOPS * 1e12))
+        out.append({"workload": name, "m": m, "precision": "mixed", "us_per_launch": ms * 1e3,
+                    "bytes_per_point": bpp, "flops_per_point": fpp, "achieved_gbs": gbs, "frac_hbm": gbs / hbm,
+                    "achieved_tflops": tfs, "frac_fp32": tfs / FP32_PEAK_TFLOPS, "frac_roofline": t_roof / t,
+                    **extra})
+
+    for m in (1_000_000, 10_000_000, 50_000_000):
+        pr = synth.gauss1d(m, seed=0, dtype=np.float32)
+        x = torch.as_tensor(pr.x).to(dev)
+        y = torch.as_tensor(pr.y).to(dev)
+        ms = timed(lambda: gbfit.evaluate(pr.model, x, y, pr.p0, precision="mixed"))
+        bpp, fpp = PASS_WORK["gauss1d_xy"]
+        record("1D Gaussian + offset, x and y FP32", m, ms, bpp, fpp, {})
+        if m == 50_000_000:
+            x64, y64 = x.double(), y.double()
+            ms64 = timed(lambda: gbfit.evaluate(pr.model, x64, y64, pr.p0, precision="fp64"), reps=3)
+            out.append({"workload": "1D Gaussian + offset, x and y FP64, plain FP64 path", "m": m,
+                        "precision": "fp64", "us_per_launch": ms64 * 1e3, "bytes_per_point": 16,
+                        "achieved_gbs": m * 16 / (ms64 / 1e3) / 1e9, "frac_hbm": m * 16 / (ms64 / 1e3) / 1e9 / hbm,
+                        "points_per_s": m / (ms64 / 1e3)})
+            del x64, y64
+        del x, y
+    pr = make_problem(0)
+    y = torch.as_tensor(pr.y).to(dev)
+    sg = torch.as_tensor(pr.sigma).to(dev)
+    ms = timed(lambda: gbfit.evaluate(pr.model, None, y, pr.p0, sigma=sg, grid_wh=(W, H), precision="mixed"))
+    bpp, fpp = PASS_WORK["gauss2d_grid_sigma"]
+    record("rotated 2D Gaussian, 1024 x 1024 grid, y and sigma FP32", M, ms, bpp, fpp, {})
+    return {"records": out, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src, "fp32_peak_tflops": FP32_PEAK_TFLOPS,
+            "timing": "CUDA events around each gbfit_evaluate launch (profiling mode), L2 flushed before each"}
 
 
 def workload_desc():
@@ -320,6 +404,8 @@ def run_ours(args, rank, local, world):
     if args.traffic is not None:
         roof["traffic"] = args.traffic
 
+    kroof = kernel_roofline(dev, flush) if rank == 0 else None
+
     # ---- e2e: pinned host buffers through the C ABI, copies inside the timed region
     yh = torch.empty(M, dtype=torch.float32, pin_memory=True)
     sh = torch.empty(M, dtype=torch.float32, pin_memory=True)
@@ -347,6 +433,7 @@ def run_ours(args, rank, local, world):
         "config": {"workload": workload_desc(), "m": M, "precision": "mixed", "nfev_per_fit": nfevs[0],
                    "l2": "flushed between steps (256 MiB write, untimed)", "parallelism": f"{world} independent fits"},
         "roofline": roof,
+        "kernel_roofline": kroof,
         "e2e": {"value": e2e_pts / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * M, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
@@ -500,9 +587,9 @@ def run_sweep(args):
                               "fit_ms": ms / steps, "point_iters_per_s": pts / (ms / 1e3),
                               "bytes_per_point": 8 if prec == "mixed" else 16,
                               "hbm_gbs_equiv": pts * bpp / (ms / 1e3) / 1e9,
-                              "hbm_frac_of_fit_time": pts * bpp / (ms / 1e3) / 1e9 / HBM_PEAK_GBS,
+                              "hbm_frac_of_fit_time": pts * bpp / (ms / 1e3) / 1e9 / measured_peaks()[0],
                               "pass_gbs": m * nf * bpp / (busy_ms / 1e3) / 1e9,
-                              "pass_hbm_frac": m * nf * bpp / (busy_ms / 1e3) / 1e9 / HBM_PEAK_GBS,
+                              "pass_hbm_frac": m * nf * bpp / (busy_ms / 1e3) / 1e9 / measured_peaks()[0],
                               "own_tile_cycles_per_iter": cyc["tile"] / it,
                               "step_cycles_per_iter": (cyc["logic"] + cyc["eigen"] + cyc["gn_path"] + cyc["step"] + cyc["prep"] + cyc["finish"]) / it,
                               "combine_cycles_per_iter": cyc["combine"] / it}))

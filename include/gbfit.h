@@ -50,6 +50,7 @@ extern "C" {
 #define GBFIT_E_CUDA            -5  /* a CUDA runtime call failed (message has the CUDA error) */
 #define GBFIT_E_TIMEOUT         -6  /* a bounded device wait gave up */
 #define GBFIT_E_UNSUPPORTED     -7  /* valid request this build does not implement */
+#define GBFIT_E_CANCELLED       -8  /* serving: the request was cancelled (gbfit_server_cancel) */
 
 /* ---- fit_status (per fit; mirrors the termination tests) ---- */
 #define GBFIT_FIT_NUMERICAL     -1  /* non-finite cost or Jacobian at p0 */
@@ -118,10 +119,23 @@ typedef struct gbfit_options {
      * (every pass FP32, the fastest and least accurate form). */
     double guard_cond;
     double guard_floor;
+    /* Limit, in seconds, of the loop kernel's grid-wide waits (round barrier,
+     * owner wait, idle wait of queue mode); past it the launch aborts and the
+     * call returns GBFIT_E_TIMEOUT with the context still usable.  <= 0: the
+     * default, 10 s.  Small values exist for testing that path: a launch
+     * whose waits are shorter than one trust-region step times out. */
+    double wait_limit_s;
 } gbfit_options;
 
 #define GBFIT_GUARD_COND_DEFAULT 1.0e3
 #define GBFIT_GUARD_FLOOR_DEFAULT 1.0e-7
+
+/* Test entry point: y[i] = 1/x[i] by the trust-region step's FP64 reciprocal
+ * (Newton-Raphson from the FP32 reciprocal; the paper has no counterpart: it
+ * is an implementation detail of the on-device step, exposed so that its
+ * accuracy can be checked against 1.0 / x).  x, y: device arrays of n
+ * doubles; synchronous on cuda_stream. */
+int gbfit_check_rcp64(const double* x, double* y, int64_t n, void* cuda_stream);
 
 /* Library version (GBFIT_VERSION). */
 int gbfit_version(void);
@@ -377,6 +391,38 @@ int gbfit_server_submit(gbfit_server* s, const gbfit_request* req, uint64_t* tic
 /* Retire, admit, and run one step of iterations; *n_active = fits resident
  * after the step, *n_queued = requests still waiting.  Blocking. */
 int gbfit_server_step(gbfit_server* s, int* n_active, int* n_queued);
+
+/* Cancel a queued or resident request (between steps: nothing of it is in
+ * flight then).  Its record is queued for gbfit_server_poll with status
+ * GBFIT_E_CANCELLED, popt and cost of its current point (p0 if it never ran)
+ * and the evaluations done; its pool, tile and slot are freed.
+ * GBFIT_E_INVALID_ARG if the ticket is neither queued nor resident. */
+int gbfit_server_cancel(gbfit_server* s, uint64_t ticket);
+
+/* Snapshot of a resident fit's state between steps (checkpoint): the
+ * trust-region state kept on the device (point, trial point, radius, Gram,
+ * scaling, eigen cache, pass constants, counters).  Resubmitting the same
+ * request with it (gbfit_server_submit_resume) continues the fit where it
+ * was; with the same data and tile table the result is bitwise the one of an
+ * uninterrupted fit. */
+#define GBFIT_SNAPSHOT_MAGIC 0x67626673u
+#define GBFIT_SNAPSHOT_STATE_BYTES 2048
+typedef struct gbfit_fit_snapshot {
+    uint32_t magic;                     /* GBFIT_SNAPSHOT_MAGIC                          */
+    uint32_t state_bytes;               /* bytes of state[] in use                       */
+    int32_t model_id, precision;
+    int64_t m;
+    int64_t reserved;                   /* (state[] starts on a 16-byte boundary)        */
+    unsigned char state[GBFIT_SNAPSHOT_STATE_BYTES];
+} gbfit_fit_snapshot;
+
+/* GBFIT_E_INVALID_ARG unless the ticket is resident (admitted, not finished). */
+int gbfit_server_snapshot(gbfit_server* s, uint64_t ticket, gbfit_fit_snapshot* out);
+
+/* Queue a request that resumes from a snapshot of the same model, size and
+ * server precision (refused otherwise); its p0 is ignored. */
+int gbfit_server_submit_resume(gbfit_server* s, const gbfit_request* req, const gbfit_fit_snapshot* snap,
+                               uint64_t* ticket);
 
 /* Copy up to max finished results (oldest first) into out; *count = copied. */
 int gbfit_server_poll(gbfit_server* s, gbfit_result_rec* out, int max, int* count);

@@ -333,6 +333,8 @@ int check_opts(const gbfit_options* o, int n) {
     if (!(o->f_scale >= 0) || !std::isfinite(o->f_scale)) return fail(GBFIT_E_INVALID_ARG, "f_scale must be > 0");
     if (std::isnan(o->guard_cond) || std::isnan(o->guard_floor))
         return fail(GBFIT_E_INVALID_ARG, "guard_cond and guard_floor must not be NaN");
+    if (std::isnan(o->wait_limit_s) || o->wait_limit_s > 3600.0)
+        return fail(GBFIT_E_INVALID_ARG, "wait_limit_s must be a number of seconds <= 3600");
     return GBFIT_OK;
 }
 
@@ -375,6 +377,8 @@ int run_fits(Ctx* c, const KernelSet* ks, int prec, std::vector<FitDesc>& hd, co
     char* hb = c->hbuf;
     memset(hb, 0, L.res_hdr + 32);                  // the job image plus a zeroed result header
     Engine E = c->engine(L);
+    for (size_t f = 0; f < nf; ++f)                 // the launch's grid-wide waits: the smallest limit asked
+        if (hd[f].wait_ns && (!E.wait_ns || hd[f].wait_ns < E.wait_ns)) E.wait_ns = hd[f].wait_ns;
     E.sc[0] = (int)ntiles;
     E.sc[1] = (int)nf;
     E.sc[2] = 0;
@@ -516,6 +520,7 @@ int fill_desc(FitDesc& d, const FitArgs& a, const gbfit_options& o, bool bounded
     const bool gfit = o.precision == GBFIT_PREC_MIXED && o.loss == GBFIT_LOSS_LINEAR;
     d.guard_cond = gfit ? guard_value(o.guard_cond, GBFIT_GUARD_COND_DEFAULT) : INFINITY;
     d.guard_floor = gfit ? guard_value(o.guard_floor, GBFIT_GUARD_FLOOR_DEFAULT) : INFINITY;
+    d.wait_ns = o.wait_limit_s > 0.0 ? (unsigned long long)std::max(1.0, o.wait_limit_s * 1e9) : 0ull;
     return GBFIT_OK;
 }
 
@@ -653,6 +658,7 @@ static int single_fit(int model_id, const void* xdata, int64_t m, int x_layout, 
                          (size_t)m * es, s, &sd))) return rc;
     std::vector<FitDesc> hd(1);
     fill_desc(hd[0], a, o, bounded, m, false, loop_grid(c, ks, o.precision));
+    hd[0].eval_only = eval_only ? 1 : 0;
     const void* x2 = (x_layout == GBFIT_X_SOA2) ? (const char*)sd.x + (size_t)m * es : nullptr;
     if (sigma && o.precision == GBFIT_PREC_FP64) {
         bool changed = false;
@@ -984,6 +990,17 @@ int gbfit_stats_get(gbfit_stats* out) {
     return GBFIT_OK;
 }
 
+int gbfit_check_rcp64(const double* x, double* y, int64_t n, void* cuda_stream) {
+    if (n < 0) return fail(GBFIT_E_INVALID_ARG, "n < 0");
+    if (n == 0) return GBFIT_OK;
+    if (!x || !y) return fail(GBFIT_E_INVALID_ARG, "x and y must not be NULL");
+    if (!is_device_ptr(x) || !is_device_ptr(y)) return fail(GBFIT_E_INVALID_ARG, "x and y must be device pointers");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    CUDA_TRY(launch_rcp64(x, y, n, 4 * 152, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return GBFIT_OK;
+}
+
 int gbfit_set_profiling(int on) {
     g_profiling = on ? 1 : 0;
     return GBFIT_OK;
@@ -1175,6 +1192,7 @@ extern "C" int gbfit_evaluate_noalloc(int model_id, const void* xdata, int64_t m
     FitArgs a{model_id, n, x_layout, dtype, m, gw, xdata, nullptr, ydata, sigma, p, nullptr, nullptr};
     FitDesc d;
     fill_desc(d, a, o, false, m, false, grid_na);
+    d.eval_only = 1;
     size_t es = dtype == GBFIT_F64 ? 8 : 4;
     d.x = x_layout == GBFIT_X_GRID ? nullptr : xdata;
     d.x2 = (x_layout == GBFIT_X_SOA2) ? (const char*)xdata + (size_t)m * es : nullptr;
@@ -1252,15 +1270,26 @@ struct RangeAlloc {
     }
 };
 
-struct SrvPending { gbfit_request req; uint64_t ticket; double t_submit; };
+struct SrvPending {
+    gbfit_request req;
+    uint64_t ticket;
+    double t_submit;
+    std::vector<unsigned char> resume;  // state prefix of a snapshot to continue from (empty: start at p0)
+};
 
 struct SrvSlot {
     bool used = false;
     uint64_t ticket = 0, tag = 0;
     size_t data_off = 0, data_bytes = 0, tile0 = 0, ntiles = 0, group0 = 0, ngroups = 0;
     double t_submit = 0, t_admit = 0;
-    int n = 0;
+    int n = 0, model = 0;
+    int64_t m = 0;
+    double p0[GBFIT_MAX_PARAMS] = {};
 };
+
+// Bytes of FitState a snapshot carries: everything before the trace counters.
+constexpr size_t SNAP_STATE_BYTES = offsetof(FitState, trace);
+static_assert(SNAP_STATE_BYTES <= GBFIT_SNAPSHOT_STATE_BYTES, "a fit's state must fit a snapshot");
 
 // Each array of a request starts on a 256-byte boundary of its pool region
 // (so that the bulk-copy ring can stream every array).
@@ -1387,7 +1416,8 @@ int gbfit_server_create(const gbfit_server_config* cfg_in, gbfit_server** out) {
     return GBFIT_OK;
 }
 
-int gbfit_server_submit(gbfit_server* s, const gbfit_request* r, uint64_t* ticket) {
+static int server_enqueue(gbfit_server* s, const gbfit_request* r, const gbfit_fit_snapshot* snap,
+                          uint64_t* ticket) {
     if (!s || !r) return fail(GBFIT_E_INVALID_ARG, "server and request must not be NULL");
     int n, rc;
     if ((rc = check_common(r->model_id, r->x_layout, r->dtype, r->ydata, &n))) return rc;
@@ -1402,6 +1432,9 @@ int gbfit_server_submit(gbfit_server* s, const gbfit_request* r, uint64_t* ticke
     if ((rc = check_params(a, &bounded))) return rc;
     if (r->loss < GBFIT_LOSS_LINEAR || r->loss > GBFIT_LOSS_ARCTAN) return fail(GBFIT_E_INVALID_ARG, "unknown loss %d", r->loss);
     if (!(r->f_scale >= 0) || !std::isfinite(r->f_scale)) return fail(GBFIT_E_INVALID_ARG, "f_scale must be > 0");
+    if (snap && (snap->magic != GBFIT_SNAPSHOT_MAGIC || snap->state_bytes != SNAP_STATE_BYTES ||
+                 snap->model_id != r->model_id || snap->m != r->m || snap->precision != s->prec))
+        return fail(GBFIT_E_INVALID_ARG, "the snapshot does not belong to this model, size and server precision");
     size_t need = req_data_bytes(*r);
     int tp, gt;
     multi_shape(r->model_id, s->prec, r->m, 0, 0, &tp, &gt);
@@ -1413,9 +1446,36 @@ int gbfit_server_submit(gbfit_server* s, const gbfit_request* r, uint64_t* ticke
     p.req = *r;
     p.ticket = s->next_ticket++;
     p.t_submit = now_s();
-    s->queue.push_back(p);
-    if (ticket) *ticket = p.ticket;
+    if (snap) p.resume.assign(snap->state, snap->state + SNAP_STATE_BYTES);
+    s->queue.push_back(std::move(p));
+    if (ticket) *ticket = s->queue.back().ticket;
     return GBFIT_OK;
+}
+
+int gbfit_server_submit(gbfit_server* s, const gbfit_request* r, uint64_t* ticket) {
+    return server_enqueue(s, r, nullptr, ticket);
+}
+
+int gbfit_server_submit_resume(gbfit_server* s, const gbfit_request* r, const gbfit_fit_snapshot* snap,
+                               uint64_t* ticket) {
+    if (!snap) return fail(GBFIT_E_INVALID_ARG, "snap is NULL");
+    return server_enqueue(s, r, snap, ticket);
+}
+
+// The device state of resident slot k (synchronous; between steps nothing runs).
+static int server_read_state(gbfit_server* s, int k, void* out) {
+    CUDA_TRY(cudaMemcpyAsync(out, s->job + s->L->state + (size_t)k * sizeof(FitState), SNAP_STATE_BYTES,
+                             cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return GBFIT_OK;
+}
+
+static void server_release(gbfit_server* s, int k) {
+    SrvSlot& sl = s->slots[k];
+    s->pool_alloc.release(sl.data_off, sl.data_bytes);
+    s->tile_alloc.release(sl.tile0, sl.ntiles);
+    s->group_alloc.release(sl.group0, sl.ngroups);
+    sl.used = false;
 }
 
 static int server_retire(gbfit_server* s) {
@@ -1451,10 +1511,7 @@ static int server_retire(gbfit_server* s) {
         rec.t_admit = sl.t_admit;
         rec.t_done = t;
         s->done.push_back(rec);
-        s->pool_alloc.release(sl.data_off, sl.data_bytes);
-        s->tile_alloc.release(sl.tile0, sl.ntiles);
-        s->group_alloc.release(sl.group0, sl.ngroups);
-        sl.used = false;
+        server_release(s, k);
     }
     return GBFIT_OK;
 }
@@ -1465,7 +1522,7 @@ int gbfit_server_step(gbfit_server* s, int* n_active, int* n_queued) {
     int rc;
     if ((rc = server_retire(s))) return rc;
     // ---- admit in arrival order while a slot and memory are free
-    std::vector<int> admitted;
+    std::vector<int> admitted, fresh;            // fresh: start at p0 (pass constants computed on the device)
     int free_slot = 0;
     while (!s->queue.empty()) {
         SrvPending& p = s->queue.front();
@@ -1515,9 +1572,16 @@ int gbfit_server_step(gbfit_server* s, int* n_active, int* n_queued) {
         d.group_base = (int64_t)g0;
         FitState* st = (FitState*)(s->hbuf + s->L->state) + free_slot;
         memset(st, 0, sizeof(FitState));
-        st->run = RS_RUNNING;
-        st->phase = PH_INIT;
-        for (int i = 0; i < n; ++i) { st->x[i] = r.p0[i]; st->xt[i] = r.p0[i]; st->scale_inv[i] = 1.0; }
+        const bool resumed = !p.resume.empty();
+        if (resumed) {
+            // the snapshot's state, pass constants for its pending evaluation included
+            memcpy(st, p.resume.data(), p.resume.size());
+            st->run = RS_RUNNING;
+        } else {
+            st->run = RS_RUNNING;
+            st->phase = PH_INIT;
+            for (int i = 0; i < n; ++i) { st->x[i] = r.p0[i]; st->xt[i] = r.p0[i]; st->scale_inv[i] = 1.0; }
+        }
         FitDesc* hd = (FitDesc*)(s->hbuf + s->L->desc) + free_slot;
         *hd = d;
         CUDA_TRY(cudaMemcpyAsync(s->job + s->L->desc + (size_t)free_slot * sizeof(FitDesc), hd, sizeof(FitDesc),
@@ -1533,21 +1597,25 @@ int gbfit_server_step(gbfit_server* s, int* n_active, int* n_queued) {
         sl.t_submit = p.t_submit;
         sl.t_admit = now_s();
         sl.n = n;
+        sl.m = r.m;
+        sl.model = r.model_id;
+        for (int i = 0; i < n; ++i) sl.p0[i] = r.p0[i];
         admitted.push_back(free_slot);
+        if (!resumed) fresh.push_back(free_slot);
         s->queue.pop_front();
     }
     // ---- counters of new fits start at zero; pass constants at p0
     Engine* Ed = (Engine*)s->job;
-    if (!admitted.empty()) {
+    for (int k : admitted) {
+        SrvSlot& sl = s->slots[k];
+        CUDA_TRY(cudaMemsetAsync(s->job + s->L->gcnt + sl.group0 * sizeof(int), 0, sl.ngroups * sizeof(int), s->stream));
+        CUDA_TRY(cudaMemsetAsync(s->job + s->L->fcnt + (size_t)k * sizeof(int), 0, sizeof(int), s->stream));
+    }
+    if (!fresh.empty()) {
         int* hl = (int*)(s->hbuf + s->L->end);
-        for (size_t k = 0; k < admitted.size(); ++k) {
-            hl[k] = admitted[k];
-            SrvSlot& sl = s->slots[admitted[k]];
-            CUDA_TRY(cudaMemsetAsync(s->job + s->L->gcnt + sl.group0 * sizeof(int), 0, sl.ngroups * sizeof(int), s->stream));
-            CUDA_TRY(cudaMemsetAsync(s->job + s->L->fcnt + (size_t)admitted[k] * sizeof(int), 0, sizeof(int), s->stream));
-        }
-        CUDA_TRY(cudaMemcpyAsync(s->d_list, hl, admitted.size() * sizeof(int), cudaMemcpyHostToDevice, s->stream));
-        int cnt = (int)admitted.size();
+        for (size_t k = 0; k < fresh.size(); ++k) hl[k] = fresh[k];
+        CUDA_TRY(cudaMemcpyAsync(s->d_list, hl, fresh.size() * sizeof(int), cudaMemcpyHostToDevice, s->stream));
+        int cnt = (int)fresh.size();
         void* a_init[] = {&Ed, &s->d_list, &cnt};
         CUDA_TRY(cudaLaunchKernel(kernel_init_slots(s->prec), dim3(cnt < 1024 ? cnt : 1024), dim3(32), a_init, 0, s->stream));
     }
@@ -1568,6 +1636,9 @@ int gbfit_server_step(gbfit_server* s, int* n_active, int* n_queued) {
         memcpy(hsc, sc8, sizeof sc8);
         CUDA_TRY(cudaMemcpyAsync(&Ed->sc[0], hsc, sizeof sc8, cudaMemcpyHostToDevice, s->stream));
         CUDA_TRY(cudaMemsetAsync(s->job + s->L->res_hdr, 0, 32, s->stream));
+        // per-SM CTA counters start at zero (a launch that aborted at its
+        // set-up barrier leaves them as they were)
+        CUDA_TRY(cudaMemsetAsync(s->job + s->L->smcnt, 0, (SM_IDS + 1) * sizeof(int), s->stream));
         int do_init = 0;
         void* a_loop[] = {&Ed, &do_init};
         CUDA_TRY(cudaLaunchCooperativeKernel(kernel_fit_loop(s->prec), dim3(s->grid), dim3(EVAL_THREADS), a_loop,
@@ -1578,7 +1649,7 @@ int gbfit_server_step(gbfit_server* s, int* n_active, int* n_queued) {
         if (hout[2]) return fail(GBFIT_E_TIMEOUT, "a round barrier of the loop kernel timed out");
         {
             std::lock_guard<std::mutex> gs(g_stats_mu);
-            g_stats.kernel_launches += 1 + (admitted.empty() ? 0 : 1);
+            g_stats.kernel_launches += 1 + (fresh.empty() ? 0 : 1);
         }
     }
     if ((rc = server_retire(s))) return rc;
@@ -1596,6 +1667,67 @@ int gbfit_server_poll(gbfit_server* s, gbfit_result_rec* out, int max, int* coun
     while (c < max && !s->done.empty()) { out[c++] = s->done.front(); s->done.pop_front(); }
     if (count) *count = c;
     return GBFIT_OK;
+}
+
+int gbfit_server_cancel(gbfit_server* s, uint64_t ticket) {
+    if (!s) return fail(GBFIT_E_INVALID_ARG, "server is NULL");
+    std::lock_guard<std::mutex> g(s->mu);
+    gbfit_result_rec rec;
+    memset(&rec, 0, sizeof rec);
+    rec.ticket = ticket;
+    rec.status = GBFIT_E_CANCELLED;
+    rec.fit_status = FS_MAX_NFEV;
+    rec.t_done = now_s();
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+        if (it->ticket == ticket) {                         // never started: p0, no evaluation
+            const gbfit_request& r = it->req;
+            rec.tag = r.tag;
+            rec.n_params = model_nparams(r.model_id);
+            for (int i = 0; i < rec.n_params; ++i) rec.popt[i] = r.p0[i];
+            rec.cost = NAN;
+            rec.t_submit = rec.t_admit = it->t_submit;
+            s->queue.erase(it);
+            s->done.push_back(rec);
+            return GBFIT_OK;
+        }
+    for (int k = 0; k < s->max_slots; ++k) {
+        SrvSlot& sl = s->slots[k];
+        if (!sl.used || sl.ticket != ticket) continue;
+        FitState st;
+        int rc = server_read_state(s, k, &st);
+        if (rc) return rc;
+        rec.tag = sl.tag;
+        rec.n_params = sl.n;
+        for (int i = 0; i < sl.n; ++i) rec.popt[i] = (st.nfev > 0) ? st.x[i] : sl.p0[i];
+        rec.cost = (st.nfev > 0) ? st.f : NAN;
+        rec.nfev = st.nfev;
+        rec.t_submit = sl.t_submit;
+        rec.t_admit = sl.t_admit;
+        s->done.push_back(rec);
+        server_release(s, k);
+        return GBFIT_OK;
+    }
+    return fail(GBFIT_E_INVALID_ARG, "ticket %llu is neither queued nor resident", (unsigned long long)ticket);
+}
+
+int gbfit_server_snapshot(gbfit_server* s, uint64_t ticket, gbfit_fit_snapshot* out) {
+    if (!s || !out) return fail(GBFIT_E_INVALID_ARG, "server and out must not be NULL");
+    std::lock_guard<std::mutex> g(s->mu);
+    for (int k = 0; k < s->max_slots; ++k) {
+        SrvSlot& sl = s->slots[k];
+        if (!sl.used || sl.ticket != ticket) continue;
+        memset(out, 0, sizeof *out);
+        int rc = server_read_state(s, k, out->state);
+        if (rc) return rc;
+        out->magic = GBFIT_SNAPSHOT_MAGIC;
+        out->state_bytes = (uint32_t)SNAP_STATE_BYTES;
+        out->model_id = sl.model;
+        out->precision = s->prec;
+        out->m = sl.m;
+        return GBFIT_OK;
+    }
+    return fail(GBFIT_E_INVALID_ARG, "ticket %llu is not resident (queued, finished or unknown)",
+                (unsigned long long)ticket);
 }
 
 int gbfit_server_destroy(gbfit_server* s) {

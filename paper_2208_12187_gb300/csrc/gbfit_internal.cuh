@@ -53,7 +53,9 @@ struct FitDesc {
     double f_scale;        // robust loss scale C (1 for the linear loss)
     // full covariance (Appendix C): rounds alternate between evaluating the
     // points into hbuf and reducing rows of X hbuf, X = L^-1 (C = L L^T)
-    int cov, pad3;
+    int cov;
+    int eval_only;         // one evaluation at p (gbfit_evaluate): no trust-region work, no pcov
+    unsigned long long wait_ns;   // limit of the loop kernel's grid-wide waits (the launch takes the smallest)
     // precision guard of the mixed path (off: +inf): a fit whose equilibrated
     // Gram condition number exceeds guard_cond continues with FP64 passes
     // from its current point; a fit that meets a tolerance while its
@@ -131,6 +133,7 @@ struct Engine {
                            // and re-armed by its step (batches of many fits); 0: rounds
     unsigned* fit_bits;    // queue mode: bit f set while fit f has unclaimed tiles ([ceil(fits / 32)])
     int* next_tile;        // queue mode: per fit, the next tile to claim in its current evaluation
+    unsigned long long wait_ns;   // limit of the grid-wide waits (round barrier, owner wait, queue idle wait)
 };
 
 }  // namespace gbfit

@@ -2,6 +2,7 @@
 // the host-side handles that pick a precision's instantiation.
 //   stage_weights_kernel  w = 1/sigma in FP64 for the plain path.
 //   tr_subproblem_kernel  one subproblem solve (test entry point).
+//   rcp64_kernel          the step's reciprocal on an array (test entry point).
 //   synth_fill_kernel     the autotuner's calibration data.
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -136,6 +137,17 @@ cudaError_t launch_synth_fill(int model, bool f64, void* x, void* x2, void* y, i
 cudaError_t launch_tr_subproblem(int n, const double* B, const double* g, double Delta, double alpha0,
                                  double* p_out, double* alpha_out, double* lam_out, cudaStream_t s) {
     tr_subproblem_kernel<<<1, 128, 0, s>>>(n, B, g, Delta, alpha0, p_out, alpha_out, lam_out);
+    return cudaGetLastError();
+}
+
+__global__ void rcp64_kernel(const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = rcp64(x[i]);
+}
+
+cudaError_t launch_rcp64(const double* x, double* y, int64_t n, int blocks, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    rcp64_kernel<<<blocks, 256, 0, s>>>(x, y, n);
     return cudaGetLastError();
 }
 

@@ -38,4 +38,5 @@ cudaError_t launch_cov_factor(double* A, double* W, double* X, double* Xc, float
                               int* flag, int sms, cudaStream_t s);
 cudaError_t launch_tr_subproblem(int n, const double* B, const double* g, double Delta, double alpha0,
                                  double* p_out, double* alpha_out, double* lam_out, cudaStream_t s);
+cudaError_t launch_rcp64(const double* x, double* y, int64_t n, int blocks, cudaStream_t s);
 }  // namespace gbfit

@@ -973,7 +973,10 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) eval_round_kernel(const Engin
 // launched cooperatively (every CTA resident), so a CTA that waits here
 // waits only for CTAs that are running.  Waits are bounded in time; past
 // the bound the CTA raises the abort bit and every CTA leaves the loop.
-constexpr unsigned long long ROUND_WAIT_LIMIT_NS = 10ull * 1000 * 1000 * 1000;
+constexpr unsigned long long ROUND_WAIT_LIMIT_NS = 10ull * 1000 * 1000 * 1000;   // default of Engine::wait_ns
+__device__ __forceinline__ unsigned long long wait_limit(const Engine& E) {
+    return E.wait_ns ? E.wait_ns : ROUND_WAIT_LIMIT_NS;
+}
 enum { CTL_STOP = 1, CTL_ABORT = 2 };
 
 // All CTAs arrive; the last one closes the round (rounds, running, stop
@@ -1015,7 +1018,7 @@ __device__ inline int grid_round_end(Engine* Ed, const Engine& E, int* ctl_smem,
             bool timed_out = false;
             while ((v = ld_acquire_u32(gen)) == g) {
                 __nanosleep(128);
-                if (global_ns() - t0 > ROUND_WAIT_LIMIT_NS) {
+                if (global_ns() - t0 > wait_limit(E)) {
                     atomicOr((int*)ctl, CTL_ABORT);
                     timed_out = true;
                     break;
@@ -1076,7 +1079,7 @@ __device__ void owner_steps(RoundSmem& sm, const Engine& E, Engine* Ed, int rank
             const unsigned long long g0 = global_ns();
             int ok = 1;
             while (ld_acquire_u32(cnt) != want) {
-                if (global_ns() - g0 > ROUND_WAIT_LIMIT_NS) { ok = 0; break; }
+                if (global_ns() - g0 > wait_limit(E)) { ok = 0; break; }
             }
             if (ok) E.fit_cnt[f] = 0;
             else atomicOr(&Ed->sc[7], CTL_ABORT);
@@ -1160,7 +1163,7 @@ __device__ void queue_loop(RoundSmem& sm, const Engine& E, Engine* Ed, RingState
                     st = (ld_acquire_u32(reinterpret_cast<const unsigned*>(E.running)) == 0u || (*ctl & CTL_ABORT)) ? 1 : 0;
                 stop = __shfl_sync(FULL, st, 0);
                 if (stop) break;
-                if (global_ns() - t0 > ROUND_WAIT_LIMIT_NS) {
+                if (global_ns() - t0 > wait_limit(E)) {
                     if (threadIdx.x == 0) atomicOr((int*)ctl, CTL_ABORT);
                     stop = 1;
                     break;

@@ -87,8 +87,13 @@ enum { VX = 0, VXT, VG, VLB, VUB, VSX, VV, VDV, VD, VGH, VC, VLAM, VGV, VSTR, VS
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
-// 1/x to about one ulp: FP32 reciprocal seed, two FP64 Newton steps (an FP64
-// division costs ~10 FP64 instructions on GB300, this ~6).
+// 1/x to about one ulp by Newton-Raphson iteration for the reciprocal
+// (y <- y + y (1 - x y), each step squaring the relative error) from the
+// correctly rounded FP32 reciprocal (relative error <= 2^-24): two steps reach
+// FP64 rounding (2^-96 before the final rounding).  An FP64 division costs
+// ~10 FP64 instructions on GB300, this ~6.  Outside FP32's comfortable range
+// (|x| <= 1e-36 or >= 1e36, non-finite) it falls back to the division.
+// Checked against 1.0 / x by gbfit_check_rcp64 (within 1 ulp).
 __device__ __forceinline__ double rcp64(double x) {
     float xf = float(x);
     float ax = fabsf(xf);

@@ -536,6 +536,10 @@ __device__ inline void write_result(const FitDesc& d, FitState* st, FitResult* r
     if (t < n) res->popt[t] = st->x[t];
     for (int k = t; k < KMAX; k += EVAL_THREADS) res->tot[k] = S.tot[k];
     if (t == 0) { res->cost = st->f; res->nfev = st->nfev; res->njev = st->njev; res->fit_status = status; }
+    if (d.eval_only) {                   // gbfit_evaluate wants the sums only
+        __syncthreads();
+        return;
+    }
     bool ok = (status >= 0) && d.m > n;
     if (!ok) {
         if (t < 64) res->pcov[t] = INFINITY;
@@ -729,7 +733,7 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
         // as if the trial is accepted (the common case), with the same
         // arithmetic as the path after the decision.  Used when it is.
         int spec = 0;
-        if (!d.jac_scale) {
+        if (!d.jac_scale && !d.eval_only) {
             const double x = (l < n) ? cst->xt[l] : 0.0, g = (l < n) ? S.tot[NT + l] : 0.0;
             for (int e = l; e < 64; e += 32) {
                 int i = e >> 3, j = e & 7;
@@ -749,7 +753,7 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
         if (l == 0) S.si[SI_SPEC] = spec;
     } else if (warp == 2) {
         // precision guard estimates at the point just evaluated (used when it is taken)
-        if (guard_on) guard_estimates(n, d.m, S.tot, cst->xt, S);
+        if (guard_on && !d.eval_only) guard_estimates(n, d.m, S.tot, cst->xt, S);
     }
     __syncthreads();
     trace_add(st, TR_LOGIC, tclk);

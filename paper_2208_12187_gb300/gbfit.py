@@ -20,7 +20,7 @@ from .build import LIB
 
 # ---- constants mirrored from include/gbfit.h
 OK = 0
-E_INVALID_ARG, E_INFEASIBLE_X0, E_OOM, E_BUDGET, E_CUDA, E_TIMEOUT, E_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
+E_INVALID_ARG, E_INFEASIBLE_X0, E_OOM, E_BUDGET, E_CUDA, E_TIMEOUT, E_UNSUPPORTED, E_CANCELLED = -1, -2, -3, -4, -5, -6, -7, -8
 MODEL_GAUSS1D, MODEL_DEXP, MODEL_GAUSS2D, MODEL_POLY2 = 0, 1, 2, 3
 X_VEC, X_SOA2, X_GRID = 0, 1, 2
 F32, F64 = 0, 1
@@ -34,7 +34,8 @@ EXPORTS = ["gbfit_version", "gbfit_last_error", "gbfit_default_options", "gbfit_
            "gbfit_stats_reset", "gbfit_stats_get", "gbfit_set_profiling", "gbfit_evaluate_noalloc",
            "gbfit_server_create", "gbfit_server_submit", "gbfit_server_step", "gbfit_server_poll",
            "gbfit_server_destroy", "gbfit_tune_get", "gbfit_tune_set", "gbfit_tune_shape", "gbfit_autotune",
-           "gbfit_model_register", "gbfit_model_log", "gbfit_curve_fit_cov", "gbfit_evaluate_cov"]
+           "gbfit_model_register", "gbfit_model_log", "gbfit_curve_fit_cov", "gbfit_evaluate_cov",
+           "gbfit_check_rcp64", "gbfit_server_cancel", "gbfit_server_snapshot", "gbfit_server_submit_resume"]
 
 
 class GbfitError(RuntimeError):
@@ -49,7 +50,7 @@ class Options(ctypes.Structure):
                 ("x_scale", ctypes.POINTER(ctypes.c_double)), ("absolute_sigma", ctypes.c_int),
                 ("precision", ctypes.c_int), ("tile_points", ctypes.c_int), ("group_tiles", ctypes.c_int),
                 ("loss", ctypes.c_int), ("reserved", ctypes.c_int * 1), ("f_scale", ctypes.c_double),
-                ("guard_cond", ctypes.c_double), ("guard_floor", ctypes.c_double)]
+                ("guard_cond", ctypes.c_double), ("guard_floor", ctypes.c_double), ("wait_limit_s", ctypes.c_double)]
 
 LOSSES = {"linear": 0, "soft_l1": 1, "huber": 2, "cauchy": 3, "arctan": 4}
 
@@ -91,6 +92,15 @@ class Request(ctypes.Structure):
                 ("loss", ctypes.c_int), ("f_scale", ctypes.c_double)]
 
 
+SNAPSHOT_STATE_BYTES = 2048
+
+
+class Snapshot(ctypes.Structure):
+    _fields_ = [("magic", ctypes.c_uint32), ("state_bytes", ctypes.c_uint32), ("model_id", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("m", ctypes.c_int64), ("reserved", ctypes.c_int64),
+                ("state", ctypes.c_ubyte * SNAPSHOT_STATE_BYTES)]
+
+
 class ResultRec(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int),
                 ("fit_status", ctypes.c_int), ("nfev", ctypes.c_int), ("n_params", ctypes.c_int),
@@ -126,6 +136,11 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.gbfit_tr_subproblem.argtypes = [I, DP, DP, D, D, DP, DP, DP, P]
     lib.gbfit_evaluate_noalloc.argtypes = [I, P, I64, I, ctypes.POINTER(ctypes.c_int64), P, P, I, DP, I, I, DP, P]
     lib.gbfit_stats_get.argtypes = [ctypes.POINTER(Stats)]
+    lib.gbfit_check_rcp64.argtypes = [P, P, I64, P]
+    lib.gbfit_server_cancel.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+    lib.gbfit_server_snapshot.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(Snapshot)]
+    lib.gbfit_server_submit_resume.argtypes = [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(Snapshot),
+                                               ctypes.POINTER(ctypes.c_uint64)]
     lib.gbfit_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]
     lib.gbfit_server_submit.argtypes = [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
     lib.gbfit_server_step.argtypes = [ctypes.c_void_p, IP, IP]
@@ -244,7 +259,7 @@ def _stream_ptr(stream):
 
 
 def _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles=0,
-             loss="linear", f_scale=1.0, guard_cond=0.0, guard_floor=0.0):
+             loss="linear", f_scale=1.0, guard_cond=0.0, guard_floor=0.0, wait_limit_s=0.0):
     load()
     o = Options.from_buffer_copy(_DEFAULT_OPT)
     o.ftol, o.xtol, o.gtol = ftol, xtol, gtol
@@ -269,6 +284,7 @@ def _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, 
     o.f_scale = float(f_scale)
     o.guard_cond = float(guard_cond)        # 0: library default; inf: off
     o.guard_floor = float(guard_floor)
+    o.wait_limit_s = float(wait_limit_s)    # 0: library default (10 s)
     return o, keep
 
 
@@ -302,20 +318,20 @@ def _scratch() -> _Scratch:
 
 
 def _cached_options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles,
-                    loss, f_scale, guard_cond=0.0, guard_floor=0.0):
+                    loss, f_scale, guard_cond=0.0, guard_floor=0.0, wait_limit_s=0.0):
     """(address of an Options, keepalive); options without an x_scale vector are cached."""
     if isinstance(x_scale, (int, float)) and x_scale == 1.0:
         key = (ftol, xtol, gtol, max_nfev, absolute_sigma, precision, tile_points, group_tiles, loss, f_scale,
-               guard_cond, guard_floor)
+               guard_cond, guard_floor, wait_limit_s)
         o = _OPT_CACHE.get(key)
         if o is None:
             o, _ = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points,
-                            group_tiles, loss, f_scale, guard_cond, guard_floor)
+                            group_tiles, loss, f_scale, guard_cond, guard_floor, wait_limit_s)
             if len(_OPT_CACHE) < 256:
                 _OPT_CACHE[key] = o
         return ctypes.addressof(o), o
     o, keep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles,
-                       loss, f_scale, guard_cond, guard_floor)
+                       loss, f_scale, guard_cond, guard_floor, wait_limit_s)
     return ctypes.addressof(o), (o, keep)
 
 
@@ -359,7 +375,7 @@ def model_log() -> str:
 def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None, ub=None,
               grid_wh=None, ftol=1e-8, xtol=1e-8, gtol=1e-8, max_nfev=None, x_scale=1.0,
               absolute_sigma=False, precision="mixed", tile_points=0, group_tiles=0, loss="linear",
-              f_scale=1.0, stream=None, guard_cond=0.0, guard_floor=0.0) -> dict:
+              f_scale=1.0, stream=None, guard_cond=0.0, guard_floor=0.0, wait_limit_s=0.0) -> dict:
     """Fit `model` by the GPU trust-region-reflective method (gbfit_curve_fit).
 
     xdata: [m] (1D models), [2, m] (2D explicit coordinates) or None with
@@ -396,7 +412,7 @@ def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None
         v[_Scratch.UB:_Scratch.UB + n] = ub
         ubp = base + 8 * _Scratch.UB
     optp, okeep = _cached_options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points,
-                                  group_tiles, loss, f_scale, guard_cond, guard_floor)
+                                  group_tiles, loss, f_scale, guard_cond, guard_floor, wait_limit_s)
     a = base + 8 * _Scratch.OUT                    # popt | pcov | cost
     ip = base + 8 * _Scratch.INTS                  # nfev | status
     call = lib.gbfit_curve_fit
@@ -415,7 +431,7 @@ def curve_fit(model: int, xdata, ydata, p0: Sequence[float], sigma=None, lb=None
 def curve_fit_batch(model: int, offsets, xdata, ydata, p0, sigma=None, lb=None, ub=None,
                     ftol=1e-8, xtol=1e-8, gtol=1e-8, max_nfev=None, x_scale=1.0,
                     absolute_sigma=False, precision="mixed", tile_points=0, group_tiles=0, loss="linear",
-                    f_scale=1.0, stream=None, guard_cond=0.0, guard_floor=0.0) -> dict:
+                    f_scale=1.0, stream=None, guard_cond=0.0, guard_floor=0.0, wait_limit_s=0.0) -> dict:
     """Many independent fits over concatenated data (gbfit_curve_fit_batch).
     tile_points / group_tiles 0: each fit's shape from the tile table."""
     lib = load()
@@ -430,7 +446,7 @@ def curve_fit_batch(model: int, offsets, xdata, ydata, p0, sigma=None, lb=None, 
     lba = None if lb is None else np.ascontiguousarray(np.broadcast_to(np.asarray(lb, np.float64), (nf, n)))
     uba = None if ub is None else np.ascontiguousarray(np.broadcast_to(np.asarray(ub, np.float64), (nf, n)))
     opt, okeep = _options(n, ftol, xtol, gtol, max_nfev, x_scale, absolute_sigma, precision, tile_points, group_tiles,
-                          loss, f_scale, guard_cond, guard_floor)
+                          loss, f_scale, guard_cond, guard_floor, wait_limit_s)
     popt = np.zeros((nf, n))
     pcov = np.zeros((nf, n, n))
     cost = np.zeros(nf)
@@ -498,6 +514,19 @@ def unpack_upper(packed, n):
             B[i, j] = B[j, i] = packed[k]
             k += 1
     return B
+
+
+def check_rcp64(x, stream=None):
+    """1/x by the device step's FP64 reciprocal (gbfit_check_rcp64); x: a CUDA
+    float64 tensor.  Returns a new tensor."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64):
+        raise TypeError("x must be a CUDA float64 tensor")
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    _check(load().gbfit_check_rcp64(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                    ctypes.c_int64(x.numel()), _stream_ptr(stream)))
+    return y
 
 
 def stats_reset():
@@ -598,7 +627,8 @@ class Server:
         self._keep = {}
 
     def submit(self, model, xdata, ydata, p0, sigma=None, lb=None, ub=None, grid_wh=None, ftol=1e-8, xtol=1e-8,
-               gtol=1e-8, max_nfev=0, tag=0, loss="linear", f_scale=1.0) -> int:
+               gtol=1e-8, max_nfev=0, tag=0, loss="linear", f_scale=1.0, resume=None) -> int:
+        """Queue a request; resume: a Snapshot (from snapshot()) to continue from."""
         n = N_PARAMS[model]
         r = Request()
         yp, dt, yk = _array_info(ydata)
@@ -622,9 +652,22 @@ class Server:
         r.loss = LOSSES[loss] if isinstance(loss, str) else int(loss)
         r.f_scale = float(f_scale)
         t = ctypes.c_uint64()
-        _check(load().gbfit_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        if resume is None:
+            _check(load().gbfit_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        else:
+            _check(load().gbfit_server_submit_resume(self._h, ctypes.byref(r), ctypes.byref(resume), ctypes.byref(t)))
         self._keep[t.value] = (xk, yk, sk)
         return t.value
+
+    def cancel(self, ticket: int):
+        """Cancel a queued or resident request (its record is polled with status E_CANCELLED)."""
+        _check(load().gbfit_server_cancel(self._h, int(ticket)))
+
+    def snapshot(self, ticket: int) -> "Snapshot":
+        """The device state of a resident request (checkpoint), for submit(..., resume=)."""
+        snap = Snapshot()
+        _check(load().gbfit_server_snapshot(self._h, int(ticket), ctypes.byref(snap)))
+        return snap
 
     def step(self):
         a, q = ctypes.c_int(), ctypes.c_int()
