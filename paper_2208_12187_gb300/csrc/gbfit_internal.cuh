@@ -28,10 +28,12 @@ constexpr int PF_C2 = PF - 1, PF_IC2 = PF - 2, PD_C2 = PD - 1, PD_IC2 = PD - 2;
 //   [0, NT)        packed upper triangle of J'^T J' at the evaluated point
 //   [NT, NT+n)     J'^T r'
 //   NT+n           sum r'^2                        (= 2 f at the evaluated point)
-//   NT+n+1         sum dr (2 r + dr)   mixed only  (= 2 (f' - f), cancellation-free)
-//   NT+n+2         sum (w h)^2         mixed only  (scale of the FP32 rounding of r, for the guard)
+//   NT+n+1         sum dr (2 r + dr)   mixed only  (= 2 (f' - f), cancellation-free); at a fit's
+//                                                  first evaluation (dr = 0) it carries sum (w h)^2
+//                                                  instead (scale of the FP32 rounding of r, for the
+//                                                  precision guard)
 __host__ __device__ constexpr int n_tri(int n) { return n * (n + 1) / 2; }
-__host__ __device__ constexpr int n_acc(int n, int prec) { return n_tri(n) + n + (prec == PREC_MIXED ? 3 : 1); }
+__host__ __device__ constexpr int n_acc(int n, int prec) { return n_tri(n) + n + (prec == PREC_MIXED ? 2 : 1); }
 
 // Immutable description of one fit (uploaded once).
 struct FitDesc {
@@ -94,7 +96,7 @@ struct alignas(16) FitState {
     double s_h[NMAX];      // scaled step of the pending trial
     double floor_x;        // mixed path: estimated FP32 rounding floor of popt at x (relative)
     double serel_x;        // mixed path: largest standard error relative to its parameter at x
-    double pad_s;          // (the prefix above is a whole number of 16-byte words)
+    double wh2;            // mixed path: sum (w h)^2 at p0 (from the first evaluation)
     // --- (the step reads everything above from a shared-memory copy) ---
     unsigned long long trace[32];  // SM cycles / ns / counts per phase (TracePhase), summed over iterations
 };

@@ -156,9 +156,9 @@ __device__ __forceinline__ void accum_point(const float* pfl, const double* pdl,
             acc[NT + N + 1] += dc;
         } else {
             acc[NT + N] = fmaf(rn, rn, acc[NT + N]);
-            acc[NT + N + 1] = fmaf(dr, fmaf(2.0f, r, dr), acc[NT + N + 1]);
+            // sum dr (2 r + dr); at the first evaluation (check, dr = 0): sum (w h)^2
             const float wh = w * hb;
-            acc[NT + N + 2] = fmaf(wh, wh, acc[NT + N + 2]);
+            acc[NT + N + 1] = check ? fmaf(wh, wh, acc[NT + N + 1]) : fmaf(dr, fmaf(2.0f, r, dr), acc[NT + N + 1]);
         }
     } else {
         double h, J[N];
@@ -224,8 +224,7 @@ __device__ __forceinline__ void accum_point2(const float* pfl, float2 X, float2 
 #pragma unroll
         for (int a = 0; a < N; ++a) acc[NT + a] = fma2(J[a], rn, acc[NT + a]);
         acc[NT + N] = fma2(rn, rn, acc[NT + N]);
-        acc[NT + N + 1] = add2(dc, acc[NT + N + 1]);
-        acc[NT + N + 2] = fma2(wh, wh, acc[NT + N + 2]);
+        acc[NT + N + 1] = check ? fma2(wh, wh, acc[NT + N + 1]) : add2(dc, acc[NT + N + 1]);
     } else {
         int idx = 0;
 #pragma unroll
@@ -238,8 +237,7 @@ __device__ __forceinline__ void accum_point2(const float* pfl, float2 X, float2 
 #pragma unroll
         for (int a = 0; a < N; ++a) acc[NT + a] = fmaf(J[a].y, rn.y, fmaf(J[a].x, rn.x, acc[NT + a]));
         acc[NT + N] = fmaf(rn.y, rn.y, fmaf(rn.x, rn.x, acc[NT + N]));
-        acc[NT + N + 1] += dc.x + dc.y;
-        acc[NT + N + 2] = fmaf(wh.y, wh.y, fmaf(wh.x, wh.x, acc[NT + N + 2]));
+        acc[NT + N + 1] = check ? fmaf(wh.y, wh.y, fmaf(wh.x, wh.x, acc[NT + N + 1])) : acc[NT + N + 1] + (dc.x + dc.y);
     }
 }
 
@@ -707,10 +705,9 @@ __device__ void cov_rows(const FitDesc& d, int tile, void* scratch, typename Acc
 
 // FP64 evaluation of points [i0, i1) inside the mixed-precision kernel (a fit
 // that the precision guard moved to FP64 passes), block-reduced: thread
-// k < n_acc(N, FP64) returns slot k of the tile sum.  Not inlined, so that its
-// FP64 registers do not enter the streaming FP32 path's allocation.
+// k < n_acc(N, FP64) returns slot k of the tile sum.
 template <class M>
-__device__ __noinline__ double tile_sum_fp64(RoundSmem& sm, int64_t i0, int64_t i1, bool check, int* bad_out) {
+__device__ __forceinline__ double tile_sum_fp64(RoundSmem& sm, int64_t i0, int64_t i1, bool check, int* bad_out) {
     constexpr int K = n_acc(M::N, PREC_FP64);
     double acc[K];
     int bad = 0;
@@ -722,8 +719,11 @@ __device__ __noinline__ double tile_sum_fp64(RoundSmem& sm, int64_t i0, int64_t 
     return tsum;
 }
 
-template <class M, int PREC, class MS>
-__device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, RingState& R, long long t_item) {
+// Tile part of a work item: evaluate the tile's points, reduce them and
+// store the tile's partial sums.  Returns the number of sum slots, or 0 when
+// the item has nothing more to do (the evaluation round of a covariance fit).
+template <class M, int PREC>
+__device__ __forceinline__ int item_tile(RoundSmem& sm, const Engine& E, int fit, int tile, RingState& R) {
     using AT = typename AccT<PREC>::T;
     constexpr int N = M::N;
     constexpr int K = n_acc(N, PREC);
@@ -733,65 +733,90 @@ __device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, 
     int64_t i1 = i0 + d.tile_points;
     if (i1 > d.m) i1 = d.m;
     bool check = sm.flag[1] == PH_INIT;
-    long long t_tile = clock64();
     R.wait_cycles = 0;
     int bad = 0;
-    // slots of this evaluation: FP64 ones for a mixed fit the guard moved to FP64
-    const bool e64 = PREC == PREC_MIXED && sm.eval64 && !d.cov;
-    const int Kuse = e64 ? n_acc(N, PREC_FP64) : K;
-    double tval = 0.0;
-    if (e64) {
-        if constexpr (PREC == PREC_MIXED) tval = tile_sum_fp64<M>(sm, i0, i1, check, &bad);
-        if (threadIdx.x == 0) sm.t_loop = clock64();
-        if (check) {
-            int any = __syncthreads_or(bad);
-            if (any && threadIdx.x == 0) atomicOr(&stp->bad_data, 1);
-        }
-    } else {
-        AT acc[K];
-        if (d.cov) {
-            if (sm.cov_stage == 0) {
-                // evaluation round: the item's points into hbuf; the last item of
-                // the fit to finish opens the row round (the grid barrier
-                // publishes hbuf and the stage)
-                cov_eval_dispatch<M, PREC>(d, sm.pf, sm.pd, i0, i1, check, bad);
-                if (check) {
-                    int any = __syncthreads_or(bad);
-                    if (any && threadIdx.x == 0) atomicOr(&stp->bad_data, 1);
-                }
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    int old = arrive_acq_rel(&E.fit_cnt[fit]);
-                    if (old == d.n_tiles - 1) {
-                        E.fit_cnt[fit] = 0;
-                        stp->cov_stage = 1;
-                    }
-                }
-                return;
+    AT acc[K];
+    if (d.cov) {
+        if (sm.cov_stage == 0) {
+            // evaluation round: the item's points into hbuf; the last item of
+            // the fit to finish opens the row round (the grid barrier
+            // publishes hbuf and the stage)
+            cov_eval_dispatch<M, PREC>(d, sm.pf, sm.pd, i0, i1, check, bad);
+            if (check) {
+                int any = __syncthreads_or(bad);
+                if (any && threadIdx.x == 0) atomicOr(&stp->bad_data, 1);
             }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int old = arrive_acq_rel(&E.fit_cnt[fit]);
+                if (old == d.n_tiles - 1) {
+                    E.fit_cnt[fit] = 0;
+                    stp->cov_stage = 1;
+                }
+            }
+            return 0;
+        }
 #pragma unroll
-            for (int k = 0; k < K; ++k) acc[k] = AT(0);
-            cov_rows<N, PREC>(d, tile, R.buf, acc);
-            check = false;
-        } else {
-            eval_tile_dispatch<M, PREC>(sm, i0, i1, check, bad, acc, R);
-        }
-        if (threadIdx.x == 0) sm.t_loop = clock64();
-        if (sm.ring_fail && threadIdx.x == 0) atomicOr(&stp->bad_data, 2);   // a bounded wait gave up
-        if (check) {
-            int any = __syncthreads_or(bad);
-            if (any && threadIdx.x == 0) atomicOr(&stp->bad_data, 1);
-        }
-        AT* red = (PREC == PREC_MIXED) ? (AT*)sm.redf : (AT*)sm.redd;
-        AT tsum;
-        block_reduce<K, AT>(acc, red, tsum);
-        tval = double(tsum);
+        for (int k = 0; k < K; ++k) acc[k] = AT(0);
+        cov_rows<N, PREC>(d, tile, R.buf, acc);
+        check = false;
+    } else {
+        eval_tile_dispatch<M, PREC>(sm, i0, i1, check, bad, acc, R);
+    }
+    if (threadIdx.x == 0) sm.t_loop = clock64();
+    if (sm.ring_fail && threadIdx.x == 0) atomicOr(&stp->bad_data, 2);   // a bounded wait gave up
+    if (check) {
+        int any = __syncthreads_or(bad);
+        if (any && threadIdx.x == 0) atomicOr(&stp->bad_data, 1);
+    }
+    AT* red = (PREC == PREC_MIXED) ? (AT*)sm.redf : (AT*)sm.redd;
+    AT tsum;
+    block_reduce<K, AT>(acc, red, tsum);
+    if (threadIdx.x == 0) sm.t_mark = clock64();
+    const int64_t row = d.tile_base + tile;
+    if (threadIdx.x < K) E.tile_part_d[row * KMAX + threadIdx.x] = double(tsum);
+    return K;
+}
+
+// The same for a fit the guard moved to FP64 passes (mixed kernel only).  Not
+// inlined: its FP64 registers stay out of the streaming FP32 path's
+// allocation, and it is called where little else is live.
+template <class M>
+__device__ __noinline__ int item_tile_e64(RoundSmem& sm, const Engine& E, int fit, int tile) {
+    constexpr int K = n_acc(M::N, PREC_FP64);
+    const FitDesc& d = sm.desc;
+    FitState* stp = E.state + fit;
+    const int64_t i0 = (int64_t)tile * d.tile_points;
+    const int64_t i1 = min(i0 + (int64_t)d.tile_points, d.m);
+    const bool check = sm.flag[1] == PH_INIT;
+    int bad = 0;
+    const double tsum = tile_sum_fp64<M>(sm, i0, i1, check, &bad);
+    if (threadIdx.x == 0) sm.t_loop = clock64();
+    if (check) {
+        int any = __syncthreads_or(bad);
+        if (any && threadIdx.x == 0) atomicOr(&stp->bad_data, 1);
     }
     if (threadIdx.x == 0) sm.t_mark = clock64();
-    int64_t row = d.tile_base + tile;
-    if (threadIdx.x < Kuse) {
-        E.tile_part_d[row * KMAX + threadIdx.x] = tval;
+    const int64_t row = d.tile_base + tile;
+    if (threadIdx.x < K) E.tile_part_d[row * KMAX + threadIdx.x] = tsum;
+    return K;
+}
+
+// One work item: its tile, then (by the last arriver) the group and fit
+// combines and the fit's trust-region step.
+template <class M, int PREC, class MS>
+__device__ void process_item(RoundSmem& sm, const Engine& E, int fit, int tile, RingState& R, long long t_item) {
+    const long long t_tile = clock64();
+    int Kuse;
+    if (PREC == PREC_MIXED && sm.eval64 && !sm.desc.cov) {
+        Kuse = item_tile_e64<M>(sm, E, fit, tile);
+        R.wait_cycles = 0;
+    } else {
+        Kuse = item_tile<M, PREC>(sm, E, fit, tile, R);
     }
+    if (Kuse == 0) return;
+    const FitDesc& d = sm.desc;
+    FitState* stp = E.state + fit;
     // ---- last arriver of the group combines the group
     __syncthreads();
     int group = tile / d.group_tiles;

@@ -424,64 +424,80 @@ __device__ __forceinline__ double guard_tol_scale(const FitState* cst) {
     return (cst->eval64 && (cst->guard_why == GUARD_FINISH || cst->guard_why == GUARD_ESC_MID)) ? 1e-2 : 1.0;
 }
 
-// One warp.  tot: packed sums of the evaluation at xt (mixed slots, with
-// sum (w h)^2 at NT+n+2); m: points.  Writes S.sd[SD_COND] and S.sd[SD_FLOOR].
-// Uses S.A and S.Af, which nothing else touches during the step's first phase.
-__device__ inline void guard_estimates(int n, int64_t m, const double* tot, const double* xt, TrfSmem& S) {
+// One warp, FP32 throughout (estimates need a digit or two; FP64 divisions
+// and square roots would make this the longest warp of the step's first
+// phase).  tot: packed sums of the evaluation at xt; wh2: sum (w h)^2 at p0;
+// m: points.  Writes S.sd[SD_COND], S.sd[SD_FLOOR] and
+// S.sd[SD_SEREL].  The matrix lives in registers as in inv32: lane l holds
+// rows i0 = l/8 and i1 = 4 + l/8 of column j = l%8.
+__device__ inline void guard_estimates(int n, int64_t m, const double* tot, double wh2, const double* xt,
+                                       TrfSmem& S) {
     const int l = threadIdx.x & 31;
     const int NT = n_tri(n);
-    // S_l = 1/sqrt(B_ll) in lane l (FP32 suffices for an estimate)
+    // S_l = 1/sqrt(B_ll) in lane l
     float sdl = 0.0f;
     bool pos = true;
     if (l < n) {
-        const double bll = tot[l * n - l * (l - 1) / 2];
-        pos = bll > 0.0 && isfinite(bll);
-        sdl = pos ? rsqrtf(float(bll)) : 0.0f;
+        const float bll = float(tot[l * n - l * (l - 1) / 2]);
+        pos = bll > 1e-30f && bll < 1e30f;
+        sdl = pos ? rsqrtf(bll) : 0.0f;
     }
     pos = __all_sync(FULL, pos);
-    // M = S B S (unit diagonal; identity outside n)
-    for (int e = l; e < 64; e += 32) {
-        const int i = e >> 3, j = e & 7;
-        const float si = __shfl_sync(FULL, sdl, i), sj = __shfl_sync(FULL, sdl, j);
-        double v = (i == j) ? 1.0 : 0.0;
-        if (i < n && j < n && i != j) {
-            const int a = min(i, j), c = max(i, j);
-            v = double(float(tot[a * n - a * (a - 1) / 2 + (c - a)]) * si * sj);
-        }
-        S.A[e] = v;
+    const int j = l & 7, i0 = l >> 3, i1 = i0 + 4;
+    const float sj = __shfl_sync(FULL, sdl, j), s0 = __shfl_sync(FULL, sdl, i0), s1 = __shfl_sync(FULL, sdl, i1);
+    auto entry = [&](int i, float si) -> float {          // M = S B S, unit diagonal, identity outside n
+        if (i == j) return 1.0f;
+        if (i >= n || j >= n) return 0.0f;
+        const int a = min(i, j), c = max(i, j);
+        return float(tot[a * n - a * (a - 1) / 2 + (c - a)]) * si * sj;
+    };
+    float a0 = entry(i0, s0), a1 = entry(i1, s1);
+    auto rowmax = [&](float v0, float v1) -> float {      // max over rows of the row sums of |.|
+        float r0 = fabsf(v0), r1 = fabsf(v1);
+        for (int o = 1; o < 8; o <<= 1) { r0 += __shfl_xor_sync(FULL, r0, o); r1 += __shfl_xor_sync(FULL, r1, o); }
+        float r = fmaxf(r0, r1);
+        for (int o = 8; o < 32; o <<= 1) r = fmaxf(r, __shfl_xor_sync(FULL, r, o));
+        return r;
+    };
+    const float rm = rowmax(i0 < n ? a0 : 0.0f, i1 < n ? a1 : 0.0f);
+    // Gauss-Jordan inverse without pivoting (pivots of the LDL^T factors: all
+    // positive exactly when M is positive definite)
+    bool ok = pos;
+    for (int k = 0; k < n; ++k) {
+        const float rowk = (k < 4) ? a0 : a1;
+        const int kb = (k & 3) << 3;
+        const float piv = __shfl_sync(FULL, rowk, kb + k);
+        const float akj = __shfl_sync(FULL, rowk, kb + j);
+        const float ai0 = __shfl_sync(FULL, a0, (l & ~7) + k);
+        const float ai1 = __shfl_sync(FULL, a1, (l & ~7) + k);
+        ok = ok && piv > 0.0f;
+        const float r = __frcp_rn(piv > 0.0f ? piv : 1.0f);
+        a0 = (i0 == k) ? ((j == k) ? r : akj * r) : ((j == k) ? -ai0 * r : fmaf(-ai0 * r, akj, a0));
+        a1 = (i1 == k) ? ((j == k) ? r : akj * r) : ((j == k) ? -ai1 * r : fmaf(-ai1 * r, akj, a1));
     }
-    __syncwarp();
-    float sc = 1.0f, mind = 0.0f;
-    const bool inv_ok = inv32(n, S.A, S.Af, sc, mind);          // every lane takes part
-    const bool ok = pos && __all_sync(FULL, inv_ok);
-    // ||M||_inf, ||M^-1||_inf (lane l < n: row l) and (M^-1)_ll
-    float rm = 0.0f, ri = 0.0f, dinv = 0.0f;
+    ok = __all_sync(FULL, ok);
+    const float ri = rowmax(i0 < n ? a0 : 0.0f, i1 < n ? a1 : 0.0f);
+    // (M^-1)_ll to lane l: row l < 4 is a0 of lane 9 l, row l >= 4 is a1 of lane 8 (l - 4) + l
+    const float d0 = __shfl_sync(FULL, a0, (l & 3) * 9), d1 = __shfl_sync(FULL, a1, (l & 3) * 8 + 4 + (l & 3));
+    const float dinv = (l < 4) ? d0 : d1;
+    // rounding floor and relative standard errors: (B^-1)_ll = S_l^2 (M^-1)_ll
+    const float rms = sqrtf(fmaxf(float(wh2), 0.0f) / float(m));
+    const float s2 = (m > n) ? float(tot[NT + n]) / float(m - n) : INFINITY;     // 2f / (m - n)
+    float fl = 0.0f, se = 0.0f;
     if (l < n) {
-        for (int j = 0; j < n; ++j) {
-            rm += fabsf(float(S.A[l * 8 + j]));
-            ri += fabsf(S.Af[l * 8 + j]);
-        }
-        dinv = S.Af[l * 8 + l];
+        const float binv = (dinv > 0.0f) ? dinv * sdl * sdl : INFINITY;
+        const float ax = fabsf(float(xt[l]));
+        fl = float(GUARD_C_H * EPS32) * rms * sqrtf(binv) / fmaxf(ax, 1.0f);
+        se = sqrtf(s2 * binv) / ax;
     }
     for (int o = 16; o; o >>= 1) {
-        rm = fmaxf(rm, __shfl_xor_sync(FULL, rm, o));
-        ri = fmaxf(ri, __shfl_xor_sync(FULL, ri, o));
+        fl = fmaxf(fl, __shfl_xor_sync(FULL, fl, o));
+        se = fmaxf(se, __shfl_xor_sync(FULL, se, o));
     }
-    // rounding floor and relative standard errors: (B^-1)_ll = S_l^2 (M^-1)_ll
-    const double rms = sqrt(fmax(tot[NT + n + 2], 0.0) / double(m));
-    const double s2 = (m > n) ? tot[NT + n] / double(m - n) : INFINITY;     // 2f / (m - n)
-    double fl = 0.0, se = 0.0;
-    if (l < n) {
-        const double binv = (dinv > 0.0f) ? double(dinv) * double(sdl) * double(sdl) : INFINITY;
-        fl = GUARD_C_H * EPS32 * rms * sqrt(binv) / fmax(fabs(xt[l]), 1.0);
-        se = sqrt(s2 * binv) / fabs(xt[l]);
-    }
-    fl = gmax8(fl);
-    se = gmax8(se);
     if (l == 0) {
         S.sd[SD_COND] = ok ? double(rm) * double(ri) : INFINITY;
-        S.sd[SD_FLOOR] = ok ? fl : INFINITY;
-        S.sd[SD_SEREL] = ok ? se : INFINITY;
+        S.sd[SD_FLOOR] = ok ? double(fl) : INFINITY;
+        S.sd[SD_SEREL] = ok ? double(se) : INFINITY;
     }
     __syncwarp();
 }
@@ -753,7 +769,9 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
         if (l == 0) S.si[SI_SPEC] = spec;
     } else if (warp == 2) {
         // precision guard estimates at the point just evaluated (used when it is taken)
-        if (guard_on && !d.eval_only) guard_estimates(n, d.m, S.tot, cst->xt, S);
+        // sum (w h)^2: this evaluation's when it is the first (slot NT+n+1), else the one kept
+        if (guard_on && !d.eval_only)
+            guard_estimates(n, d.m, S.tot, cst->phase == PH_INIT ? S.tot[NT + n + 1] : cst->wh2, cst->xt, S);
     }
     __syncthreads();
     trace_add(st, TR_LOGIC, tclk);
@@ -783,6 +801,7 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
                 esc = GUARD_FINISH;
             S.si[SI_ESC] = esc;
             if (take) { st->floor_x = S.sd[SD_FLOOR]; st->serel_x = S.sd[SD_SEREL]; }
+            if (cst->phase == PH_INIT) st->wh2 = S.tot[NT + n + 1];
         }
         __syncthreads();
         if (S.si[SI_ESC]) {
