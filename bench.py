@@ -84,7 +84,7 @@ class L2Flush:
 # the headline workload, 5 passes) from the ncu capture summarised in
 # profiles/fit_loop_mixed_gauss2d_1024.md; None whenever the kernel has
 # changed since the capture.
-TRAFFIC_BYTES_PER_LAUNCH = None
+TRAFFIC_BYTES_PER_LAUNCH = 8.6725e6
 
 
 def measured_peaks():
@@ -497,6 +497,41 @@ def layouts_and_fp64(args, pr, y, sg, flush, dev):
         out[name] = {"value": pts / (ms / 1e3), "unit": UNIT, "ms_per_fit": ms / 3, "nfev": r["nfev"],
                      "popt": r["popt"]}
     return out
+
+
+def run_eval_pass(args):
+    """The fused evaluation pass alone (gbfit_evaluate) on the 1D Gaussian at
+    the sizes of --sizes and the precisions of --precisions: --steps launches
+    each after the L2 flush, CUDA-event time per launch (one JSON line per
+    size and precision).  The capture target of the kernel-only ncu profiles."""
+    import torch
+    from paper_2208_12187_gb300 import build, gbfit, synth
+    build.build()
+    gbfit.load()
+    dev = torch.device("cuda", 0)
+    flush = L2Flush(dev)
+    hbm, _ = measured_peaks()
+    for m in [int(float(v)) for v in args.sizes.split(",")]:
+        pr = synth.gauss1d(m, seed=0, dtype=np.float64)
+        for prec in args.precisions.split(","):
+            dt = torch.float32 if prec == "mixed" else torch.float64
+            x = torch.as_tensor(pr.x).to(dt).to(dev)
+            y = torch.as_tensor(pr.y).to(dt).to(dev)
+            call = lambda: gbfit.evaluate(pr.model, x, y, pr.p0, precision=prec)
+            call()
+            gbfit.set_profiling(True)
+            gbfit.stats_reset()
+            for _ in range(args.steps):
+                flush.zero_()
+                call()
+            st = gbfit.stats()
+            gbfit.set_profiling(False)
+            us = st["eval_ms"] / max(st["eval_launches"], 1) * 1e3
+            bpp = 8 if prec == "mixed" else 16
+            print(json.dumps({"mode": "eval_pass", "model": "gauss1d", "m": m, "precision": prec,
+                              "us_per_launch": us, "gbs": m * bpp / us / 1e3, "frac_hbm": m * bpp / us / 1e3 / hbm,
+                              "launches": int(st["eval_launches"])}), flush=True)
+            del x, y
 
 
 def run_phases(args):
@@ -942,6 +977,8 @@ def main():
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--user", action="store_true", help="user-defined models (run-time compiled) vs built-in")
     ap.add_argument("--cov", action="store_true", help="full-covariance fits (sizes from --sizes)")
+    ap.add_argument("--eval-pass", action="store_true",
+                    help="the fused evaluation pass alone (gbfit_evaluate), 1D Gaussian, --sizes x --precisions")
     ap.add_argument("--phases", action="store_true",
                     help="per-iteration phase cycles of the loop kernel (headline and 1D workloads, warm L2)")
     ap.add_argument("--compare", action="store_true",
@@ -972,6 +1009,8 @@ def main():
         return run_compare(args)
     if args.phases:
         return run_phases(args)
+    if args.eval_pass:
+        return run_eval_pass(args)
     rank, local, world = dist_setup(args)
     if args.impl == "reference":
         res = run_reference(args, rank, world)
