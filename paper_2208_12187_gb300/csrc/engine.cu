@@ -940,7 +940,9 @@ int gbfit_autotune(int model_id, int precision, int64_t m_max, int64_t points_pe
                     std::vector<FitResult> hr;
                     std::vector<FitDesc> hdc = hd;
                     e = cudaEventRecord(e0, s);
-                    if (e == cudaSuccess && (rc = run_fits(c, builtin_kernels(), precision, hdc, p0s, hr, s, nullptr))) return cleanup(rc);
+                    const KernelSet* kst = nullptr;
+                    if ((rc = kernels_for_model(model_id, &kst))) return cleanup(rc);
+                    if (e == cudaSuccess && (rc = run_fits(c, kst, precision, hdc, p0s, hr, s, nullptr))) return cleanup(rc);
                     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
                     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);

@@ -153,8 +153,30 @@ bool model_shape(int id, int* n, int* dims) {
     return true;
 }
 
+// A built-in model's own kernel set: the mixed loop kernel compiled for that
+// model alone, the all-model FP64 kernel (ids -1 - model keep the engine's
+// cached graphs apart from the registry's).  Models without a single-model
+// instantiation use the registry's set.
+const KernelSet* builtin_single_kernels(int model) {
+    static std::once_flag once[GBFIT_NUM_MODELS];
+    static KernelSet k[GBFIT_NUM_MODELS];
+    std::call_once(once[model], [model] {
+        const KernelSet* all = builtin_kernels();
+        k[model] = *all;
+        const void* f = kernel_fit_loop_single_mixed(model);
+        const int b = f ? blocks_per_sm_single_mixed(model) : 0;
+        // the single-model grid must not exceed the all-model kernel's (both fit its scratch)
+        if (f && b >= 1 && b <= all->blocks_per_sm[PREC_MIXED]) {
+            k[model].id = -1 - model;
+            k[model].fit_loop[PREC_MIXED] = f;
+            k[model].blocks_per_sm[PREC_MIXED] = b;
+        }
+    });
+    return &k[model];
+}
+
 int kernels_for_model(int id, const KernelSet** out) {
-    if (id >= 0 && id < GBFIT_NUM_MODELS) { *out = builtin_kernels(); return GBFIT_OK; }
+    if (id >= 0 && id < GBFIT_NUM_MODELS) { *out = builtin_single_kernels(id); return GBFIT_OK; }
     int k = id - GBFIT_USER_MODEL_BASE;
     if (k < 0 || k >= GBFIT_MAX_USER_MODELS) return fail(GBFIT_E_INVALID_ARG, "unknown model %d", id);
     std::lock_guard<std::mutex> g(g_um_mu);
