@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gbfit.h"
 #include "kernels.cuh"
 #include "models.cuh"
@@ -51,6 +53,16 @@ int fail(int code, const char* fmt, ...) {
 }  // namespace
 
 namespace gbfit {
+
+// NVTX ranges around each call and its phases (staging, the loop launch, the
+// result copy; the server's retire / admit / launch), for timelines in
+// Nsight tools; free when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 int set_error(int code, const char* msg) {
     g_err = msg;
     return code;
@@ -357,6 +369,7 @@ double guard_value(double v, double dflt) { return v > 0.0 ? v : dflt; }
 // job buffer, one loop-kernel launch, one device-to-host copy of the results.
 int run_fits(Ctx* c, const KernelSet* ks, int prec, std::vector<FitDesc>& hd, const std::vector<std::vector<double>>& p0s,
              std::vector<FitResult>& hr, cudaStream_t s, int* rounds_out) {
+    NvtxRange nv("gbfit.run_fits");
     const auto t_host0 = std::chrono::steady_clock::now();
     size_t nf = hd.size();
     size_t ntiles = 0, ngroups = 0;
@@ -419,7 +432,10 @@ int run_fits(Ctx* c, const KernelSet* ks, int prec, std::vector<FitDesc>& hd, co
             CUDA_TRY(cudaEventCreate(&e1));
             CUDA_TRY(cudaEventRecord(e0, s));
         }
-        CUDA_TRY(cudaGraphLaunch(ex, s));
+        {
+            NvtxRange nvl("gbfit.loop_launch");
+            CUDA_TRY(cudaGraphLaunch(ex, s));
+        }
         if (g_profiling) {
             CUDA_TRY(cudaEventRecord(e1, s));
             CUDA_TRY(cudaEventSynchronize(e1));
@@ -469,6 +485,7 @@ struct Staged {
 
 int stage_data(Ctx* c, const void* x, size_t xbytes, const void* y, size_t ybytes, const void* sg, size_t sbytes,
                cudaStream_t s, Staged* out) {
+    NvtxRange nv("gbfit.stage_data");
     bool hx = x && !is_device_ptr(x), hy = !is_device_ptr(y), hsg = sg && !is_device_ptr(sg);
     out->x = x; out->y = y; out->sigma = sg;
     size_t need = (hx ? xbytes + 256 : 0) + (hy ? ybytes + 256 : 0) + (hsg ? sbytes + 256 : 0);
@@ -541,6 +558,7 @@ int set_data(Ctx* c, FitDesc& d, const void* x, const void* x2, const void* y, c
 // points and reducing rows of X [h - y, J].  One D2H read of the factor's
 // status word (a synchronisation) before the fit.
 int stage_cov(Ctx* c, FitDesc& d, const double* cov, int64_t m, int n, cudaStream_t s) {
+    NvtxRange nv("gbfit.stage_cov");
     bool ch = false;
     int rc;
     const size_t mp = cov_padded((int)m);
@@ -1481,6 +1499,7 @@ static void server_release(gbfit_server* s, int k) {
 }
 
 static int server_retire(gbfit_server* s) {
+    NvtxRange nv("gbfit.server_retire");
     // which resident fits finished: the `run` word of every slot's state
     int* flags = (int*)(s->hbuf + s->L->end + (size_t)s->max_slots * 4 + 256);
     CUDA_TRY(cudaMemcpy2DAsync(flags, sizeof(int), s->job + s->L->state + offsetof(FitState, run), sizeof(FitState),
@@ -1520,6 +1539,7 @@ static int server_retire(gbfit_server* s) {
 
 int gbfit_server_step(gbfit_server* s, int* n_active, int* n_queued) {
     if (!s) return fail(GBFIT_E_INVALID_ARG, "server is NULL");
+    NvtxRange nv("gbfit.server_step");
     std::lock_guard<std::mutex> g(s->mu);
     int rc;
     if ((rc = server_retire(s))) return rc;

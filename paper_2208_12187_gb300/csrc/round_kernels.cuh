@@ -288,6 +288,9 @@ struct RingShape {
     static constexpr int SX = 0, SX2 = 1;                                   // slots (when present)
     static constexpr int SY = LAYOUT == X_GRID ? 0 : LAYOUT == X_SOA2 ? 2 : 1;
     static constexpr int SS = SY + 1;
+    // the implicit grid tracks each thread's pixel by advancing 2 x EVAL_THREADS
+    // points per step: a chunk must be a whole number of such steps
+    static_assert(LAYOUT != X_GRID || CH % (2 * EVAL_THREADS) == 0, "grid chunks must be multiples of 512 points");
 };
 constexpr long long MBAR_SPIN_LIMIT = 1ll << 22;     // bounded waits (error flag past the limit)
 
