@@ -57,14 +57,15 @@ M = W * H
 TOL = dict(ftol=1e-10, xtol=1e-10, gtol=1e-10)
 # Algorithmic work of one evaluation pass per point, rotated 2D Gaussian, mixed
 # precision, implicit grid with sigma: bytes read (y, sigma: FP32) and FP32
-# FLOPs (FMA = 2) of model value, cancellation-free difference, Jacobian row
-# and the Gram / gradient / cost accumulation.
-# Count of the current formulation (FFMA = 2, FADD / FMUL = 1, exp / rcp
-# on the MUFU not counted): model value, difference form and Jacobian row 86,
-# weights, residuals and the Gram / gradient / cost / actual-reduction /
-# (w h)^2 accumulation 90.
+# FLOPs (FFMA = 2, FADD / FMUL = 1, exp / rcp on the MUFU not counted).
+# Difference form (trials near convergence): model value, cancellation-free
+# difference and Jacobian row 86; weights, residuals and the Gram / gradient /
+# cost / actual-reduction accumulation 90.  Direct form (a fit's first
+# evaluation and wide trials): model value and Jacobian row at the trial
+# point 40; weights and residual 10; Gram / gradient / cost / (w h)^2 sums 74.
 BYTES_PER_POINT = 8
 FLOPS_PER_POINT = 176
+FLOPS_PER_POINT_DIRECT = 124
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 L2_FLUSH_BYTES = 256 << 20
@@ -84,7 +85,7 @@ class L2Flush:
 # the headline workload, 5 passes) from the ncu capture summarised in
 # profiles/fit_loop_mixed_gauss2d_1024.md; None whenever the kernel has
 # changed since the capture.
-TRAFFIC_BYTES_PER_LAUNCH = 8.6725e6
+TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 def measured_peaks():
@@ -98,12 +99,13 @@ def measured_peaks():
         return 6800.0, "fallback (no MEASURED_PEAKS.json)"
 
 
-# Algorithmic work per point of one fused evaluation pass (model value,
-# cancellation-free difference, Jacobian row, residual, Gram / gradient /
-# cost / actual-reduction / (w h)^2 sums; FMA = 2 FLOP, MUFU not counted):
-# 1D Gaussian + offset on x, y FP32 (no sigma): 35 model + 38 accumulation;
-# rotated 2D Gaussian on the grid with sigma: 86 model + 90 accumulation.
-PASS_WORK = {"gauss1d_xy": (8, 73), "gauss2d_grid_sigma": (8, 176)}
+# Algorithmic work per point of one fused evaluation pass at fixed p
+# (gbfit_evaluate: a first evaluation, so the direct form): model value and
+# Jacobian row, residual, Gram / gradient / cost / (w h)^2 sums; FMA = 2 FLOP,
+# MUFU not counted.  1D Gaussian + offset on x, y FP32 (no sigma): 12 model +
+# 28 residual and accumulation; rotated 2D Gaussian on the grid with sigma:
+# 40 model + 10 weights and residual + 74 accumulation.
+PASS_WORK = {"gauss1d_xy": (8, 40), "gauss2d_grid_sigma": (8, FLOPS_PER_POINT_DIRECT)}
 # Plain FP64 pass (1D Gaussian on x, y FP64): 16 bytes per point; FP64
 # instructions per point counted by ncu (profiles/eval_fp64_gauss1d_5e7.md).
 FP64_PEAK_GFMA = 590.0        # FP64 FMA rate measured on this machine's GB300 (probe kernel, 1/62 of FP32)
@@ -390,14 +392,17 @@ def run_ours(args, rank, local, world):
     gbfit.set_profiling(False)
     launches_p = max(sp["eval_launches"], 1)
     avg_ms = sp["eval_ms"] / launches_p
-    flops_per_launch = M * FLOPS_PER_POINT * passes / launches_p
+    # each fit's first evaluation and its wide trials run the direct form, the rest the difference form
+    direct = launches_p + sp["phase_cycles"]["n_wide"]
+    flops_per_launch = M * (FLOPS_PER_POINT_DIRECT * direct + FLOPS_PER_POINT * (passes - direct)) / launches_p
     achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
     busy = sp["loop_busy_ms"] / max(sp["loop_busy_ms"] + sp["loop_wait_ms"], 1e-12)
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
             "kernel": "fit_loop_kernel<mixed> (rotated 2D Gaussian, grid, sigma; one launch per fit)",
-            "flops_per_point": FLOPS_PER_POINT, "bytes_per_point": BYTES_PER_POINT,
-            "passes_per_launch": passes / launches_p, "flops_per_launch": flops_per_launch,
+            "flops_per_point": {"difference_form": FLOPS_PER_POINT, "direct_form": FLOPS_PER_POINT_DIRECT},
+            "bytes_per_point": BYTES_PER_POINT, "passes_per_launch": passes / launches_p,
+            "direct_form_passes_per_launch": direct / launches_p, "flops_per_launch": flops_per_launch,
             "avg_launch_us": avg_ms * 1e3,
             "cta_time_in_work_frac": busy,
             "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (unit counts and max clock)"}

@@ -496,7 +496,10 @@ typedef struct gbfit_stats {
                                  global timer, per round of the fit's owner CTA): 24 round
                                  (barrier exit to barrier arrival), 25 owner's wait for the
                                  group sums, 26 barrier (arrival to exit), 27 launch start
-                                 to the first round (once per fit); 28-31 spare */
+                                 to the first round (once per fit); 28 evaluations in FP64
+                                 by a mixed fit (count), 29-30 precision-guard escalations
+                                 and FP64 finishes (count), 31 wide trials evaluated in the
+                                 direct form (count) */
     double host_ms;           /* host wall time inside the run of fits (job set-up, launch,
                                  wait for the device, result copy)                    */
     double loop_busy_ms;      /* loop kernel, summed over CTAs: time in rounds' work    */

@@ -19,7 +19,11 @@ enum WKind { W_NONE = 0, W_ARRAY = 1, W_SIGMA = 2 };
 enum RunState { RS_RUNNING = 0, RS_DONE = 1 };
 // PH_REINIT: the fit's current point is evaluated again in FP64 (precision
 // guard of the mixed path); the fit then continues with FP64 passes.
-enum Phase { PH_INIT = 0, PH_TRIAL = 1, PH_REINIT = 2 };
+// PH_WIDE: a trial of the mixed path whose predicted reduction is at least
+// WIDE_PRED_FRAC of f, evaluated in the direct form (no difference); its
+// actual reduction is f - f' of the two FP32-evaluated costs.
+enum Phase { PH_INIT = 0, PH_TRIAL = 1, PH_REINIT = 2, PH_WIDE = 3 };
+constexpr double WIDE_PRED_FRAC = 1e-2;
 enum Loss { LOSS_LINEAR = 0, LOSS_SOFT_L1, LOSS_HUBER, LOSS_CAUCHY, LOSS_ARCTAN };
 // pass-constant slots holding the robust loss's C^2 and 1/C^2
 constexpr int PF_C2 = PF - 1, PF_IC2 = PF - 2, PD_C2 = PD - 1, PD_IC2 = PD - 2;

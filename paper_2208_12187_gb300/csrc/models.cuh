@@ -12,6 +12,12 @@
 //                  The actual reduction of Eq. accuracy is then accumulated as
 //                  sum dr (2 r + dr), which keeps full relative accuracy when
 //                  f(p) - f(p') is many orders below f (near convergence).
+//   direct (FP32, packed models): value and partials at p' alone.  It serves
+//                  evaluations that need no difference: a fit's first one
+//                  (p' = p; the same bits as the mixed form's) and trial
+//                  points whose predicted reduction is a large fraction of
+//                  f, where f - f' from two FP32-evaluated costs resolves the
+//                  ratio of Eq. accuracy well enough.
 // Pass constants are prepared once per pass from FP64 parameters:
 //   plain: pd[] (doubles) from p'.
 //   mixed: pf[] (floats) from float images of p, p' and of the FP64
@@ -155,6 +161,7 @@ struct MGauss1D {
         pf[7] = kt; pf[8] = P.xt[0]; pf[9] = P.dx[0]; pf[10] = P.dx[3];
         pf[11] = P.xt[0] * 2.0f * kt;                      // A'/s'^2
         pf[12] = P.xt[0] * 2.0f * kt / st;                 // A'/s'^3
+        pf[13] = P.xt[3];                                  // c'
     }
     __device__ static void eval_mixed(const float* pf, float X, float, float& hb, float& dh, float* J) {
         float d = (X - pf[1]) - pf[2];
@@ -181,6 +188,16 @@ struct MGauss1D {
         float2 En, dE;
         exp_shift2(E, mul2(bc(pf[7]), mul2(dn, dn)), dq, En, dE);
         dh = fma2(bc(pf[0]), dE, fma2(bc(pf[9]), En, bc(pf[10])));
+        float2 t = mul2(En, dn);
+        J[0] = En; J[1] = mul2(bc(pf[11]), t); J[2] = mul2(bc(pf[12]), mul2(t, dn)); J[3] = bc(1.0f);
+    }
+    // value and partials at the trial point alone (direct form, no
+    // difference): the same operations as the trial side of eval_mixed2, so
+    // that at a first evaluation (trial = base) both forms give the same bits
+    __device__ static void eval_direct2(const float* pf, float2 X, float2, float2& h, float2* J) {
+        float2 dn = sub2(sub2(sub2(X, bc(pf[1])), bc(pf[2])), bc(pf[5]));
+        float2 En = expn2(mul2(bc(pf[7]), mul2(dn, dn)));
+        h = fma2(bc(pf[8]), En, bc(pf[13]));
         float2 t = mul2(En, dn);
         J[0] = En; J[1] = mul2(bc(pf[11]), t); J[2] = mul2(bc(pf[12]), mul2(t, dn)); J[3] = bc(1.0f);
     }
@@ -212,6 +229,7 @@ struct MDexp {
         pf[9] = P.dx[0]; pf[10] = P.dx[2]; pf[11] = P.dx[4];
         pf[12] = P.xt[0] * k1n * k1n; pf[13] = P.xt[2] * k2n * k2n;
         pf[14] = k1n; pf[15] = k2n;
+        pf[16] = P.xt[4];                                   // c'
     }
     __device__ static void eval_mixed(const float* pf, float X, float, float& hb, float& dh, float* J) {
         float q1 = X * pf[1], q2 = X * pf[3];
@@ -231,6 +249,13 @@ struct MDexp {
         exp_shift2(e1, mul2(X, bc(pf[14])), mul2(X, bc(pf[5])), e1n, de1);
         exp_shift2(e2, mul2(X, bc(pf[15])), mul2(X, bc(pf[6])), e2n, de2);
         dh = fma2(bc(pf[0]), de1, fma2(bc(pf[9]), e1n, fma2(bc(pf[2]), de2, fma2(bc(pf[10]), e2n, bc(pf[11])))));
+        J[0] = e1n; J[1] = mul2(bc(pf[12]), mul2(X, e1n)); J[2] = e2n; J[3] = mul2(bc(pf[13]), mul2(X, e2n));
+        J[4] = bc(1.0f);
+    }
+    // direct form at the trial point (the trial side of eval_mixed2)
+    __device__ static void eval_direct2(const float* pf, float2 X, float2, float2& h, float2* J) {
+        float2 e1n = expn2(mul2(X, bc(pf[14]))), e2n = expn2(mul2(X, bc(pf[15])));
+        h = fma2(bc(pf[7]), e1n, fma2(bc(pf[8]), e2n, bc(pf[16])));
         J[0] = e1n; J[1] = mul2(bc(pf[12]), mul2(X, e1n)); J[2] = e2n; J[3] = mul2(bc(pf[13]), mul2(X, e2n));
         J[4] = bc(1.0f);
     }
@@ -292,6 +317,7 @@ struct MGauss2D {
         pf[18] = P.xt[0]; pf[19] = P.dx[0]; pf[20] = P.dx[6];
         pf[21] = ct; pf[22] = st;
         pf[23] = 2.0f * kat / sxt; pf[24] = 2.0f * kbt / syt;
+        pf[25] = P.xt[6];                                   // c'
     }
     // prep_mixed on a whole warp: the four angles' sin/cos and the four
     // widths' 1/(2 w^2) (and 2 k / w) in lanes 0-3 at once, the rest on
@@ -325,6 +351,7 @@ struct MGauss2D {
             pf[18] = P.xt[0]; pf[19] = P.dx[0]; pf[20] = P.dx[6];
             pf[21] = ct; pf[22] = st;
             pf[23] = tmp[14]; pf[24] = tmp[15];
+            pf[25] = P.xt[6];
         }
         __syncwarp();
     }
@@ -381,6 +408,27 @@ struct MGauss2D {
         J[5] = mul2(mul2(mul2(Q, bc(2.0f * (pf[15] - pf[14]))), un), vn);
         J[6] = bc(1.0f);
     }
+    // direct form at the trial point: u' = (X - x0') cos th' + (Y - y0') sin th'
+    // and v' from the base offsets and the shifts ku, kv (at a first
+    // evaluation ku = kv = 0 and th' = th: the bits of eval_mixed2's u, v)
+    __device__ static void eval_direct2(const float* pf, float2 X, float2 Y, float2& h, float2* J) {
+        float2 dx = sub2(sub2(X, bc(pf[1])), bc(pf[2]));
+        float2 dy = sub2(sub2(Y, bc(pf[3])), bc(pf[4]));
+        float2 un = fma2(dx, bc(pf[21]), fma2(dy, bc(pf[22]), bc(pf[12])));
+        float2 vn = fma2(dy, bc(pf[21]), fma2(dx, bc(-pf[22]), bc(pf[13])));
+        float2 qn = fma2(mul2(bc(pf[14]), un), un, mul2(mul2(bc(pf[15]), vn), vn));
+        float2 En = expn2(qn);
+        h = fma2(bc(pf[18]), En, bc(pf[25]));
+        float2 Q = mul2(bc(pf[18]), En);
+        float2 au = mul2(bc(2.0f * pf[14]), un), bv = mul2(bc(2.0f * pf[15]), vn);
+        J[0] = En;
+        J[1] = mul2(Q, fma2(au, bc(pf[21]), mul2(bv, bc(-pf[22]))));
+        J[2] = mul2(Q, fma2(au, bc(pf[22]), mul2(bv, bc(pf[21]))));
+        J[3] = mul2(mul2(mul2(Q, bc(pf[23])), un), un);
+        J[4] = mul2(mul2(mul2(Q, bc(pf[24])), vn), vn);
+        J[5] = mul2(mul2(mul2(Q, bc(2.0f * (pf[15] - pf[14]))), un), vn);
+        J[6] = bc(1.0f);
+    }
 };
 
 // ------------------------------------------------------------------ poly2
@@ -391,6 +439,7 @@ struct MPoly2 {
     static constexpr bool WARP_PREP = false;
     static constexpr int PACK = 0;
     __device__ static void eval_mixed2(const float*, float2, float2, float2&, float2&, float2*) {}
+    __device__ static void eval_direct2(const float*, float2, float2, float2&, float2*) {}
     __device__ static void prep_plain(const double* p, double* pd) { pd[0] = p[0]; pd[1] = p[1]; pd[2] = p[2]; }
     __device__ static void eval_plain(const double* pd, double X, double, double& h, double* J) {
         h = fma(fma(pd[2], X, pd[1]), X, pd[0]);

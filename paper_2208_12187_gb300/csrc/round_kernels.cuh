@@ -191,7 +191,10 @@ __device__ __forceinline__ void accum_point(const float* pfl, const double* pdl,
 // Two points at once with packed FP32 (mixed precision): model, residual
 // and weights packed; accumulators packed (ACC = float2, two partial sums
 // per slot) or scalar (ACC = float, both points added to one sum).
-template <class M, int WK, typename ACC>
+// DIR: the direct form (value and partials at the trial point alone, no
+// difference): slot NT+N+1 takes sum (w h)^2 at a first evaluation (check)
+// and nothing otherwise (the step then forms f - f' itself).
+template <class M, int WK, typename ACC, bool DIR = false>
 __device__ __forceinline__ void accum_point2(const float* pfl, float2 X, float2 Y, float2 yv, float2 sv, bool check,
                                              ACC (&acc)[n_acc(M::N, PREC_MIXED)], int& bad) {
     constexpr int N = M::N;
@@ -204,17 +207,22 @@ __device__ __forceinline__ void accum_point2(const float* pfl, float2 X, float2 
     if (check && !(isfinite(X.x) && isfinite(X.y) && isfinite(Y.x) && isfinite(Y.y) && isfinite(yv.x) &&
                    isfinite(yv.y))) bad = 1;
     float2 hb, dh, J[N];
-    M::eval_mixed2(pfl, X, Y, hb, dh, J);
+    if constexpr (DIR) {
+        M::eval_direct2(pfl, X, Y, hb, J);
+        dh = bc(0.0f);
+    } else {
+        M::eval_mixed2(pfl, X, Y, hb, dh, J);
+    }
     float2 r = sub2(hb, yv), dr = dh, wh = hb;
     if (WK == W_SIGMA) {
         r = mul2(w, r);
-        dr = mul2(w, dr);
+        if (!DIR) dr = mul2(w, dr);
         wh = mul2(w, hb);
 #pragma unroll
         for (int a = 0; a < N; ++a) J[a] = mul2(w, J[a]);
     }
-    float2 rn = add2(r, dr);
-    float2 dc = mul2(dr, fma2(bc(2.0f), r, dr));
+    const float2 rn = DIR ? r : add2(r, dr);
+    const float2 dc = DIR ? bc(0.0f) : mul2(dr, fma2(bc(2.0f), r, dr));
     if constexpr (std::is_same<ACC, float2>::value) {
         int idx = 0;
 #pragma unroll
@@ -224,7 +232,7 @@ __device__ __forceinline__ void accum_point2(const float* pfl, float2 X, float2 
 #pragma unroll
         for (int a = 0; a < N; ++a) acc[NT + a] = fma2(J[a], rn, acc[NT + a]);
         acc[NT + N] = fma2(rn, rn, acc[NT + N]);
-        acc[NT + N + 1] = check ? fma2(wh, wh, acc[NT + N + 1]) : add2(dc, acc[NT + N + 1]);
+        if (!DIR || check) acc[NT + N + 1] = check ? fma2(wh, wh, acc[NT + N + 1]) : add2(dc, acc[NT + N + 1]);
     } else {
         int idx = 0;
 #pragma unroll
@@ -237,7 +245,8 @@ __device__ __forceinline__ void accum_point2(const float* pfl, float2 X, float2 
 #pragma unroll
         for (int a = 0; a < N; ++a) acc[NT + a] = fmaf(J[a].y, rn.y, fmaf(J[a].x, rn.x, acc[NT + a]));
         acc[NT + N] = fmaf(rn.y, rn.y, fmaf(rn.x, rn.x, acc[NT + N]));
-        acc[NT + N + 1] = check ? fmaf(wh.y, wh.y, fmaf(wh.x, wh.x, acc[NT + N + 1])) : acc[NT + N + 1] + (dc.x + dc.y);
+        if (!DIR || check)
+            acc[NT + N + 1] = check ? fmaf(wh.y, wh.y, fmaf(wh.x, wh.x, acc[NT + N + 1])) : acc[NT + N + 1] + (dc.x + dc.y);
     }
 }
 
@@ -344,7 +353,7 @@ struct RingState {
     long long wait_cycles;       // thread 0: cycles spent waiting for chunks of the current tile
 };
 
-template <class M, int LAYOUT, int WK>
+template <class M, int LAYOUT, int WK, bool DIR = false>
 __device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0, int64_t i1, bool check,
                                  float (&acc)[n_acc(M::N, PREC_MIXED)], int& bad, RingState& R) {
     using RS = RingShape<LAYOUT, WK>;
@@ -413,7 +422,7 @@ __device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0,
                 float2 X = *reinterpret_cast<const float2*>(B + RS::SX * CH + k);
                 float2 yv = *reinterpret_cast<const float2*>(B + RS::SY * CH + k);
                 float2 sv = (WK == W_SIGMA) ? *reinterpret_cast<const float2*>(B + RS::SS * CH + k) : bc(1.0f);
-                accum_point2<M, WK, float2>(pfl, X, bc(0.0f), yv, sv, check, acc2, bad);
+                accum_point2<M, WK, float2, DIR>(pfl, X, bc(0.0f), yv, sv, check, acc2, bad);
             }
         } else if constexpr (PK2) {
             for (int k = 2 * t; k < cnt; k += 2 * EVAL_THREADS) {
@@ -432,7 +441,7 @@ __device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0,
                 }
                 float2 yv = *reinterpret_cast<const float2*>(B + RS::SY * CH + k);
                 float2 sv = (WK == W_SIGMA) ? *reinterpret_cast<const float2*>(B + RS::SS * CH + k) : bc(1.0f);
-                accum_point2<M, WK, float>(pfl, X, Y, yv, sv, check, acc, bad);
+                accum_point2<M, WK, float, DIR>(pfl, X, Y, yv, sv, check, acc, bad);
             }
         } else
 #pragma unroll 2
@@ -559,11 +568,16 @@ __device__ void eval_tile_dispatch(const RoundSmem& sm, int64_t i0, int64_t i1, 
 #undef RB_CASE
         return;
     }
-    // mixed precision on FP32 data streams through the bulk-copy ring
+    // mixed precision on FP32 data streams through the bulk-copy ring; packed
+    // models evaluate a first evaluation and a wide trial in the direct form
+    const bool dir = M::PACK != 0 && sm.flag[1] != PH_TRIAL;
 #define GB_CASE(LAY, WKV)                                                                              \
     if constexpr (PREC == PREC_MIXED && WKV != W_ARRAY) {                                              \
-        if (!f64) tile_points_ring<M, LAY, WKV>(d, pfl, i0, i1, check, acc, bad, R);                   \
-        else tile_points<M, PREC, double, LAY, WKV>(d, pfl, pdl, i0, i1, check, acc, bad);             \
+        if (f64) tile_points<M, PREC, double, LAY, WKV>(d, pfl, pdl, i0, i1, check, acc, bad);         \
+        else if constexpr (M::PACK != 0) {                                                             \
+            if (dir) tile_points_ring<M, LAY, WKV, true>(d, pfl, i0, i1, check, acc, bad, R);          \
+            else tile_points_ring<M, LAY, WKV, false>(d, pfl, i0, i1, check, acc, bad, R);             \
+        } else tile_points_ring<M, LAY, WKV>(d, pfl, i0, i1, check, acc, bad, R);                      \
     } else {                                                                                           \
         if (f64) tile_points<M, PREC, double, LAY, WKV>(d, pfl, pdl, i0, i1, check, acc, bad);         \
         else tile_points<M, PREC, float, LAY, WKV>(d, pfl, pdl, i0, i1, check, acc, bad);              \

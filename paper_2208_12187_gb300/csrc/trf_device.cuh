@@ -55,7 +55,7 @@ enum TracePhase { TR_TILE = 0, TR_COMBINE, TR_LOGIC, TR_EIGEN, TR_C_FENCE, TR_ST
                   TR_C_GROUP, TR_C_FINAL, TR_E_WARM, TR_E_J32, TR_E_NS, TR_E_RR, TR_E_SWEEPS, TR_E_REFINES,
                   TR_GN, TR_N_GN, TR_N_EIG, TR_N_ALG2IT, TR_N_BOUNDED, TR_PRE_TILE, TR_TILE_LOOP, TR_RING_WAIT,
                   TR_ROUND_NS, TR_OWNER_WAIT_NS, TR_BARRIER_NS, TR_START_NS, TR_N_EVAL64, TR_N_ESC, TR_N_FIN,
-                  TR_RES31 };
+                  TR_N_WIDE };
 
 // Shared-memory workspace of the warp that runs one fit's step.
 struct TrfSmem {

@@ -643,6 +643,26 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
     const bool e64 = PREC == PREC_MIXED && cst->eval64;
     const bool guard_on = PREC == PREC_MIXED && !e64 && (d.guard_cond < INFINITY || d.guard_floor < INFINITY);
     if (e64 && t == 0) trace_bump(st->trace, TR_N_EVAL64, 1);
+    // data flags raised by the pass's tiles (bit 0: invalid data at the first
+    // evaluation, bit 1: a bounded bulk-copy wait gave up), read from L2: the
+    // prefetched state copy can predate other CTAs' flags
+    const int bad = __ldcg(&st->bad_data);
+
+    // ================= evaluation only (gbfit_evaluate): the sums at p are the result
+    if (d.eval_only) {
+        if (t < n) res->popt[t] = cst->x[t];
+        for (int k = t; k < KMAX; k += EVAL_THREADS) res->tot[k] = S.tot[k];
+        if (t == 0) {
+            const int status = (bad & 1) ? FS_INVALID_DATA : (bad & 2) ? FS_NUMERICAL : FS_MAX_NFEV;
+            res->cost = 0.5 * S.tot[NT + n]; res->nfev = 1; res->njev = 1; res->fit_status = status;
+            st->f = res->cost; st->nfev = 1; st->njev = 1;
+            st->run = RS_DONE; st->fit_status = status;
+            atomicSub(running, 1);
+        }
+        __syncthreads();
+        if (t < 32) res->trace[t] = double(__ldcg(st->trace + t));
+        return;
+    }
 
     // ================= phase 1 (warp 0): accept / reject, termination tests
     if (warp == 0) {
@@ -668,12 +688,13 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             if (reinit) factor_valid = 0;
             bool fin = (l >= NT + n + 1 || isfinite(S.tot[l])) && (l + 32 >= NT + n + 1 || isfinite(S.tot[l + 32]));
             fin = __all_sync(FULL, fin);
-            if (init && cst->bad_data) status = FS_INVALID_DATA;
-            else if (!fin) status = FS_NUMERICAL;
+            if (init && (bad & 1)) status = FS_INVALID_DATA;
+            else if (!fin || (bad & 2)) status = FS_NUMERICAL;
         } else {
             nfev += 1;
             double f_new = 0.5 * f2n;
-            double actual = mixed_pass ? -0.5 * S.tot[NT + n + 1] : f - f_new;
+            // mixed FP32 pass: the cancellation-free sum, except after a wide trial (direct form)
+            double actual = (mixed_pass && cst->phase != PH_WIDE) ? -0.5 * S.tot[NT + n + 1] : f - f_new;
             double pred = cst->predicted;
             double gamma = (isfinite(f_new) && isfinite(actual) && pred > 0.0) ? actual * rcp64(pred) : -INFINITY;
             bool accepted;
@@ -693,6 +714,7 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             if (ftol_ok && xtol_ok) status = FS_FTOL_XTOL;
             else if (ftol_ok) status = FS_FTOL;
             else if (xtol_ok) status = FS_XTOL;
+            if (bad & 2) status = FS_NUMERICAL;
         }
         // the Gram at the (new) current point, unpacked from its packed upper triangle
         {
@@ -1016,14 +1038,21 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             while (r >= n - a) { r -= n - a; ++a; }
             st->B[k] = S.B[a * 8 + a + r];
         }
+        // a trial whose predicted reduction is a large fraction of f is evaluated
+        // in the direct form (packed models, linear loss, mixed FP32 passes)
+        int packed = 0;
+        MS::dispatch(d.model, [&](auto m) { packed = decltype(m)::PACK; });
+        const bool wide = PREC == PREC_MIXED && !e64 && packed != 0 && d.loss == LOSS_LINEAR && !d.cov &&
+                          -qval >= WIDE_PRED_FRAC * S.sd[SD_F];
         if (l == 0) {
             st->f = S.sd[SD_F]; st->Delta = Delta; st->alpha = alpha; st->nfev = S.si[SI_NFEV];
             st->njev = S.si[SI_NJEV]; st->predicted = -qval;
             st->step_norm = w_norm; st->s_norm = s_norm; st->xtol_thr = d.xtol * (d.xtol + x_norm);
-            st->phase = PH_TRIAL; st->last_kind = kind; st->alg2_iters = a2it;
+            st->phase = wide ? PH_WIDE : PH_TRIAL; st->last_kind = kind; st->alg2_iters = a2it;
             st->cov_stage = 0;
             trace_bump(st->trace, TR_N_ALG2IT, a2it);
             trace_bump(st->trace, TR_N_BOUNDED, kind != 0);
+            trace_bump(st->trace, TR_N_WIDE, wide ? 1 : 0);
         }
         __syncwarp();
     }

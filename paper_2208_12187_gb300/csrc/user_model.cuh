@@ -334,6 +334,7 @@ struct MUser {
         for (int j = 0; j < N; ++j) J[j] = r.g[j];
     }
     __device__ static void eval_mixed2(const float*, float2, float2, float2&, float2&, float2*) {}
+    __device__ static void eval_direct2(const float*, float2, float2, float2&, float2*) {}
 };
 
 // A model set of one user model: every fit of a launch is that model.

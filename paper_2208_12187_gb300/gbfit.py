@@ -73,7 +73,7 @@ PHASES = ["tile", "combine", "logic", "eigen", "comb_fence", "step", "prep", "fi
           "eig_warm", "eig_j32", "eig_ns", "eig_rr", "j32_sweeps", "refine_passes", "gn_path", "n_gn", "n_eig",
           "n_alg2_iters", "n_bounded_nonfull", "pre_tile", "tile_loop", "ring_wait",
           "round_ns", "owner_wait_ns", "barrier_ns", "start_ns", "n_eval64", "n_guard_escalated",
-          "n_guard_finished", "spare31"]
+          "n_guard_finished", "n_wide"]
 
 
 class ServerConfig(ctypes.Structure):
