@@ -517,8 +517,11 @@ int gbfit_stats_get(gbfit_stats* out);
 /*
  * on = 1: each launch of the loop kernel (one per fit or batch call) is
  * bracketed by CUDA events on the call's stream and its time added to
- * gbfit_stats.eval_ms (one extra host synchronisation per call).
- * on = 0 (default): no events.  Results are identical.
+ * gbfit_stats.eval_ms (one extra host synchronisation per call).  A short
+ * hold kernel (60 us) is queued ahead of the start event, so that the host
+ * has submitted the launch by the time the event fires: the events time the
+ * kernel, not the host's submission.
+ * on = 0 (default): no events, no hold.  Results are identical.
  */
 int gbfit_set_profiling(int on);
 

@@ -39,6 +39,9 @@ thread_local std::string g_err;
 std::mutex g_stats_mu;
 gbfit_stats g_stats = {};
 int g_profiling = 0;
+// profiling: the stream is held this long before a timed launch's start event
+// (longer than the host's submission of the launch that follows it)
+constexpr unsigned long long PROFILE_HOLD_NS = 60000;
 
 int fail(int code, const char* fmt, ...) {
     char buf[512];
@@ -430,6 +433,8 @@ int run_fits(Ctx* c, const KernelSet* ks, int prec, std::vector<FitDesc>& hd, co
         if (g_profiling) {
             CUDA_TRY(cudaEventCreate(&e0));
             CUDA_TRY(cudaEventCreate(&e1));
+            // the GPU stays busy while the launch is submitted: the events time the kernel
+            CUDA_TRY(launch_hold(PROFILE_HOLD_NS, s));
             CUDA_TRY(cudaEventRecord(e0, s));
         }
         {

@@ -72,6 +72,27 @@ __global__ void tr_subproblem_kernel(int n, const double* B, const double* g, do
     if (l == 0) *alpha_out = alpha;
 }
 
+// Holds its stream for about ns nanoseconds (one thread on the global timer,
+// bounded by an iteration cap).  Queued ahead of a profiled launch, it keeps
+// the GPU busy while the host submits that launch, so that the launch's
+// start event fires when the launch can start and the event pair times the
+// kernel rather than the host's submission.
+__global__ void hold_kernel(unsigned long long ns) {
+    if (threadIdx.x != 0) return;
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (int it = 0; it < (1 << 20); ++it) {
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 >= ns) break;
+        __nanosleep(200);
+    }
+}
+
+cudaError_t launch_hold(unsigned long long ns, cudaStream_t s) {
+    hold_kernel<<<1, 32, 0, s>>>(ns);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ host-side handles
 void* kernel_eval_round(int prec) { return prec == PREC_MIXED ? kernel_eval_round_mixed() : kernel_eval_round_fp64(); }
 void* kernel_init_fits(int prec) { return prec == PREC_MIXED ? kernel_init_fits_mixed() : kernel_init_fits_fp64(); }

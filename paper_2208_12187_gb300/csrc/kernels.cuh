@@ -39,6 +39,8 @@ cudaError_t launch_cov_factor(double* A, double* W, double* X, double* Xc, float
 cudaError_t launch_tr_subproblem(int n, const double* B, const double* g, double Delta, double alpha0,
                                  double* p_out, double* alpha_out, double* lam_out, cudaStream_t s);
 cudaError_t launch_rcp64(const double* x, double* y, int64_t n, int blocks, cudaStream_t s);
+// Keeps the stream busy for about ns nanoseconds (profiling: queued before a timed launch).
+cudaError_t launch_hold(unsigned long long ns, cudaStream_t s);
 // The mixed loop kernel compiled for built-in model `model` alone (the 1D
 // Gaussian; null for the others) and its resident CTAs per SM
 // (kernels_single.cu).

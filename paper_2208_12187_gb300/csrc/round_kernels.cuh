@@ -194,18 +194,26 @@ __device__ __forceinline__ void accum_point(const float* pfl, const double* pdl,
 // DIR: the direct form (value and partials at the trial point alone, no
 // difference): slot NT+N+1 takes sum (w h)^2 at a first evaluation (check)
 // and nothing otherwise (the step then forms f - f' itself).
-template <class M, int WK, typename ACC, bool DIR = false>
+// Data checks (check: a first evaluation) ride on two running values: chk
+// = sum v * 0 over the checked values v (0 while every v is finite, NaN from
+// the first non-finite one on) and smin = min sigma; the caller tests them
+// once after its loop.  XY: the coordinates come from memory (not the grid).
+template <class M, int WK, typename ACC, bool DIR = false, bool XY = true>
 __device__ __forceinline__ void accum_point2(const float* pfl, float2 X, float2 Y, float2 yv, float2 sv, bool check,
-                                             ACC (&acc)[n_acc(M::N, PREC_MIXED)], int& bad) {
+                                             ACC (&acc)[n_acc(M::N, PREC_MIXED)], float2& chk, float& smin) {
     constexpr int N = M::N;
     constexpr int NT = n_tri(N);
     float2 w = bc(1.0f);
-    if (WK == W_SIGMA) {
-        if (check && !(sv.x > 0.0f && isfinite(sv.x) && sv.y > 0.0f && isfinite(sv.y))) bad = 1;
-        w = make_float2(__fdividef(1.0f, sv.x), __fdividef(1.0f, sv.y));
+    if (check) {
+        chk = fma2(yv, bc(0.0f), chk);
+        if (XY) chk = fma2(X, bc(0.0f), chk);
+        if (XY && M::DIM == 2) chk = fma2(Y, bc(0.0f), chk);
+        if (WK == W_SIGMA) {
+            chk = fma2(sv, bc(0.0f), chk);
+            smin = fminf(smin, fminf(sv.x, sv.y));
+        }
     }
-    if (check && !(isfinite(X.x) && isfinite(X.y) && isfinite(Y.x) && isfinite(Y.y) && isfinite(yv.x) &&
-                   isfinite(yv.y))) bad = 1;
+    if (WK == W_SIGMA) w = make_float2(__fdividef(1.0f, sv.x), __fdividef(1.0f, sv.y));
     float2 hb, dh, J[N];
     if constexpr (DIR) {
         M::eval_direct2(pfl, X, Y, hb, J);
@@ -344,9 +352,17 @@ __device__ __forceinline__ int arrive_acq_rel(int* ctr) {
     return old;
 }
 
+__device__ __forceinline__ unsigned atom_add_acq_rel_cta_shared(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(smem_addr(p)), "r"(v)
+                 : "memory");
+    return old;
+}
+
 struct RingState {
     unsigned long long* bar;     // [NST] full barriers (bulk-copy completion)
-    unsigned long long* empty;   // [NST] empty barriers (one arrival per warp when a stage is consumed)
+    unsigned* rel;               // [NST] per-stage release counters (one acq_rel add per warp per consumed chunk;
+                                 // the warp that completes a multiple of the warp count refills the stage)
     float* buf;                  // [NST][STAGE_FLOATS]
     unsigned seq;                // chunks consumed by this CTA so far (same in all threads)
     int* fail;                   // shared flag: a bounded wait gave up
@@ -379,13 +395,12 @@ __device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0,
     const int nch = (int)((nring + CH - 1) / CH);
     const int64_t a1 = a0 + nring;
     auto count = [&](int c) { return (int)min((int64_t)CH, nring - (int64_t)c * CH); };
-    // issue chunk c into its stage once every warp has released the stage's
-    // previous chunk (bounded wait; a timeout marks the ring failed)
+    // issue chunk c into its stage (free: at a tile's start every earlier
+    // chunk is consumed; later, the caller is the last warp to release it)
     auto issue = [&](int c) {
         unsigned g = R.seq + c;
         int s = g % NST;
         unsigned long long* bar = R.bar + s;
-        if (g >= (unsigned)NST && !mbar_wait(R.empty + s, ((g / NST) - 1) & 1)) { *R.fail = 1; return; }
         const unsigned nb = (unsigned)count(c) * sizeof(float);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(bar, nb * RS::NA);
@@ -407,6 +422,8 @@ __device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0,
     float2 acc2[PK ? K : 1];         // (the head's sums move in, so that acc[] is dead in the loop)
 #pragma unroll
     for (int k = 0; k < (PK ? K : 1); ++k) acc2[k] = make_float2(PK ? acc[k] : 0.0f, 0.0f);
+    float2 chk = bc(0.0f);           // data checks of the packed loops (accum_point2)
+    float smin = INFINITY;
     for (int c = 0; c < nch; ++c) {
         unsigned g = R.seq + c;
         int s = g % NST;
@@ -422,7 +439,7 @@ __device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0,
                 float2 X = *reinterpret_cast<const float2*>(B + RS::SX * CH + k);
                 float2 yv = *reinterpret_cast<const float2*>(B + RS::SY * CH + k);
                 float2 sv = (WK == W_SIGMA) ? *reinterpret_cast<const float2*>(B + RS::SS * CH + k) : bc(1.0f);
-                accum_point2<M, WK, float2, DIR>(pfl, X, bc(0.0f), yv, sv, check, acc2, bad);
+                accum_point2<M, WK, float2, DIR>(pfl, X, bc(0.0f), yv, sv, check, acc2, chk, smin);
             }
         } else if constexpr (PK2) {
             for (int k = 2 * t; k < cnt; k += 2 * EVAL_THREADS) {
@@ -441,7 +458,7 @@ __device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0,
                 }
                 float2 yv = *reinterpret_cast<const float2*>(B + RS::SY * CH + k);
                 float2 sv = (WK == W_SIGMA) ? *reinterpret_cast<const float2*>(B + RS::SS * CH + k) : bc(1.0f);
-                accum_point2<M, WK, float, DIR>(pfl, X, Y, yv, sv, check, acc, bad);
+                accum_point2<M, WK, float, DIR, LAYOUT != X_GRID>(pfl, X, Y, yv, sv, check, acc, chk, smin);
             }
         } else
 #pragma unroll 2
@@ -460,15 +477,22 @@ __device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0,
             accum_point<M, PREC_MIXED, WK>(pfl, nullptr, X, Y, yv, sv, check, acc, bad);
         }
         __syncwarp();
-        if ((t & 31) == 0) mbar_arrive(R.empty + s);      // this warp is done with the stage
-        if (t == 0 && c + NST < nch) issue(c + NST);
+        if ((t & 31) == 0) {
+            // this warp is done with the stage; the last of the CTA's warps
+            // to release it refills it with the chunk NST ahead (no warp waits)
+            const unsigned old = atom_add_acq_rel_cta_shared(R.rel + s, 1u);
+            if ((old + 1) % (EVAL_THREADS / 32) == 0 && c + NST < nch) issue(c + NST);
+        }
     }
     __syncthreads();
     if (*R.fail) {
         // give copies still in flight a bounded chance to land before leaving
         for (int c = 0; c < nch; ++c) { unsigned g = R.seq + c; mbar_wait(R.bar + (g % NST), (g / NST) & 1); }
+        if (t < NST) R.rel[t] = 0;      // warps that left early did not release their stages
+        __syncthreads();
     }
     R.seq += nch;
+    if (check && !(chk.x == 0.0f && chk.y == 0.0f && smin > 0.0f)) bad = 1;
     if constexpr (PK) {
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] = acc2[k].x + acc2[k].y;
@@ -481,7 +505,7 @@ __device__ void tile_points_ring(const FitDesc& d, const float* pfl, int64_t i0,
 struct RoundSmem {
     Engine eng;                        // the launch's engine record (kept out of registers)
     unsigned long long mbar[NST];
-    unsigned long long mbar_empty[NST];
+    unsigned ring_rel[NST];
     int ring_fail;
     FitDesc desc;
     long long t_mark, t_fence, t_group, t_loop;
@@ -920,7 +944,7 @@ __device__ __forceinline__ void stage_engine(RoundSmem& sm, const Engine* Ep) {
 template <int PREC>
 __device__ __forceinline__ void round_setup(RoundSmem& sm, float* ring_buf, RingState& R) {
     R.bar = sm.mbar;
-    R.empty = sm.mbar_empty;
+    R.rel = sm.ring_rel;
     R.buf = ring_buf;
     R.seq = 0;
     R.fail = &sm.ring_fail;
@@ -929,7 +953,7 @@ __device__ __forceinline__ void round_setup(RoundSmem& sm, float* ring_buf, Ring
         if (threadIdx.x == 0) {
             for (int s = 0; s < NST; ++s) {
                 mbar_init(&sm.mbar[s], 1);
-                mbar_init(&sm.mbar_empty[s], EVAL_THREADS / 32);
+                sm.ring_rel[s] = 0;
             }
             sm.ring_fail = 0;
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

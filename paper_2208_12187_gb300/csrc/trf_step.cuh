@@ -815,11 +815,11 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
                 esc = (cst->phase == PH_INIT) ? GUARD_ESC_INIT : GUARD_ESC_MID;
             // a finish: the floor estimate is above guard_floor, a parameter's
             // standard error is above GUARD_SE_REL of it, or the FP32
-            // iteration stopped on xtol (steps that shrink below xtol by
-            // rejections can stall it short of its own fixed point)
+            // iteration stopped on xtol alone (steps that shrink below xtol
+            // by rejections can stall it short of its own fixed point; a stop
+            // on ftol and xtol together ends on an accepted step, like ftol)
             else if (stt >= FS_GTOL && stt <= FS_FTOL_XTOL && d.guard_floor < INFINITY &&
-                     (!(floor_x <= d.guard_floor) || !(serel_x <= GUARD_SE_REL) || stt == FS_XTOL ||
-                      stt == FS_FTOL_XTOL))
+                     (!(floor_x <= d.guard_floor) || !(serel_x <= GUARD_SE_REL) || stt == FS_XTOL))
                 esc = GUARD_FINISH;
             S.si[SI_ESC] = esc;
             if (take) { st->floor_x = S.sd[SD_FLOOR]; st->serel_x = S.sd[SD_SEREL]; }
