@@ -83,9 +83,9 @@ class L2Flush:
         self.w.zero_()
 # DRAM bytes (read + write) per launch of the loop kernel (one whole fit of
 # the headline workload, 5 passes) from the ncu capture summarised in
-# profiles/fit_loop_mixed_gauss2d_1024.md; None whenever the kernel has
-# changed since the capture.
-TRAFFIC_BYTES_PER_LAUNCH = None
+# profiles/fit_loop_mixed_gauss2d_1024.md (8.66 MB read + 3.07 MB written);
+# None whenever the kernel has changed since the capture.
+TRAFFIC_BYTES_PER_LAUNCH = 11.73e6
 
 
 def measured_peaks():
@@ -109,6 +109,9 @@ PASS_WORK = {"gauss1d_xy": (8, 40), "gauss2d_grid_sigma": (8, FLOPS_PER_POINT_DI
 # Plain FP64 pass (1D Gaussian on x, y FP64): 16 bytes per point; FP64
 # instructions per point counted by ncu (profiles/eval_fp64_gauss1d_5e7.md).
 FP64_PEAK_GFMA = 590.0        # FP64 FMA rate measured on this machine's GB300 (probe kernel, 1/62 of FP32)
+# FP64 thread instructions per point of that pass (DFMA 25, DADD 8.1, DMUL 7 and the
+# rest, ncu InstructionStats of the 5e7-point capture), each one FP64 pipe issue
+FP64_INST_PER_POINT = 42.0
 
 
 def kernel_roofline(dev, flush):
@@ -152,10 +155,13 @@ def kernel_roofline(dev, flush):
         if m == 50_000_000:
             x64, y64 = x.double(), y.double()
             ms64 = timed(lambda: gbfit.evaluate(pr.model, x64, y64, pr.p0, precision="fp64"), reps=3)
+            pps = m / (ms64 / 1e3)
             out.append({"workload": "1D Gaussian + offset, x and y FP64, plain FP64 path", "m": m,
                         "precision": "fp64", "us_per_launch": ms64 * 1e3, "bytes_per_point": 16,
                         "achieved_gbs": m * 16 / (ms64 / 1e3) / 1e9, "frac_hbm": m * 16 / (ms64 / 1e3) / 1e9 / hbm,
-                        "points_per_s": m / (ms64 / 1e3)})
+                        "points_per_s": pps, "bound": "fp64 pipe",
+                        "fp64_inst_per_point": FP64_INST_PER_POINT,
+                        "frac_fp64_pipe": pps * FP64_INST_PER_POINT / (FP64_PEAK_GFMA * 1e9)})
             del x64, y64
         del x, y
     pr = make_problem(0)

@@ -18,6 +18,11 @@ int eval_blocks_per_sm_mixed() {
     if (!attr_set) {
         cudaFuncSetAttribute(eval_round_kernel<PREC_MIXED, BuiltinModels>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         cudaFuncSetAttribute(fit_loop_kernel<PREC_MIXED, BuiltinModels>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        // the whole unified L1 / shared array as shared memory: two CTAs with their rings per SM
+        cudaFuncSetAttribute(eval_round_kernel<PREC_MIXED, BuiltinModels>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(fit_loop_kernel<PREC_MIXED, BuiltinModels>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
         attr_set = true;
     }
     int b = 0, b2 = 0;

@@ -22,6 +22,9 @@ int blocks_mixed() {
     const void* f = loop_mixed<M>();
     const int dyn = (int)RING_BYTES;
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+        cudaSuccess)
+        return 0;
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, EVAL_THREADS, dyn) != cudaSuccess) return 0;
     return b;

@@ -337,9 +337,16 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
+// Bounded both in polls and in time (global timer, checked every 256 polls):
+// a chunk that never lands gives up within about MBAR_WAIT_NS.
+constexpr unsigned long long MBAR_WAIT_NS = 1000ull * 1000 * 1000;
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    for (long long it = 0; it < MBAR_SPIN_LIMIT; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long it = 1; it < MBAR_SPIN_LIMIT; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 0 && global_ns() - t0 > MBAR_WAIT_NS) break;
+    }
     return false;
 }
 

@@ -411,6 +411,11 @@ enum { SI_STATUS = 0, SI_NFEV, SI_NJEV, SI_FACTOR, SI_GN, SI_REJECTED, SI_PCOV, 
 // exp for exponents up to ~10), measured against FP64 fixed points.
 constexpr double GUARD_C_H = 16.0;
 constexpr double GUARD_SE_REL = 0.05;
+// A stall by rejections (a stop on xtol alone) finishes in FP64 when the floor
+// estimate exceeds this fraction of guard_floor (ten times stricter than a
+// stop on ftol: the stalled point is anywhere within the noise ball, not at
+// the FP32 fixed point).
+constexpr double GUARD_STALL_FRAC = 0.1;
 constexpr double EPS32 = 5.960464477539063e-08;
 
 // Termination scale of a mixed fit the guard moved to FP64 passes after FP32
@@ -815,11 +820,15 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
                 esc = (cst->phase == PH_INIT) ? GUARD_ESC_INIT : GUARD_ESC_MID;
             // a finish: the floor estimate is above guard_floor, a parameter's
             // standard error is above GUARD_SE_REL of it, or the FP32
-            // iteration stopped on xtol alone (steps that shrink below xtol
-            // by rejections can stall it short of its own fixed point; a stop
-            // on ftol and xtol together ends on an accepted step, like ftol)
+            // iteration stopped on xtol alone with a floor estimate above
+            // GUARD_STALL_FRAC of guard_floor.  (A stop on xtol alone is a
+            // stall by rejections: the gradient has sunk into its FP32
+            // rounding noise, so the point lies anywhere within about the
+            // floor of the FP32 fixed point; a stop on ftol and xtol together
+            // ends on an accepted step, like ftol.)
             else if (stt >= FS_GTOL && stt <= FS_FTOL_XTOL && d.guard_floor < INFINITY &&
-                     (!(floor_x <= d.guard_floor) || !(serel_x <= GUARD_SE_REL) || stt == FS_XTOL))
+                     (!(floor_x <= d.guard_floor) || !(serel_x <= GUARD_SE_REL) ||
+                      (stt == FS_XTOL && !(floor_x <= GUARD_STALL_FRAC * d.guard_floor))))
                 esc = GUARD_FINISH;
             S.si[SI_ESC] = esc;
             if (take) { st->floor_x = S.sd[SD_FLOOR]; st->serel_x = S.sd[SD_SEREL]; }

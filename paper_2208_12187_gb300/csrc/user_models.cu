@@ -193,6 +193,8 @@ int kernels_for_model(int id, const KernelSet** out) {
             const void* f = (const void*)kern;
             const int dyn = (int)eval_dyn_smem(p);
             e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+            if (e == cudaSuccess && p == PREC_MIXED)     // two CTAs with their bulk-copy rings per SM
+                e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
             int b = 0;
             if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, EVAL_THREADS, dyn);
             if (e != cudaSuccess) return fail(GBFIT_E_CUDA, "user model %d occupancy: %s", id, cudaGetErrorString(e));
