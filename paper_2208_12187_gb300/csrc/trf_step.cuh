@@ -719,6 +719,13 @@ __device__ void trf_step(const FitDesc& d, FitState* st, FitResult* res, TrfSmem
             if (ftol_ok && xtol_ok) status = FS_FTOL_XTOL;
             else if (ftol_ok) status = FS_FTOL;
             else if (xtol_ok) status = FS_XTOL;
+            // FP32 passes: a rejected trial whose predicted reduction is below
+            // ftol f ends the fit as a stall (status xtol, as the shrinking
+            // radius would after a few more rejected passes): any later
+            // accepted step would reduce f by less still, and in FP32 such a
+            // step follows the rounding noise of the gradient (the guard's
+            // stall rule then decides on an FP64 finish)
+            else if (rejected && mixed_pass && pred < d.ftol * f) status = FS_XTOL;
             if (bad & 2) status = FS_NUMERICAL;
         }
         // the Gram at the (new) current point, unpacked from its packed upper triangle
