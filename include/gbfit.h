@@ -53,11 +53,14 @@ extern "C" {
 #define GBFIT_E_CANCELLED       -8  /* serving: the request was cancelled (gbfit_server_cancel) */
 
 /* ---- fit_status (per fit; mirrors the termination tests) ---- */
-#define GBFIT_FIT_NUMERICAL     -1  /* non-finite cost or Jacobian at p0 */
+#define GBFIT_FIT_NUMERICAL     -1  /* non-finite cost or Jacobian at p0, or a bounded wait for
+                                       streamed data gave up (the sums are incomplete) */
 #define GBFIT_FIT_MAX_NFEV       0  /* nfev reached max_nfev */
 #define GBFIT_FIT_GTOL           1  /* ||v * g||_inf < gtol */
 #define GBFIT_FIT_FTOL           2  /* accepted step with f - f_new < ftol * f */
-#define GBFIT_FIT_XTOL           3  /* step with ||w|| < xtol * (xtol + ||x||) */
+#define GBFIT_FIT_XTOL           3  /* step with ||w|| < xtol * (xtol + ||x||); mixed precision, FP32
+                                       passes: also a rejected trial whose predicted reduction is
+                                       below ftol * f (a stall in the FP32 rounding noise) */
 #define GBFIT_FIT_FTOL_XTOL      4  /* both on the same step */
 #define GBFIT_FIT_INVALID_DATA  -2  /* sigma <= 0 or non-finite x/y/sigma found on the device */
 
