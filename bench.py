@@ -83,9 +83,9 @@ class L2Flush:
         self.w.zero_()
 # DRAM bytes (read + write) per launch of the loop kernel (one whole fit of
 # the headline workload, 5 passes) from the ncu capture summarised in
-# profiles/fit_loop_mixed_gauss2d_1024.md (8.66 MB read + 3.07 MB written);
+# profiles/fit_loop_mixed_gauss2d_1024.md (8.666 MB read + 3.3 KB written);
 # None whenever the kernel has changed since the capture.
-TRAFFIC_BYTES_PER_LAUNCH = 11.73e6
+TRAFFIC_BYTES_PER_LAUNCH = 8.6697e6
 
 
 def measured_peaks():
