@@ -334,9 +334,6 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
 // Bounded both in polls and in time (global timer, checked every 256 polls):
 // a chunk that never lands gives up within about MBAR_WAIT_NS.
 constexpr unsigned long long MBAR_WAIT_NS = 1000ull * 1000 * 1000;
