@@ -17,7 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libgbfit.so")
-SOURCES = ["kernels_mixed.cu", "kernels_fp64.cu", "kernels_single.cu", "kernels.cu", "engine.cu", "user_models.cu",
+SOURCES = ["kernels_mixed.cu", "kernels_mixed_eval.cu", "kernels_fp64.cu", "kernels_fp64_eval.cu", "kernels_single.cu",
+           "kernels.cu", "engine.cu", "user_models.cu",
            "cov_kernels.cu"]
 # device headers embedded in the library for run-time compilation of user models
 RTC_HEADERS = ["rtc_compat.cuh", "gbfit_internal.cuh", "sync_device.cuh", "models.cuh", "trf_device.cuh", "trf_step.cuh",

@@ -16,6 +16,8 @@ void* kernel_init_slots_mixed();
 void* kernel_init_slots_fp64();
 int eval_blocks_per_sm_mixed();
 int eval_blocks_per_sm_fp64();
+int eval_round_blocks_per_sm_mixed();      // resident CTAs per SM of the single-round kernel alone
+int eval_round_blocks_per_sm_fp64();
 size_t eval_dyn_smem_mixed();
 size_t eval_dyn_smem_fp64();
 void* kernel_eval_round(int prec);
